@@ -1,0 +1,21 @@
+"""FP64 CPU oracle for the randomized LU decomposition (Shabat, Shmueli, Aizenbud,
+Averbuch, "Randomized LU Decomposition", Algorithm 1).
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path imports this package: only
+``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` may call it. It shares no code with the CUDA path; the only module
+both sides use is the seeded input generator ``paper_1310_7202_gb300.synth``, which holds
+none of the method's arithmetic.
+
+Every function cites the passage of the paper it follows. Pins (tests that tie the oracle
+to something other than itself) live in ``tests/test_oracle_*.py``.
+"""
+from .rlu_oracle import (  # noqa: F401
+    PHILOX_M0, PHILOX_M1, PHILOX_W0, PHILOX_W1,
+    philox4x32_10, philox_stream,
+    series_ln, series_sincos_2pi, box_muller, gaussian,
+    lu_partial_pivot, lu_column_pivot, pinv_apply,
+    rlu_factor, reconstruct_error, spectral_norm,
+    theorem1_constant, theorem1_success_probability, theorem1_failure_terms,
+    check_dims,
+)

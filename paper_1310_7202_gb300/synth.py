@@ -1,0 +1,97 @@
+"""Seeded synthetic inputs: matrices with a prescribed singular spectrum,
+A = U diag(sigma) V^T, U and V the orthonormal factors of the QR of seeded N(0,1)
+matrices (sign-fixed so that diag(R) > 0).
+
+This module is shared by the tests, the benchmark and the oracle side. It holds none of
+the randomized LU's own arithmetic (its Gaussians come from numpy / torch generators,
+not from the factorization's Philox stream).
+
+Spectra used by the paper's experiments (Section 5) and by the workloads built on them:
+  * exponential decay (Section 5.1, 3000 x 3000, l = k + 3),
+  * sigma_k = 100 / (9 + k)^2 normalised to sigma_1 = 1 (Section 5.2),
+and the workload spectra: a two-level spectrum (1 for i <= 20, then 1e-3 * 0.9^(i-21)),
+i^-2, 0.99^i, exp(-i/k) and i^-1.5.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def spectrum(kind: str, r: int, k: int | None = None) -> np.ndarray:
+    """Singular values sigma_1..sigma_r (1-based index i) of a named spectrum."""
+    i = np.arange(1, r + 1, dtype=np.float64)
+    if kind == "two_level":          # 1 for i <= 20, 1e-3 * 0.9^(i-21) after
+        return np.where(i <= 20, 1.0, 1e-3 * 0.9 ** (i - 21))
+    if kind == "inv_square":         # i^-2
+        return i ** -2.0
+    if kind == "geometric_099":      # 0.99^i
+        return 0.99 ** i
+    if kind == "exp_k":              # exp(-i/k)
+        return np.exp(-i / float(k))
+    if kind == "inv_1p5":            # i^-1.5
+        return i ** -1.5
+    if kind == "rank_k":             # exactly rank k: 1 for i <= k, 0 after
+        return np.where(i <= k, 1.0, 0.0)
+    if kind == "paper_slow":         # 100/(9+i)^2, normalised so that sigma_1 = 1
+        s = 100.0 / (9.0 + i) ** 2
+        return s / s[0]
+    if kind == "paper_exp":          # exponential decay, e^(-i/10) scaled to sigma_1 = 1
+        return np.exp(-(i - 1.0) / 10.0)
+    raise ValueError(f"unknown spectrum {kind!r}")
+
+
+def _haar_like_q(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    g = rng.standard_normal((rows, cols))
+    q, r = np.linalg.qr(g)
+    d = np.sign(np.diag(r))
+    d[d == 0] = 1.0
+    return q * d
+
+
+def prescribed_matrix(m: int, n: int, sigma: np.ndarray, seed_u: int, seed_v: int,
+                      dtype=np.float64) -> np.ndarray:
+    """A = U diag(sigma) V^T (m x n) on the CPU in FP64, then rounded to ``dtype``.
+    U is m x r and V is n x r with r = len(sigma) <= min(m, n)."""
+    r = len(sigma)
+    assert r <= min(m, n)
+    U = _haar_like_q(np.random.default_rng(seed_u), m, r)
+    V = _haar_like_q(np.random.default_rng(seed_v), n, r)
+    A = (U * sigma) @ V.T
+    return np.ascontiguousarray(A.astype(dtype))
+
+
+def prescribed_matrix_torch(m: int, n: int, sigma: np.ndarray, seed_u: int, seed_v: int,
+                            dtype, device: str = "cuda"):
+    """Same construction with torch on ``device`` (for sizes where CPU QR is slow). The
+    Gaussians come from torch's generator for that device; the QR and the product run in
+    FP32 (or FP64 when ``dtype`` is float64) and the result is rounded to ``dtype``."""
+    import torch
+
+    r = len(sigma)
+    work = torch.float64 if dtype == torch.float64 else torch.float32
+
+    def q_of(seed, rows):
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+        x = torch.randn(rows, r, generator=g, device=device, dtype=work)
+        q, rr = torch.linalg.qr(x)
+        d = torch.sign(torch.diagonal(rr))
+        d[d == 0] = 1.0
+        return q * d
+
+    U = q_of(seed_u, m)
+    V = q_of(seed_v, n)
+    s = torch.as_tensor(sigma, dtype=work, device=device)
+    A = (U * s) @ V.T
+    return A.to(dtype).contiguous()
+
+
+# The workloads, by size, spectrum and storage (see the design doc for the recipe).
+WORKLOADS = {
+    "fp64_512": dict(m=512, n=512, k=20, l=25, spectrum="two_level", dtype="f64",
+                     seed_u=11, seed_v=12, seed_g=1),
+    "fp32_8192": dict(m=8192, n=8192, k=200, l=210, spectrum="inv_square", dtype="f32",
+                      seed_u=21, seed_v=22, seed_g=2),
+    "bf16_32768x16384": dict(m=32768, n=16384, k=512, l=532, spectrum="geometric_099",
+                             dtype="bf16", seed_u=31, seed_v=32, seed_g=3),
+}

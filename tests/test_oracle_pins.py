@@ -1,0 +1,337 @@
+"""Pins for the FP64 oracle: each test ties an oracle function to something other than
+itself (a library routine, a closed form, an invariant, a value printed in the paper, or
+brute force on a tiny input). CPU only."""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+import scipy.stats as st
+
+import oracle as O
+from paper_1310_7202_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ----------------------------------------------------------------------------------------
+# Step 1: Philox4x32-10 against an independent library implementation (Triton's, run by
+# its CPU interpreter in a child process), for several keys, counters and stream ids.
+# ----------------------------------------------------------------------------------------
+
+_TRITON_SCRIPT = r"""
+import json, sys
+import numpy as np
+import torch, triton, triton.language as tl
+from triton.language.random import philox_impl
+
+@triton.jit
+def kern(c_ptr, out_ptr, k0, k1, N: tl.constexpr):
+    offs = tl.arange(0, N)
+    c0 = tl.load(c_ptr + offs * 4 + 0).to(tl.uint32, bitcast=True)
+    c1 = tl.load(c_ptr + offs * 4 + 1).to(tl.uint32, bitcast=True)
+    c2 = tl.load(c_ptr + offs * 4 + 2).to(tl.uint32, bitcast=True)
+    c3 = tl.load(c_ptr + offs * 4 + 3).to(tl.uint32, bitcast=True)
+    a, b, c, d = philox_impl(c0, c1, c2, c3, k0.to(tl.uint32), k1.to(tl.uint32))
+    tl.store(out_ptr + offs * 4 + 0, a.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + offs * 4 + 1, b.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + offs * 4 + 2, c.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + offs * 4 + 3, d.to(tl.int32, bitcast=True))
+
+cases = json.loads(sys.stdin.read())
+res = []
+for case in cases:
+    ctr = np.array(case["ctr"], dtype=np.uint32).view(np.int32)
+    n = len(ctr) // 4
+    out = torch.zeros(4 * n, dtype=torch.int32)
+    kern[(1,)](torch.from_numpy(ctr.copy()), out, case["k0"], case["k1"], N=n)
+    res.append((out.numpy().view(np.uint32)).tolist())
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_triton_library():
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(5)
+    cases = []
+    for k0, k1 in [(0, 0), (0xFFFFFFFF, 0xFFFFFFFF), (0x243F6A88, 0x85A308D3), (7, 1)]:
+        ctr = rng.integers(0, 2**32, size=(16, 4), dtype=np.uint64)
+        ctr[0] = 0
+        ctr[1] = 0xFFFFFFFF
+        cases.append(dict(ctr=ctr.reshape(-1).tolist(), k0=k0, k1=k1))
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    out = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(cases),
+                         capture_output=True, text=True, env=env, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    ref = json.loads(out.stdout.strip().splitlines()[-1])
+    for case, want in zip(cases, ref):
+        ctr = np.array(case["ctr"], dtype=np.uint64).reshape(-1, 4)
+        got = O.philox4x32_10(ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3],
+                              case["k0"], case["k1"])
+        got = np.stack(got, axis=1).reshape(-1)
+        assert got.tolist() == want
+
+
+def test_philox_stream_layout():
+    # counter = (index lo, index hi, stream, 0), key = (seed lo, seed hi)
+    seed, stream = 0x0123456789ABCDEF, 3
+    s = O.philox_stream(seed, stream, (1 << 32) - 2, 4).reshape(4, 4)
+    for t, idx in enumerate(range((1 << 32) - 2, (1 << 32) + 2)):
+        one = O.philox4x32_10(np.array([idx & 0xFFFFFFFF]), np.array([idx >> 32]),
+                              np.array([stream]), np.array([0]),
+                              seed & 0xFFFFFFFF, seed >> 32)
+        assert [int(v[0]) for v in one] == s[t].tolist()
+
+
+# ----------------------------------------------------------------------------------------
+# Box-Muller series against libm (error bounds) and the Gaussian's distribution.
+# ----------------------------------------------------------------------------------------
+
+def test_series_ln_matches_libm():
+    rng = np.random.default_rng(1)
+    x = rng.integers(0, 2**32, size=200000, dtype=np.uint64)
+    edge = np.array([0, 1, 2**31 - 1, 2**31, 0xB504F333, 0xB504F334, 2**32 - 2, 2**32 - 1],
+                    dtype=np.uint64)
+    x = np.concatenate([x, edge])
+    u = (x.astype(np.float64) + 1.0) * 2.0**-32
+    got = O.series_ln(u)
+    want = np.log(u)
+    # within 4 ulp of |ln u| (ln u = 0 exactly at u = 1)
+    tol = 4 * np.spacing(np.maximum(np.abs(want), 1e-300))
+    assert np.all(np.abs(got - want) <= tol)
+    assert O.series_ln(np.array([1.0]))[0] == 0.0
+
+
+def test_series_sincos_matches_libm():
+    rng = np.random.default_rng(2)
+    x = rng.integers(0, 2**32, size=200000, dtype=np.uint64)
+    x = np.concatenate([x, np.arange(0, 2**32, 2**29, dtype=np.uint64),
+                        np.arange(0, 2**32, 2**29, dtype=np.uint64) + 1,
+                        np.arange(2**29, 2**32 + 1, 2**29, dtype=np.uint64) - 1])
+    s, c = O.series_sincos_2pi(x)
+    th = 2.0 * np.pi * (x.astype(np.float64) * 2.0**-32)
+    # libm's argument itself carries the rounding of 2*pi*x (<= 2 ulp of 2*pi)
+    assert np.max(np.abs(s - np.sin(th))) < 4e-15
+    assert np.max(np.abs(c - np.cos(th))) < 4e-15
+    assert np.max(np.abs(s * s + c * c - 1.0)) < 1e-15
+
+
+def test_gaussian_distribution_and_layout():
+    n, l = 1000, 1000
+    G = O.gaussian(12345, 0, n, l)
+    z = G.T.reshape(-1)                      # element order e = j*n + i
+    N = z.size
+    assert abs(z.mean()) < 5.0 / math.sqrt(N)
+    assert abs(z.var() - 1.0) < 5.0 * math.sqrt(2.0 / N)
+    assert st.kstest(z, "norm").pvalue > 1e-3
+    # fourth moment of N(0,1) is 3
+    assert abs(np.mean(z ** 4) - 3.0) < 0.05
+    # layout: elements 4c..4c+3 come from counter c as (BM(x0,x1), BM(x2,x3))
+    w = O.philox_stream(12345, 0, 0, 2).reshape(2, 4)
+    a0, a1 = O.box_muller(w[:, 0], w[:, 1])
+    b0, b1 = O.box_muller(w[:, 2], w[:, 3])
+    first8 = np.stack([a0, a1, b0, b1], axis=1).reshape(-1)
+    assert np.array_equal(first8, G[:8, 0])
+    # ragged tail: n*l not a multiple of 4
+    G2 = O.gaussian(9, 1, 7, 3)
+    assert G2.shape == (7, 3)
+    assert np.array_equal(G2, O.gaussian(9, 1, 21, 1).reshape(3, 7).T)
+
+
+def test_gaussian_streams_differ():
+    a = O.gaussian(1, 0, 64, 4)
+    b = O.gaussian(1, 1, 64, 4)
+    c = O.gaussian(2, 0, 64, 4)
+    assert not np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+# ----------------------------------------------------------------------------------------
+# Step 3: partial-pivot LU against LAPACK getrf (scipy.linalg.lu_factor).
+# ----------------------------------------------------------------------------------------
+
+def _ipiv_to_perm(ipiv, m):
+    perm = np.arange(m)
+    for j, p in enumerate(ipiv):
+        perm[[j, p]] = perm[[p, j]]
+    return perm
+
+
+@pytest.mark.parametrize("m,l", [(7, 3), (40, 12), (97, 31), (16, 16)])
+def test_lu_partial_pivot_matches_lapack(m, l):
+    rng = np.random.default_rng(m * 100 + l)
+    Y = rng.standard_normal((m, l))
+    LU, perm, zero, gaps = O.lu_partial_pivot(Y)
+    ref, ipiv = sl.lu_factor(Y)
+    assert np.array_equal(perm, _ipiv_to_perm(ipiv, m)[:m])
+    assert np.allclose(LU, ref, rtol=0, atol=1e-12)
+    assert zero == -1
+    Ly = np.tril(LU, -1) + np.eye(m, l)
+    Uy = np.triu(LU[:l])
+    assert np.max(np.abs(Ly)) <= 1.0
+    assert np.allclose(Ly @ Uy, Y[perm], atol=1e-12)
+
+
+def test_lu_partial_pivot_zero_column_and_ties():
+    Y = np.array([[0.0, 1.0], [0.0, 2.0], [0.0, -2.0]])
+    LU, perm, zero, _ = O.lu_partial_pivot(Y)
+    assert zero == 0 and perm[0] == 0          # zero pivot: no swap, reported
+    # tie in |value|: the first in current row order wins (getf2 / i?amax rule)
+    Y = np.array([[1.0, 0.0], [-3.0, 1.0], [3.0, 5.0]])
+    _, perm, _, _ = O.lu_partial_pivot(Y)
+    assert perm[0] == 1
+
+
+# ----------------------------------------------------------------------------------------
+# Step 6: column-pivoted LU = getrf of B^T (same Schur complements, same pivots).
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k,n", [(3, 9), (12, 50), (20, 20)])
+def test_lu_column_pivot_matches_lapack_on_transpose(k, n):
+    rng = np.random.default_rng(k * 1000 + n)
+    B = rng.standard_normal((k, n))
+    Lb, Ub, q, zero, _ = O.lu_column_pivot(B)
+    _, ipiv = sl.lu_factor(B.T)
+    assert np.array_equal(q, _ipiv_to_perm(ipiv, n))
+    assert np.allclose(Lb @ Ub, B[:, q], atol=1e-12)
+    d = np.abs(np.diag(Ub))
+    for j in range(k):
+        assert np.all(np.abs(Ub[j, j:]) <= d[j] * (1 + 1e-15))
+    assert np.allclose(np.diag(Lb), 1.0) and np.allclose(np.triu(Lb, 1), 0.0)
+
+
+# ----------------------------------------------------------------------------------------
+# Step 5: B = L_y^+ P A against least squares (QR/SVD based, independent of the Gram).
+# ----------------------------------------------------------------------------------------
+
+def test_pinv_apply_matches_lstsq():
+    rng = np.random.default_rng(3)
+    m, k, n = 120, 9, 40
+    Y = rng.standard_normal((m, k + 2))
+    LU, _, _, _ = O.lu_partial_pivot(Y)
+    Ly = np.tril(LU[:, :k], -1) + np.eye(m, k)
+    PA = rng.standard_normal((m, n))
+    B = O.pinv_apply(Ly, PA)
+    ref = np.linalg.lstsq(Ly, PA, rcond=None)[0]
+    assert np.allclose(B, ref, rtol=1e-11, atol=1e-11)
+    # normal equations hold: L_y^T (L_y B - PA) = 0
+    assert np.max(np.abs(Ly.T @ (Ly @ B - PA))) < 1e-10
+
+
+# ----------------------------------------------------------------------------------------
+# End to end: closed forms, the identity in the proof of Theorem 4.1, brute force.
+# ----------------------------------------------------------------------------------------
+
+def _check_structure(res, m, n, k):
+    P, Q, L, U = res["P"], res["Q"], res["L"], res["U"]
+    assert sorted(P.tolist()) == list(range(m))
+    assert sorted(Q.tolist()) == list(range(n))
+    assert L.shape == (m, k) and U.shape == (k, n)
+    assert np.allclose(np.triu(L[:k], 1), 0.0)
+    assert np.allclose(np.diag(L[:k]), 1.0)
+    assert np.allclose(np.tril(U[:, :k], -1), 0.0)
+
+
+def test_exact_rank_k_reconstructs_to_rounding():
+    m, n, k, l = 200, 150, 12, 17
+    A = synth.prescribed_matrix(m, n, synth.spectrum("rank_k", min(m, n), k), 1, 2)
+    res = O.rlu_factor(A, k, l, seed=5)
+    _check_structure(res, m, n, k)
+    fro, spec = O.reconstruct_error(A, res["P"], res["Q"], res["L"], res["U"])
+    assert fro / np.linalg.norm(A) < 1e-12
+    assert spec < 1e-12
+
+
+def test_full_rank_k_equals_n_is_exact_lu():
+    n = 24
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((n, n))
+    res = O.rlu_factor(A, n, n, seed=3)
+    fro, _ = O.reconstruct_error(A, res["P"], res["Q"], res["L"], res["U"])
+    assert fro / np.linalg.norm(A) < 1e-12
+
+
+def test_proof_identity_eq_main_bound():
+    # LU - PAQ = (L_y L_y^+ - I) P A Q  (proof of Theorem 4.1, Eq. main_bound_proof)
+    m, n, k, l = 90, 70, 8, 11
+    A = synth.prescribed_matrix(m, n, synth.spectrum("inv_square", min(m, n)), 3, 4)
+    res = O.rlu_factor(A, k, l, seed=8)
+    P, Q, L, U, Ly = res["P"], res["Q"], res["L"], res["U"], res["Ly"]
+    PAQ = A[P][:, Q]
+    lhs = L @ U - PAQ
+    rhs = (Ly @ np.linalg.pinv(Ly) - np.eye(m)) @ PAQ
+    assert np.max(np.abs(lhs - rhs)) < 1e-12
+    # ||L_y L_y^+|| <= 1 and L_y^+ L_y = I (used in the proof of Lemma 4.2)
+    assert np.linalg.norm(Ly @ np.linalg.pinv(Ly), 2) <= 1 + 1e-12
+    assert np.allclose(np.linalg.pinv(Ly) @ Ly, np.eye(k), atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_brute_force_bounds_tiny(seed):
+    # sigma_{k+1} <= ||LU - PAQ||_2 <= C(n,k,l,beta=5,gamma=5) sigma_{k+1} (Theorem 4.1;
+    # the lower bound is Eckart-Young). sigma by full SVD of A.
+    m, n, k, l = 48, 40, 6, 9
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n)) @ np.diag(0.7 ** np.arange(n)) @ rng.standard_normal((n, n))
+    s = np.linalg.svd(A, compute_uv=False)
+    res = O.rlu_factor(A, k, l, seed=seed + 10)
+    _, spec = O.reconstruct_error(A, res["P"], res["Q"], res["L"], res["U"])
+    C = O.theorem1_constant(n, k, l, 5.0, 5.0)
+    assert s[k] * (1 - 1e-10) <= spec <= C * s[k]
+
+
+def test_reconstruct_error_known_residual():
+    # R = PAQ - LU with L U = 0 and A = x y^T: ||R||_F = ||R||_2 = |x||y|
+    m, n, k = 30, 20, 2
+    x = np.arange(1.0, m + 1)
+    y = np.linspace(-1, 1, n)
+    A = np.outer(x, y)
+    P = np.arange(m)[::-1]
+    Q = np.roll(np.arange(n), 3)
+    fro, spec = O.reconstruct_error(A, P, Q, np.zeros((m, k)), np.zeros((k, n)))
+    want = np.linalg.norm(x) * np.linalg.norm(y)
+    assert abs(fro - want) < 1e-12 * want and abs(spec - want) < 1e-12 * want
+
+
+def test_power_iteration_matches_svd():
+    rng = np.random.default_rng(6)
+    R = rng.standard_normal((300, 200)) @ np.diag(np.linspace(3, 1, 200))
+    want = np.linalg.norm(R, 2)
+    got = O.spectral_norm(R, dense_limit=10)
+    assert abs(got - want) < 1e-6 * want
+
+
+# ----------------------------------------------------------------------------------------
+# Theorem 4.1: the success probability against Table 1 of the paper.
+# ----------------------------------------------------------------------------------------
+
+def test_theorem1_xi_matches_table1():
+    rows = []
+    with open(os.path.join(HERE, "golden", "xi_table.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                a, b, c, d = line.split()
+                rows.append((int(a), float(b), float(c), float(d)))
+    assert len(rows) == 9
+    for lk, beta, gamma, one_minus_xi in rows:
+        k = 20
+        t1, t2 = O.theorem1_failure_terms(10000, k, k + lk, beta, gamma)
+        got = t1 + t2
+        # the table prints two significant digits
+        assert abs(got - one_minus_xi) <= 0.025 * one_minus_xi, (lk, beta, gamma, got)
+
+
+def test_theorem1_constant_closed_form():
+    # n=1, k=0, l=1, beta=gamma=1: 2*sqrt(3) + 2*sqrt(2)*(0+1)
+    assert abs(O.theorem1_constant(1, 0, 1, 1.0, 1.0) - (2 * math.sqrt(3) + 2 * math.sqrt(2))) < 1e-14
+
+
+def test_check_dims():
+    O.check_dims(10, 8, 3, 8)
+    for bad in [(10, 8, 0, 3), (10, 8, 4, 3), (10, 8, 3, 9), (5, 8, 3, 6)]:
+        with pytest.raises(ValueError):
+            O.check_dims(*bad)
