@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Benchmark of the randomized LU hot path (Algorithm 1 of Shabat et al.) on GB300.
+
+One step = one whole factorization (steps 1-8) of the workload's synthetic matrix, inputs
+resident in HBM. Prints one JSON line (rank 0):
+  value      rank-k factorizations per second over all ranks (replicas: weak scaling)
+  e2e        the same through the public API with the input copied from pinned host memory
+             and the factors copied back inside the timed region
+  roofline   the dominant kernel's achieved rate (algorithmic work / CUDA-event duration)
+             against the measured (or derived) peak
+  cpu_baseline  the FP64 oracle timed on the host cores on the same workload
+
+--impl reference times the oracle itself (the reference arm) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1310_7202_gb300 import synth  # noqa: E402
+
+METRIC = "rank-k LU/s and GEMM TFLOP/s vs plain FP32 at fixed error; serve p50/p99"
+WORKLOAD = "fp32_8192"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+def dist_setup(backend: str):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------------------------------
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def stage_work(name: str, m: int, n: int, k: int, l: int, esz: int):
+    """Algorithmic work of one launch of a timed step: (flops, bytes)."""
+    return {
+        "gaussian": (0.0, n * l * esz),
+        "gemm_Y": (2.0 * m * n * l, (m * n + n * l + m * l) * esz),
+        "lu_Y": (float(m) * l * l, 2.0 * m * l * esz),
+        "build_Ly": (0.0, 3.0 * m * k * esz),
+        "gram": (2.0 * m * k * k, m * k * esz + k * k * 8),
+        "chol_inv": (2.0 * k ** 3 / 3.0, 3.0 * k * k * 8),
+        "gemm_C": (2.0 * m * n * k, (m * n + m * k + k * n) * esz),
+        "tri_B": (4.0 * k * k * n, 5.0 * k * n * esz),
+        "lu_B": (float(n) * k * k, 2.0 * n * k * esz),
+        "gather_Lb_U": (0.0, 2.0 * k * n * esz),
+        "gemm_L": (2.0 * m * k * k, 2.0 * m * k * esz),
+    }[name]
+
+
+STAGE_SOURCE = {"gaussian": "gauss.cu", "gemm_Y": "gemm_simt.cu", "lu_Y": "panel_lu.cu",
+                "build_Ly": "small.cu", "gram": "gemm_simt.cu", "chol_inv": "small.cu",
+                "gemm_C": "gemm_simt.cu", "tri_B": "gemm_simt.cu", "lu_B": "panel_lu.cu",
+                "gather_Lb_U": "small.cu", "gemm_L": "gemm_simt.cu"}
+
+
+def source_sha(stage: str) -> str:
+    p = os.path.join(ROOT, "paper_1310_7202_gb300", "csrc", STAGE_SOURCE[stage])
+    with open(p, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def dram_traffic(stage: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, when it was taken on the
+    current source of the kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = source_sha(stage)
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == stage \
+                and parts[1] == workload and parts[2] == sha:
+            return float(parts[3])
+    return None
+
+
+# ---------------------------------------------------------------------------------------
+def make_input(w: dict, device: str):
+    sigma = synth.spectrum(w["spectrum"], min(w["m"], w["n"]), w["k"])
+    dt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[w["dtype"]]
+    A = synth.prescribed_matrix_torch(w["m"], w["n"], sigma, w["seed_u"], w["seed_v"], dt,
+                                      device=device)
+    return A, sigma
+
+
+def oracle_once(A_host: np.ndarray, w: dict):
+    import oracle as O
+    G = None
+    if w["dtype"] != "f64":
+        G = O.gaussian_f32(w["seed_g"], 0, w["n"], w["l"]).astype(np.float64)
+    return O.rlu_factor(A_host, w["k"], w["l"], seed=w["seed_g"], G=G)
+
+
+def cpu_baseline(A_host: np.ndarray, w: dict, budget_s: float = 15.0):
+    """The oracle as it stands, on the host cores: whole factorizations of the workload
+    until about ``budget_s`` seconds have passed (at least one)."""
+    t0 = time.perf_counter()
+    count = 0
+    res = None
+    while True:
+        res = oracle_once(A_host, w)
+        count += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": count / el, "unit": "LU/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{count} whole FP64 factorizations of the workload's matrix "
+                      f"(numpy, multithreaded BLAS), {el:.1f} s"}, res
+
+
+def precision_of(w):
+    return "f64" if w["dtype"] == "f64" else "f32"
+
+
+# ---------------------------------------------------------------------------------------
+def run_ours(args):
+    import oracle as O
+    from paper_1310_7202_gb300 import rlu
+
+    world, rank, local = dist_setup("nccl")
+    dev = torch.device("cuda", local)
+    w = synth.WORKLOADS[args.workload]
+    m, n, k, l = w["m"], w["n"], w["k"], w["l"]
+    prec = precision_of(w)
+    esz = 8 if prec == "f64" else 4
+    A, sigma = make_input(w, "cuda")
+    fz = rlu.Factorizer(m, n, k, l, prec)
+    ns = rlu.NUM_TIMED_STEPS
+    names = rlu.timed_step_names()
+    K, W = args.steps, args.warmup
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * ns)] for _ in range(K)]
+    stream = torch.cuda.current_stream()
+
+    for _ in range(W):
+        fz(A, w["seed_g"])
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = rlu.launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_stop = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        barrier(world)
+        t_start.record(stream)
+        for i in range(K):
+            fz(A, w["seed_g"], stages={"events": evs[i]})
+        t_stop.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = rlu.launch_count() - launches0
+    ms = t_start.elapsed_time(t_stop)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = world * K / (ms_max / 1e3)
+    stage_ms = {names[i]: statistics.mean(evs[s][2 * i].elapsed_time(evs[s][2 * i + 1])
+                                          for s in range(K)) for i in range(ns)}
+
+    # ---- end to end through the public API: host input in, host factors out ----------
+    A_pin = torch.empty((m, n), dtype=A.dtype, pin_memory=True)
+    A_pin.copy_(A)
+    A_dev = torch.empty_like(A)
+    outs = {"P": torch.empty(m, dtype=torch.int32, pin_memory=True),
+            "Q": torch.empty(n, dtype=torch.int32, pin_memory=True),
+            "L": torch.empty((m, k), dtype=fz.dtype, pin_memory=True),
+            "U": torch.empty((k, n), dtype=fz.dtype, pin_memory=True)}
+    h2d = A.numel() * A.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in outs.values())
+
+    def e2e_step():
+        A_dev.copy_(A_pin, non_blocking=True)
+        P, Q, L, U, info = fz(A_dev, w["seed_g"])
+        outs["P"].copy_(P, non_blocking=True)
+        outs["Q"].copy_(Q, non_blocking=True)
+        outs["L"].copy_(L, non_blocking=True)
+        outs["U"].copy_(U, non_blocking=True)
+
+    for _ in range(max(1, min(W, 3))):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    e2e = {"value": world * K / (e2e_ms / 1e3), "unit": "LU/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    # ---- accuracy of the last factorization (outside the timed region) -----------------
+    P, Q, L, U, info = fz(A, w["seed_g"])
+    fro_d, _ = rlu.reconstruct_error(A, P, Q, L, U)
+    torch.cuda.synchronize()
+    err = {"fro": fro_d.item(), "rel_fro": fro_d.item() / float(np.sqrt(np.sum(sigma ** 2))),
+           "sigma_1": float(sigma[0]), "sigma_k1": float(sigma[k]),
+           "info": info.cpu().tolist()}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ---------------------------------------------
+    peaks, peak_kind = load_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    main_stream = [s for s in names if s != "chol_inv"]  # chol_inv overlaps gemm_C
+    dom = max(main_stream, key=lambda s: stage_ms[s])
+    flops, byts = stage_work(dom, m, n, k, l, esz)
+    dom_ms = stage_ms[dom]
+    if flops > 0 and dom.startswith(("gemm", "gram", "tri")):
+        peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12 if prec == "f32" else None
+        roof = {"kernel": dom, "bound": "alu", "achieved": flops / (dom_ms / 1e3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x "
+                               f"{peaks['sm_max_mhz']:.0f} MHz (SIMT FFMA)"}
+    else:
+        peak = peaks["hbm_gbs"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": byts / (dom_ms / 1e3) / 1e9,
+                "peak": peak, "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs"}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+    tr = dram_traffic(dom, args.workload)
+    roof["traffic"] = tr
+    roof["algorithmic_per_launch"] = flops if roof["unit"] == "TFLOP/s" else byts
+    roof["launch_ms"] = dom_ms
+
+    gemm_ms = stage_ms["gemm_Y"] + stage_ms["gemm_C"]
+    gemm_tflops = 2.0 * m * n * (l + k) / (gemm_ms / 1e3) / 1e12
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        A_host = A.double().cpu().numpy()
+        cpu, ores = cpu_baseline(A_host, w)
+        fro_o, _ = O.reconstruct_error(A_host, ores["P"], ores["Q"], ores["L"], ores["U"],
+                                       spectral=False)
+        err["oracle_fro"] = fro_o
+        err["within_tolerance"] = bool(err["fro"] <= 1.1 * fro_o + 1e-4 * sigma[0])
+        err["tolerance"] = "fro <= 1.1 * oracle_fro + 1e-4 * sigma_1"
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "LU/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": f"{args.workload}: m={m} n={n} k={k} l={l}, "
+                               f"sigma_i={w['spectrum']}, {w['dtype']} storage, "
+                               f"{prec} path (SIMT GEMMs, cluster LUs)",
+                   "m": m, "n": n, "k": k, "l": l, "precision": prec,
+                   "l2": f"inputs larger than L2 (A = {A.numel() * A.element_size() / 1e6:.0f} MB)",
+                   "parallelism": f"{world} independent replica(s)"},
+        "gemm_tflops": gemm_tflops,
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "stages_ms": {s: round(v, 4) for s, v in stage_ms.items()},
+        "error": err,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[args.workload]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A, sigma = make_input(w, dev)
+    A_host = A.double().cpu().numpy()
+    for _ in range(args.warmup):
+        oracle_once(A_host, w)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_once(A_host, w)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    m, n, k, l = w["m"], w["n"], w["k"], w["l"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "LU/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: m={m} n={n} k={k} l={l}, "
+                               f"sigma_i={w['spectrum']}, {w['dtype']} storage",
+                   "m": m, "n": n, "k": k, "l": l},
+        "cpu_baseline": {"value": value, "unit": "LU/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} whole FP64 factorizations of the workload's "
+                                   "matrix (numpy, multithreaded BLAS)"},
+        "e2e": {"value": value, "unit": "LU/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

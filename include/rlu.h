@@ -1,0 +1,168 @@
+/*
+ * rlu.h - C ABI of the GB300 (sm_103a) randomized LU library.
+ *
+ * The library computes the randomized LU decomposition of Algorithm 1 of Shabat, Shmueli,
+ * Aizenbud and Averbuch, "Randomized LU Decomposition" (Section 4): for an m x n matrix A
+ * and integers k <= l it returns row and column permutations P, Q, a unit lower
+ * trapezoidal L (m x k) and an upper trapezoidal U (k x n) with
+ *     || P A Q - L U || = O(sigma_{k+1}(A))            (Eq. 1 and Theorem 4.1).
+ *
+ * Conventions shared by every entry point
+ *   - All matrix and vector pointers are DEVICE pointers owned by the caller. The library
+ *     never allocates device memory inside a call; scratch space is the caller's
+ *     ``workspace`` buffer, sized by the matching *_workspace_size() query.
+ *   - ``stream`` is a cudaStream_t passed as void* (NULL = the legacy default stream). Every
+ *     call only enqueues work on that stream (and on library-owned helper streams that
+ *     fork from and join back into it) and returns without synchronising.
+ *   - Argument errors are detected on the host and returned synchronously; nothing is
+ *     enqueued then. Conditions found on the device (zero pivots, NaN/Inf) are written to
+ *     the caller's device-resident rlu_info.
+ *   - Permutations are 0-based gather vectors: (P A Q)[i][j] = A[P[i]][Q[j]].
+ *   - A is row-major (element (i, j) at A[i*lda + j], lda >= n). L is column-major
+ *     (element (i, t) at L[t*ldl + i], ldl >= m). U is row-major (U[t*ldu + j], ldu >= n).
+ *   - Steps 1-8 below refer to the steps of Algorithm 1.
+ */
+#ifndef RLU_H
+#define RLU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RLU_OK = 0,
+  RLU_EINVAL = 1,        /* an argument is out of range, NULL or misaligned */
+  RLU_ENOMEM = 2,        /* workspace smaller than *_workspace_size() */
+  RLU_EUNSUPPORTED = 3,  /* dtype / precision combination not provided */
+  RLU_ECUDA = 4          /* a CUDA runtime call failed (launch, attribute, event) */
+} rlu_status;
+
+typedef enum { RLU_F64 = 0, RLU_F32 = 1, RLU_BF16 = 2 } rlu_dtype;
+
+/* Arithmetic of the whole path.
+ *   RLU_PREC_F64: A, G, Y, B, L, U in FP64, FP64 arithmetic everywhere. A must be RLU_F64.
+ *   RLU_PREC_F32: "plain FP32". A, G, Y, B, L, U in FP32; FP32 SIMT GEMMs and LUs; the
+ *                 k x k Gram matrix is reduced in FP64 and factored (Cholesky) in FP64.
+ *                 A must be RLU_F32. */
+typedef enum { RLU_PREC_F64 = 0, RLU_PREC_F32 = 1 } rlu_precision;
+
+/* Device-resident status written by rlu_factor (the caller reads it after the stream
+ * completes). */
+typedef struct {
+  int32_t status;              /* RLU_OK, or a device-detected failure code            */
+  int32_t first_zero_pivot_y;  /* first step of the LU of Y (step 3) with a zero pivot,
+                                  -1 if none (not an error: getrf semantics)            */
+  int32_t first_zero_pivot_b;  /* same for the column-pivoted LU of B (step 6)          */
+  int32_t nonfinite;           /* nonzero if a NaN or Inf met a pivot search            */
+} rlu_info;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t rlu_version(void);
+
+/* Short static string for a status code. */
+const char* rlu_status_string(int32_t status);
+
+/* Raw Philox4x32-10 stream behind step 1 (Salmon et al., SC'11): for c = 0..n_counters-1
+ * writes the four output words of counter index (first_counter + c) to out[4c .. 4c+3].
+ * Counter words = (index lo32, index hi32, stream_id, 0); key = (seed lo32, seed hi32).
+ * out: device, 4*n_counters uint32. Errors: RLU_EINVAL if out is NULL or n_counters < 0. */
+int32_t rlu_philox_u32(uint64_t seed, uint32_t stream_id, uint64_t first_counter,
+                       int64_t n_counters, uint32_t* out, void* stream);
+
+/* Step 1: the Gaussian matrix G (n x l, column-major, ldg >= n) with i.i.d. N(0,1) entries.
+ * Entry (i, j) is element e = j*n + i of the stream; counter e/4 gives elements
+ * 4c..4c+3 as two Box-Muller pairs (x0,x1) and (x2,x3). dtype RLU_F64: the FP64 transform
+ * (u = (x0+1)/2^32, series logarithm and sine/cosine in IEEE-rounded FP64 operations);
+ * RLU_F32: the same transform in FP32 operations on u = (floor(x0/2^8)+1)/2^24 and the
+ * top 27 bits of x1; RLU_BF16: the FP32 value rounded to nearest even.
+ * Errors: RLU_EINVAL on NULL G, n or l < 0, or ldg < n. */
+int32_t rlu_gaussian(uint64_t seed, uint32_t stream_id, int64_t n, int64_t l,
+                     int32_t dtype, void* G, int64_t ldg, void* stream);
+
+/* Bytes of workspace rlu_factor needs for these sizes and precision (0 if invalid). */
+size_t rlu_workspace_size(int64_t m, int64_t n, int32_t k, int32_t l, int32_t prec);
+
+/* Algorithm 1, steps 1-8: randomized LU of A (m x n, row-major, lda >= n).
+ *   k, l      : 1 <= k <= l <= min(m, n) (Algorithm 1 input; l <= min(m, n) as in the
+ *               lemmas behind Theorem 4.1).
+ *   seed      : Philox key for G (stream id 0).
+ *   P (m), Q (n): int32 gather permutations (outputs).
+ *   L (m x k, column-major, ldl >= m), U (k x n, row-major, ldu >= n): outputs, FP64 for
+ *               RLU_PREC_F64 and FP32 for RLU_PREC_F32.
+ *   info      : device rlu_info (output; may be NULL).
+ *   workspace : device scratch of at least rlu_workspace_size() bytes, 256-byte aligned.
+ * Step 3 is LU with partial pivoting over all l columns (getf2 tie rule: first maximum in
+ * the current row order); step 5 uses the normal equations
+ * L_y^+ = (L_y^T L_y)^{-1} L_y^T (remark after Algorithm 1) with a Cholesky factor of the
+ * k x k Gram matrix in FP64; step 6 pivots on the largest entry of row j of the current
+ * Schur complement and keeps the unit diagonal on L_b.
+ * Errors: RLU_EINVAL (dimensions, NULL pointers, strides), RLU_EUNSUPPORTED (dtype does
+ * not match prec), RLU_ENOMEM (workspace too small), RLU_ECUDA (launch failure). */
+int32_t rlu_factor(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                   int32_t k, int32_t l, uint64_t seed, int32_t prec,
+                   int32_t* P, int32_t* Q, void* L, int64_t ldl, void* U, int64_t ldu,
+                   rlu_info* info, void* workspace, size_t ws_bytes, void* stream);
+
+/* Optional copies of the intermediates of Algorithm 1, for verification, and optional
+ * per-step timing events. Every pointer may be NULL; types follow the path (FP64 or FP32).
+ *   G  : n x l column-major (ld n)      step 1
+ *   Y  : m x l column-major (ld m)      step 2, before the LU
+ *   Ly : m x k column-major (ld m)      step 4, unit lower trapezoidal, pivot row order
+ *   B  : k x n row-major    (ld n)      step 5, before its LU
+ *   events: 2*RLU_NUM_TIMED_STEPS caller-created cudaEvent_t handles (as void*); when
+ *           n_events is large enough, events[2i] and events[2i+1] are recorded right before
+ *           and after timed step i, on the stream that runs it (see rlu_timed_step_name). */
+typedef struct {
+  void* G;
+  void* Y;
+  void* Ly;
+  void* B;
+  void** events;
+  int32_t n_events;
+} rlu_stage_outputs;
+
+/* Timed steps of rlu_factor_stages, in order: 0 gaussian (step 1), 1 Y = A G (step 2),
+ * 2 LU of Y (step 3), 3 L_y / L~ (step 4), 4 Gram (step 5), 5 Cholesky + inverse (step 5,
+ * helper stream), 6 C = L~^T A (step 5), 7 B = R^-1 R^-T C (step 5), 8 LU of B (step 6),
+ * 9 L_b / U gathers (steps 6, 8), 10 L = L_y L_b (step 7). */
+#define RLU_NUM_TIMED_STEPS 11
+
+/* Name of timed step i (static string), or NULL when out of range. */
+const char* rlu_timed_step_name(int32_t i);
+
+/* Number of kernels this library has enqueued since it was loaded (host-side counter,
+ * all devices and threads). */
+uint64_t rlu_launch_count(void);
+
+/* rlu_factor that also writes the intermediates named in ``stages`` (may be NULL, then it
+ * is rlu_factor). Same arguments, errors and workspace. */
+int32_t rlu_factor_stages(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                          int32_t k, int32_t l, uint64_t seed, int32_t prec,
+                          int32_t* P, int32_t* Q, void* L, int64_t ldl, void* U,
+                          int64_t ldu, rlu_info* info, void* workspace, size_t ws_bytes,
+                          const rlu_stage_outputs* stages, void* stream);
+
+/* Bytes of workspace rlu_reconstruct_error needs. */
+size_t rlu_reconstruct_workspace_size(int64_t m, int64_t n, int32_t k);
+
+/* Error of Eq. (1) / Eq. (relErr): R = P A Q - L U with A (m x n) of ``dtype`` and L, U of
+ * ``lu_dtype`` (layouts as in rlu_factor). Writes ||R||_F to err_fro[0] (FP64 sum of
+ * squares of residuals formed in FP64 from the stored values) and, if err_spec is not NULL,
+ * a power-iteration estimate of ||R||_2 after ``power_iters`` steps of x <- R^T R x from a
+ * fixed start vector (a lower bound that converges to ||R||_2) to err_spec[0].
+ * err_fro, err_spec: device doubles. Errors: RLU_EINVAL, RLU_EUNSUPPORTED, RLU_ENOMEM. */
+int32_t rlu_reconstruct_error(const void* A, int32_t dtype, int64_t m, int64_t n,
+                              int64_t lda, int32_t k, const int32_t* P, const int32_t* Q,
+                              const void* L, int64_t ldl, const void* U, int64_t ldu,
+                              int32_t lu_dtype, double* err_fro, double* err_spec,
+                              int32_t power_iters, void* workspace, size_t ws_bytes,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLU_H */

@@ -14,6 +14,7 @@ from .rlu_oracle import (  # noqa: F401
     PHILOX_M0, PHILOX_M1, PHILOX_W0, PHILOX_W1,
     philox4x32_10, philox_stream,
     series_ln, series_sincos_2pi, box_muller, gaussian,
+    box_muller_f32, gaussian_f32,
     lu_partial_pivot, lu_column_pivot, pinv_apply,
     rlu_factor, reconstruct_error, spectral_norm,
     theorem1_constant, theorem1_success_probability, theorem1_failure_terms,

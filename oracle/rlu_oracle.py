@@ -170,6 +170,82 @@ def gaussian(seed: int, stream_id: int, n: int, l: int) -> np.ndarray:
     return flat.reshape(l, n).T.copy()        # column j holds elements j*n .. j*n+n-1
 
 
+_F32 = np.float32
+_LN2_F = np.float32(float.fromhex("0x1.62e430p-1"))    # float nearest ln 2
+_SQRT2_F = np.float32(float.fromhex("0x1.6a09e6p+0"))  # float nearest sqrt 2
+_PI_4_F = np.float32(float.fromhex("0x1.921fb6p-1"))   # float nearest pi/4
+
+
+def _series_coefficients_f32(n_ln=6, n_trig=7):
+    """FP32 coefficient tables, every entry one IEEE-rounded FP32 division:
+    1/(2n+1) for the logarithm; a_n = a_{n-1}/((2n)(2n+1)) (sine) and
+    b_n = b_{n-1}/((2n-1)(2n)) (cosine), signs alternating."""
+    ln = [_F32(1.0) / _F32(2 * n + 1) for n in range(n_ln)]
+    s, c = [_F32(1.0)], [_F32(1.0)]
+    for n in range(1, n_trig):
+        s.append(s[-1] / _F32((2 * n) * (2 * n + 1)))
+        c.append(c[-1] / _F32((2 * n - 1) * (2 * n)))
+    s = [v if n % 2 == 0 else -v for n, v in enumerate(s)]
+    c = [v if n % 2 == 0 else -v for n, v in enumerate(c)]
+    return ln, s, c
+
+
+def box_muller_f32(xa: np.ndarray, xb: np.ndarray):
+    """Box-Muller in FP32 operations only (the generator of the FP32 and BF16 paths):
+    u = (floor(xa/2^8) + 1)/2^24 in (0, 1]; ln u by the atanh series (6 terms);
+    octant q = xb >> 29 and 24-bit fraction (xb >> 5) mod 2^24 (complemented in odd
+    octants) give phi in [0, pi/4]; sine and cosine by 7-term Taylor series.
+    Returns (r cos theta, r sin theta) as float32."""
+    ln_c, sin_c, cos_c = _series_coefficients_f32()
+    xa = np.asarray(xa, dtype=np.uint64)
+    xb = np.asarray(xb, dtype=np.uint64)
+    u = ((xa >> np.uint64(8)).astype(_F32) + _F32(1.0)) * _F32(2.0**-24)
+    mant, ex = np.frexp(u)
+    f = mant * _F32(2.0)
+    e = (ex - 1).astype(_F32)
+    big = f > _SQRT2_F
+    f = np.where(big, mant, f).astype(_F32)
+    e = np.where(big, e + _F32(1.0), e).astype(_F32)
+    s = (f - _F32(1.0)) / (f + _F32(1.0))
+    z = s * s
+    p = np.full_like(z, ln_c[-1])
+    for cf in reversed(ln_c[:-1]):
+        p = p * z + cf
+    lnu = e * _LN2_F + (s * p) * _F32(2.0)
+    r = np.sqrt(lnu * _F32(-2.0))
+    q = (xb >> np.uint64(29)).astype(np.int64)
+    wi = ((xb >> np.uint64(5)) & np.uint64((1 << 24) - 1)).astype(_F32)
+    wi = np.where((q & 1) == 1, _F32(1 << 24) - wi, wi).astype(_F32)
+    phi = _PI_4_F * (wi * _F32(2.0**-24))
+    z = phi * phi
+    sp = np.full_like(z, sin_c[-1])
+    for cf in reversed(sin_c[:-1]):
+        sp = sp * z + cf
+    sin_phi = phi * sp
+    cp = np.full_like(z, cos_c[-1])
+    for cf in reversed(cos_c[:-1]):
+        cp = cp * z + cf
+    cos_phi = cp
+    conds = [q == i for i in range(8)]
+    sin_t = np.select(conds, [sin_phi, cos_phi, cos_phi, sin_phi, -sin_phi, -cos_phi,
+                              -cos_phi, -sin_phi]).astype(_F32)
+    cos_t = np.select(conds, [cos_phi, sin_phi, -sin_phi, -cos_phi, -cos_phi, -sin_phi,
+                              sin_phi, cos_phi]).astype(_F32)
+    return r * cos_t, r * sin_t
+
+
+def gaussian_f32(seed: int, stream_id: int, n: int, l: int) -> np.ndarray:
+    """Step 1 for the FP32 / BF16 paths: same stream and element layout as gaussian(),
+    transform box_muller_f32. Returns float32 (n x l)."""
+    total = n * l
+    nc = (total + 3) // 4
+    words = philox_stream(seed, stream_id, 0, nc).reshape(nc, 4)
+    z0, z1 = box_muller_f32(words[:, 0], words[:, 1])
+    z2, z3 = box_muller_f32(words[:, 2], words[:, 3])
+    flat = np.stack([z0, z1, z2, z3], axis=1).reshape(-1)[:total]
+    return flat.reshape(l, n).T.copy()
+
+
 # ---------------------------------------------------------------------------------------
 # Steps 3 and 6 of Algorithm 1: LU with partial (row) and column pivoting.
 # ---------------------------------------------------------------------------------------

@@ -1,0 +1,22 @@
+// Interface of the cluster LU kernel (see panel_lu.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace rlu {
+
+struct LuArgs {
+  void* X;             // R x C column-major, factored in place
+  int64_t ldx;         // >= R
+  int R, C;            // rows, steps (C <= R)
+  int nb;              // panel width (set by the launcher)
+  int rpc;             // rows per CTA (set by the launcher)
+  int32_t* perm;       // [R] out: row at final position p
+  int32_t* zero_step;  // out: first step with a zero pivot, -1 if none (may be NULL)
+  int32_t* nonfinite;  // out: OR-ed with 1 when a NaN/Inf is met (may be NULL)
+};
+
+// crout = false: Doolittle (step 3, LU of Y); crout = true: pivot row scaled (step 6 on B^T).
+int32_t launch_cluster_lu(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s);
+
+}  // namespace rlu

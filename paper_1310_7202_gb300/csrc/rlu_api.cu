@@ -1,0 +1,346 @@
+// C ABI and host orchestration of Algorithm 1 (randomized LU) on one GB300.
+//
+// rlu_factor enqueues, on the caller's stream:
+//   step 1  G = gaussian(seed)                                   gauss.cu
+//   step 2  Y = A G                                              gemm_simt.cu
+//   step 3  P Y = L_y U_y, partial pivoting, all l steps        panel_lu.cu (Doolittle)
+//   step 4  L_y = first k columns; L~ = P^T L_y                  small.cu build_ly
+//   step 5  M = L~^T L~ (FP64 sum of partial products); fork: R = chol(M), R^{-1} on a
+//           helper stream while C = L~^T A runs; join; B = R^{-1} (R^{-T} C)
+//   step 6  B Q = L_b U_b, column pivoting (LU of B^T)           panel_lu.cu (Crout)
+//   step 7  L = L_y L_b                                          gemm_simt.cu
+//   step 8  U = U_b                                              small.cu gather_lb_u
+#include <atomic>
+#include <mutex>
+
+#include "common.cuh"
+#include "gemm_simt.cuh"
+#include "panel_lu.cuh"
+#include "residual.cuh"
+#include "small.cuh"
+
+namespace rlu {
+
+int32_t launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t n, int64_t l, int32_t dtype,
+                        void* G, int64_t ldg, cudaStream_t s);
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launches(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
+
+static const char* kStepNames[RLU_NUM_TIMED_STEPS] = {
+    "gaussian", "gemm_Y", "lu_Y", "build_Ly", "gram", "chol_inv", "gemm_C", "tri_B", "lu_B",
+    "gather_Lb_U", "gemm_L"};
+
+// Records the start/end event of timed step i when the caller asked for events.
+struct StepTimer {
+  const rlu_stage_outputs* st;
+  int32_t rec(int i, bool end, cudaStream_t s) const {
+    if (!st || !st->events || st->n_events < 2 * RLU_NUM_TIMED_STEPS) return RLU_OK;
+    RLU_CUDA_TRY(cudaEventRecord((cudaEvent_t)st->events[2 * i + (end ? 1 : 0)], s));
+    return RLU_OK;
+  }
+};
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+  int n = 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 1;
+  if (dev >= 0 && dev < 64) cached[dev] = n;
+  return n;
+}
+
+// Helper stream and fork/join events of one device (created on first use).
+struct SideStream {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  std::mutex mu;
+};
+
+static int32_t side_stream(SideStream** out) {
+  static SideStream per_dev[64];
+  int dev = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return RLU_EUNSUPPORTED;
+  SideStream& ss = per_dev[dev];
+  std::lock_guard<std::mutex> lock(ss.mu);
+  if (ss.side == nullptr) {
+    RLU_CUDA_TRY(cudaStreamCreateWithFlags(&ss.side, cudaStreamNonBlocking));
+    RLU_CUDA_TRY(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+    RLU_CUDA_TRY(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+  }
+  *out = &ss;
+  return RLU_OK;
+}
+
+static int split_for(int64_t M, int64_t N, int64_t K, int bm, int bn) {
+  const int64_t tiles = ceil_div(M, bm) * ceil_div(N, bn);
+  const int64_t target = 2 * (int64_t)sm_count();
+  int64_t s = ceil_div(target, tiles);
+  const int64_t kmax = K / 64 > 1 ? K / 64 : 1;  // at least 64 of K per split
+  if (s > kmax) s = kmax;
+  if (s < 1) s = 1;
+  return (int)s;
+}
+
+// Workspace layout of rlu_factor for one size / precision.
+struct Plan {
+  int32_t dt = RLU_F32;
+  size_t esz = 4;
+  int64_t m = 0, n = 0;
+  int k = 0, l = 0;
+  int64_t ldg = 0, ldy = 0, ldl = 0, ldb = 0;
+  int split_y = 1, split_g = 1, split_c = 1;
+  size_t off_G = 0, off_Y = 0, off_Lt = 0, off_Lp = 0, off_M = 0, off_Rinv = 0, off_RinvT = 0,
+         off_C = 0, off_T = 0, off_B = 0, off_Lb = 0, off_part = 0, total = 0;
+};
+
+static size_t carve(size_t& cur, size_t bytes) {
+  const size_t at = cur;
+  cur += (size_t)round_up((int64_t)bytes, 256);
+  return at;
+}
+
+static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p) {
+  if (prec == RLU_PREC_F64) {
+    p.dt = RLU_F64;
+    p.esz = 8;
+  } else if (prec == RLU_PREC_F32) {
+    p.dt = RLU_F32;
+    p.esz = 4;
+  } else {
+    return false;
+  }
+  if (!(k >= 1 && k <= l && l <= m && l <= n)) return false;
+  if (m > INT32_MAX / 2 || n > INT32_MAX / 2) return false;
+  p.m = m; p.n = n; p.k = k; p.l = l;
+  p.ldg = round_up(n, 8);
+  p.ldy = round_up(m, 8);
+  p.ldl = round_up(m, 8);
+  p.ldb = round_up(n, 8);
+  const int bm = gemm_tile_m(p.dt), bn = gemm_tile_n(p.dt);
+  p.split_y = split_for(m, l, n, bm, bn);
+  p.split_g = split_for(k, k, m, bm, bn);
+  if (p.dt == RLU_F32 && p.split_g < 2) p.split_g = 2;  // FP32 partials, FP64 reduction
+  p.split_c = split_for(k, n, m, bm, bn);
+  size_t part = 0;
+  auto upd = [&](size_t b) { part = b > part ? b : part; };
+  if (p.split_y > 1) upd((size_t)p.split_y * m * l * p.esz);
+  upd((size_t)p.split_g * k * k * p.esz);
+  if (p.split_c > 1) upd((size_t)p.split_c * k * n * p.esz);
+  size_t cur = 0;
+  const size_t e = p.esz;
+  p.off_G = carve(cur, (size_t)p.ldg * l * e);
+  p.off_Y = carve(cur, (size_t)p.ldy * l * e);
+  p.off_Lt = carve(cur, (size_t)p.ldl * k * e);
+  p.off_Lp = carve(cur, (size_t)p.ldl * k * e);
+  p.off_M = carve(cur, (size_t)k * k * 8);
+  p.off_Rinv = carve(cur, (size_t)k * k * 8);
+  p.off_RinvT = carve(cur, (size_t)k * k * e);
+  p.off_C = carve(cur, (size_t)k * p.ldb * e);
+  p.off_T = carve(cur, (size_t)k * p.ldb * e);
+  p.off_B = carve(cur, (size_t)k * p.ldb * e);
+  p.off_Lb = carve(cur, (size_t)k * k * e);
+  p.off_part = carve(cur, part);
+  p.total = cur;
+  return true;
+}
+
+template <typename T>
+static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, int32_t* P,
+                        int32_t* Q, T* L, int64_t ldl_out, T* U, int64_t ldu, rlu_info* info,
+                        char* ws, const rlu_stage_outputs* st, cudaStream_t s) {
+  T* G = reinterpret_cast<T*>(ws + p.off_G);
+  T* Y = reinterpret_cast<T*>(ws + p.off_Y);
+  T* Lt = reinterpret_cast<T*>(ws + p.off_Lt);
+  T* Lp = reinterpret_cast<T*>(ws + p.off_Lp);
+  double* M = reinterpret_cast<double*>(ws + p.off_M);
+  double* Rinv = reinterpret_cast<double*>(ws + p.off_Rinv);
+  T* RinvT = reinterpret_cast<T*>(ws + p.off_RinvT);
+  T* Cb = reinterpret_cast<T*>(ws + p.off_C);
+  T* Tb = reinterpret_cast<T*>(ws + p.off_T);
+  T* Bb = reinterpret_cast<T*>(ws + p.off_B);
+  T* Lb = reinterpret_cast<T*>(ws + p.off_Lb);
+  void* part = ws + p.off_part;
+  const int64_t m = p.m, n = p.n;
+  const int k = p.k, l = p.l;
+
+  const StepTimer tm{st};
+  if (info) RLU_TRY(info_init(info, s));
+  // step 1
+  RLU_TRY(tm.rec(0, false, s));
+  RLU_TRY(launch_gaussian(seed, 0, n, l, p.dt, G, p.ldg, s));
+  RLU_TRY(tm.rec(0, true, s));
+  if (st && st->G) RLU_TRY(copy_cm<T>(G, p.ldg, static_cast<T*>(st->G), n, n, l, s));
+  // step 2: Y (m x l, col-major) = A (row-major) * G (col-major)
+  RLU_TRY(tm.rec(1, false, s));
+  {
+    GemmOp op{A, lda, true, G, p.ldg, true, Y, p.ldy, false, m, l, n, p.split_y, part, false};
+    RLU_TRY((gemm_simt<T, T>(op, s)));
+  }
+  RLU_TRY(tm.rec(1, true, s));
+  if (st && st->Y) RLU_TRY(copy_cm<T>(Y, p.ldy, static_cast<T*>(st->Y), m, m, l, s));
+  // step 3
+  RLU_TRY(tm.rec(2, false, s));
+  {
+    LuArgs a{};
+    a.X = Y; a.ldx = p.ldy; a.R = (int)m; a.C = l; a.perm = P;
+    a.zero_step = info ? &info->first_zero_pivot_y : nullptr;
+    a.nonfinite = info ? &info->nonfinite : nullptr;
+    RLU_TRY(launch_cluster_lu(p.dt, false, a, s));
+  }
+  RLU_TRY(tm.rec(2, true, s));
+  // step 4
+  RLU_TRY(tm.rec(3, false, s));
+  RLU_TRY(build_ly<T>(Y, p.ldy, m, k, P, Lt, Lp, p.ldl, s));
+  RLU_TRY(tm.rec(3, true, s));
+  if (st && st->Ly) RLU_TRY(copy_cm<T>(Lp, p.ldl, static_cast<T*>(st->Ly), m, m, k, s));
+  // step 5: Gram M = L~^T L~ in FP64
+  RLU_TRY(tm.rec(4, false, s));
+  {
+    GemmOp op{Lt, p.ldl, true, Lt, p.ldl, true, M, k, true, k, k, m, p.split_g, part, false};
+    RLU_TRY((gemm_simt<T, double>(op, s)));
+  }
+  RLU_TRY(tm.rec(4, true, s));
+  SideStream* ss = nullptr;
+  RLU_TRY(side_stream(&ss));
+  {
+    std::lock_guard<std::mutex> lock(ss->mu);
+    RLU_CUDA_TRY(cudaEventRecord(ss->fork, s));
+    RLU_CUDA_TRY(cudaStreamWaitEvent(ss->side, ss->fork, 0));
+    RLU_TRY(tm.rec(5, false, ss->side));
+    RLU_TRY(chol_inv<T>(M, k, Rinv, RinvT, info ? &info->status : nullptr, ss->side));
+    RLU_TRY(tm.rec(5, true, ss->side));
+    RLU_CUDA_TRY(cudaEventRecord(ss->join, ss->side));
+    // C = L~^T A (k x n, row-major)
+    RLU_TRY(tm.rec(6, false, s));
+    GemmOp op{Lt, p.ldl, true, A, lda, false, Cb, p.ldb, true, k, n, m, p.split_c, part, false};
+    RLU_TRY((gemm_simt<T, T>(op, s)));
+    RLU_TRY(tm.rec(6, true, s));
+    RLU_CUDA_TRY(cudaStreamWaitEvent(s, ss->join, 0));
+  }
+  // T = R^{-T} C ; B = R^{-1} T
+  RLU_TRY(tm.rec(7, false, s));
+  {
+    GemmOp op{RinvT, k, false, Cb, p.ldb, false, Tb, p.ldb, true, k, n, k, 1, nullptr, false};
+    RLU_TRY((gemm_simt<T, T>(op, s)));
+  }
+  {
+    GemmOp op{RinvT, k, true, Tb, p.ldb, false, Bb, p.ldb, true, k, n, k, 1, nullptr, false};
+    RLU_TRY((gemm_simt<T, T>(op, s)));
+  }
+  RLU_TRY(tm.rec(7, true, s));
+  if (st && st->B) RLU_TRY(copy_cm<T>(Bb, p.ldb, static_cast<T*>(st->B), n, n, k, s));
+  // step 6: LU of B^T (n x k, col-major = B row-major), Crout form
+  RLU_TRY(tm.rec(8, false, s));
+  {
+    LuArgs a{};
+    a.X = Bb; a.ldx = p.ldb; a.R = (int)n; a.C = k; a.perm = Q;
+    a.zero_step = info ? &info->first_zero_pivot_b : nullptr;
+    a.nonfinite = info ? &info->nonfinite : nullptr;
+    RLU_TRY(launch_cluster_lu(p.dt, true, a, s));
+  }
+  RLU_TRY(tm.rec(8, true, s));
+  // step 8 (and L_b for step 7)
+  RLU_TRY(tm.rec(9, false, s));
+  RLU_TRY(gather_lb_u<T>(Bb, p.ldb, Q, k, n, Lb, U, ldu, s));
+  RLU_TRY(tm.rec(9, true, s));
+  // step 7: L = L_y L_b
+  RLU_TRY(tm.rec(10, false, s));
+  {
+    GemmOp op{Lp, p.ldl, false, Lb, k, true, L, ldl_out, false, m, k, k, 1, nullptr, false};
+    RLU_TRY((gemm_simt<T, T>(op, s)));
+  }
+  RLU_TRY(tm.rec(10, true, s));
+  return RLU_OK;
+}
+
+static int32_t validate(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                        int32_t k, int32_t l, int32_t prec, const int32_t* P, const int32_t* Q,
+                        const void* L, int64_t ldl, const void* U, int64_t ldu) {
+  if (!A || !P || !Q || !L || !U) return RLU_EINVAL;
+  if (m < 1 || n < 1 || k < 1 || k > l || l > m || l > n) return RLU_EINVAL;
+  if (lda < n || ldl < m || ldu < n) return RLU_EINVAL;
+  if (prec == RLU_PREC_F64 && dtype != RLU_F64) return RLU_EUNSUPPORTED;
+  if (prec == RLU_PREC_F32 && dtype != RLU_F32) return RLU_EUNSUPPORTED;
+  if (prec != RLU_PREC_F64 && prec != RLU_PREC_F32) return RLU_EUNSUPPORTED;
+  return RLU_OK;
+}
+
+}  // namespace rlu
+
+using namespace rlu;
+
+extern "C" int32_t rlu_version(void) { return 100; }
+
+extern "C" const char* rlu_timed_step_name(int32_t i) {
+  return (i >= 0 && i < RLU_NUM_TIMED_STEPS) ? kStepNames[i] : nullptr;
+}
+
+extern "C" uint64_t rlu_launch_count(void) { return g_launches.load(); }
+
+extern "C" const char* rlu_status_string(int32_t status) {
+  switch (status) {
+    case RLU_OK: return "ok";
+    case RLU_EINVAL: return "invalid argument";
+    case RLU_ENOMEM: return "workspace too small";
+    case RLU_EUNSUPPORTED: return "unsupported dtype/precision/size";
+    case RLU_ECUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+extern "C" size_t rlu_workspace_size(int64_t m, int64_t n, int32_t k, int32_t l, int32_t prec) {
+  Plan p;
+  if (!make_plan(m, n, k, l, prec, p)) return 0;
+  return p.total;
+}
+
+extern "C" int32_t rlu_factor_stages(const void* A, int32_t dtype, int64_t m, int64_t n,
+                                     int64_t lda, int32_t k, int32_t l, uint64_t seed,
+                                     int32_t prec, int32_t* P, int32_t* Q, void* L, int64_t ldl,
+                                     void* U, int64_t ldu, rlu_info* info, void* workspace,
+                                     size_t ws_bytes, const rlu_stage_outputs* stages,
+                                     void* stream) {
+  RLU_TRY(validate(A, dtype, m, n, lda, k, l, prec, P, Q, L, ldl, U, ldu));
+  Plan p;
+  if (!make_plan(m, n, k, l, prec, p)) return RLU_EINVAL;
+  if (workspace == nullptr || ws_bytes < p.total) return RLU_ENOMEM;
+  if (((uintptr_t)workspace & 255u) != 0) return RLU_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p.dt == RLU_F64)
+    return factor_t<double>(p, (const double*)A, lda, seed, P, Q, (double*)L, ldl, (double*)U,
+                            ldu, info, (char*)workspace, stages, s);
+  return factor_t<float>(p, (const float*)A, lda, seed, P, Q, (float*)L, ldl, (float*)U, ldu,
+                         info, (char*)workspace, stages, s);
+}
+
+extern "C" int32_t rlu_factor(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                              int32_t k, int32_t l, uint64_t seed, int32_t prec, int32_t* P,
+                              int32_t* Q, void* L, int64_t ldl, void* U, int64_t ldu,
+                              rlu_info* info, void* workspace, size_t ws_bytes, void* stream) {
+  return rlu_factor_stages(A, dtype, m, n, lda, k, l, seed, prec, P, Q, L, ldl, U, ldu, info,
+                           workspace, ws_bytes, nullptr, stream);
+}
+
+extern "C" size_t rlu_reconstruct_workspace_size(int64_t m, int64_t n, int32_t k) {
+  if (m < 1 || n < 1 || k < 1) return 0;
+  return residual_workspace_bytes(m, n, k);
+}
+
+extern "C" int32_t rlu_reconstruct_error(const void* A, int32_t dtype, int64_t m, int64_t n,
+                                         int64_t lda, int32_t k, const int32_t* P,
+                                         const int32_t* Q, const void* L, int64_t ldl,
+                                         const void* U, int64_t ldu, int32_t lu_dtype,
+                                         double* err_fro, double* err_spec, int32_t power_iters,
+                                         void* workspace, size_t ws_bytes, void* stream) {
+  if (!A || !P || !Q || !L || !U || !err_fro) return RLU_EINVAL;
+  if (m < 1 || n < 1 || k < 1 || lda < n || ldl < m || ldu < n || power_iters < 0)
+    return RLU_EINVAL;
+  if (workspace == nullptr || ws_bytes < residual_workspace_bytes(m, n, k)) return RLU_ENOMEM;
+  ResidualArgs a{A, lda, P, Q, L, ldl, U, ldu, m, n, k};
+  return residual_error(dtype, lu_dtype, a, err_fro, err_spec, power_iters, (double*)workspace,
+                        (cudaStream_t)stream);
+}

@@ -1,0 +1,227 @@
+"""Python binding of the C ABI in include/rlu.h (ctypes; argument marshalling only).
+
+Every computation runs in librlu.so's CUDA kernels. PyTorch only provides device memory
+(the tensors passed in and the outputs allocated here) and the current CUDA stream.
+Loading fails loudly if librlu.so has not been built or no CUDA device is present: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librlu.so")
+
+RLU_OK, RLU_EINVAL, RLU_ENOMEM, RLU_EUNSUPPORTED, RLU_ECUDA = 0, 1, 2, 3, 4
+RLU_F64, RLU_F32, RLU_BF16 = 0, 1, 2
+RLU_PREC_F64, RLU_PREC_F32 = 0, 1
+
+PREC_BY_NAME = {"f64": RLU_PREC_F64, "f32": RLU_PREC_F32}
+_DT_OF_TORCH = {torch.float64: RLU_F64, torch.float32: RLU_F32, torch.bfloat16: RLU_BF16}
+_TORCH_OF_PREC = {RLU_PREC_F64: torch.float64, RLU_PREC_F32: torch.float32}
+
+# Every symbol include/rlu.h declares.
+EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian",
+            "rlu_workspace_size", "rlu_factor", "rlu_factor_stages", "rlu_timed_step_name",
+            "rlu_launch_count", "rlu_reconstruct_workspace_size", "rlu_reconstruct_error")
+
+
+class RluError(RuntimeError):
+    pass
+
+
+class _StageOutputs(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("Ly", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("events", ctypes.POINTER(ctypes.c_void_p)),
+                ("n_events", ctypes.c_int32)]
+
+
+NUM_TIMED_STEPS = 11
+
+
+_lib = None
+
+
+def load_library(require_cuda: bool = True) -> ctypes.CDLL:
+    """Load librlu.so and declare the prototypes of include/rlu.h."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RluError(f"{LIB_PATH} is missing: build it with "
+                       "`python -m paper_1310_7202_gb300.build` (no CPU fallback exists)")
+    if require_cuda and not torch.cuda.is_available():
+        raise RluError("librlu needs a CUDA device (sm_103a); none is available")
+    lib = ctypes.CDLL(LIB_PATH)
+    i32, i64, u32, u64, vp, sz = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                  ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t)
+    lib.rlu_version.restype = i32
+    lib.rlu_version.argtypes = []
+    lib.rlu_status_string.restype = ctypes.c_char_p
+    lib.rlu_status_string.argtypes = [i32]
+    lib.rlu_philox_u32.restype = i32
+    lib.rlu_philox_u32.argtypes = [u64, u32, u64, i64, vp, vp]
+    lib.rlu_gaussian.restype = i32
+    lib.rlu_gaussian.argtypes = [u64, u32, i64, i64, i32, vp, i64, vp]
+    lib.rlu_workspace_size.restype = sz
+    lib.rlu_workspace_size.argtypes = [i64, i64, i32, i32, i32]
+    fac = [vp, i32, i64, i64, i64, i32, i32, u64, i32, vp, vp, vp, i64, vp, i64, vp, vp, sz]
+    lib.rlu_factor.restype = i32
+    lib.rlu_factor.argtypes = fac + [vp]
+    lib.rlu_factor_stages.restype = i32
+    lib.rlu_factor_stages.argtypes = fac + [ctypes.POINTER(_StageOutputs), vp]
+    lib.rlu_timed_step_name.restype = ctypes.c_char_p
+    lib.rlu_timed_step_name.argtypes = [i32]
+    lib.rlu_launch_count.restype = ctypes.c_uint64
+    lib.rlu_launch_count.argtypes = []
+    lib.rlu_reconstruct_workspace_size.restype = sz
+    lib.rlu_reconstruct_workspace_size.argtypes = [i64, i64, i32]
+    lib.rlu_reconstruct_error.restype = i32
+    lib.rlu_reconstruct_error.argtypes = [vp, i32, i64, i64, i64, i32, vp, vp, vp, i64, vp, i64,
+                                          i32, vp, vp, i32, vp, sz, vp]
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str) -> None:
+    if status != RLU_OK:
+        msg = _lib.rlu_status_string(status).decode() if _lib else str(status)
+        raise RluError(f"{what} failed: {msg} (status {status})")
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def philox_u32(seed: int, stream_id: int, first_counter: int, n_counters: int,
+               stream=None) -> torch.Tensor:
+    """Raw Philox4x32-10 words (int32 tensor holding the uint32 bit patterns)."""
+    lib = load_library()
+    out = torch.empty(4 * max(n_counters, 1), dtype=torch.int32, device="cuda")
+    _check(lib.rlu_philox_u32(seed, stream_id, first_counter, n_counters, _dev_ptr(out),
+                              _stream_ptr(stream)), "rlu_philox_u32")
+    return out[: 4 * n_counters]
+
+
+def gaussian(seed: int, stream_id: int, n: int, l: int, dtype=torch.float64,
+             stream=None) -> torch.Tensor:
+    """Step 1: G (n x l) as an (n, l) tensor with column-major storage."""
+    lib = load_library()
+    store = torch.empty((l, n), dtype=dtype, device="cuda")
+    _check(lib.rlu_gaussian(seed, stream_id, n, l, _DT_OF_TORCH[dtype], _dev_ptr(store), n,
+                            _stream_ptr(stream)), "rlu_gaussian")
+    return store.t()
+
+
+def workspace_size(m: int, n: int, k: int, l: int, prec: int) -> int:
+    return int(load_library().rlu_workspace_size(m, n, k, l, prec))
+
+
+def _colmajor(rows: int, cols: int, dtype) -> torch.Tensor:
+    return torch.empty((cols, rows), dtype=dtype, device="cuda").t()
+
+
+class Factorizer:
+    """Reusable buffers (outputs, workspace, info) for repeated rlu_factor calls of one
+    size and precision."""
+
+    def __init__(self, m: int, n: int, k: int, l: int, prec: int | str = RLU_PREC_F32):
+        self.lib = load_library()
+        self.prec = PREC_BY_NAME[prec] if isinstance(prec, str) else int(prec)
+        self.m, self.n, self.k, self.l = m, n, k, l
+        dt = _TORCH_OF_PREC[self.prec]
+        self.dtype = dt
+        ws = self.lib.rlu_workspace_size(m, n, k, l, self.prec)
+        if ws == 0:
+            raise RluError(f"invalid sizes m={m} n={n} k={k} l={l} prec={self.prec}")
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device="cuda")
+        self.P = torch.empty(m, dtype=torch.int32, device="cuda")
+        self.Q = torch.empty(n, dtype=torch.int32, device="cuda")
+        self.L = _colmajor(m, k, dt)
+        self.U = torch.empty((k, n), dtype=dt, device="cuda")
+        self.info = torch.empty(4, dtype=torch.int32, device="cuda")
+
+    def __call__(self, A: torch.Tensor, seed: int, stages: dict | None = None, stream=None):
+        """Enqueue rlu_factor(A) on the current stream; returns (P, Q, L, U, info)."""
+        m, n, k, l = self.m, self.n, self.k, self.l
+        if A.shape != (m, n) or A.stride(1) != 1 or A.device.type != "cuda":
+            raise RluError("A must be a row-major (m, n) CUDA tensor")
+        dt = _DT_OF_TORCH[A.dtype]
+        args = [_dev_ptr(A), dt, m, n, A.stride(0), k, l, seed, self.prec,
+                _dev_ptr(self.P), _dev_ptr(self.Q), _dev_ptr(self.L), self.L.stride(1),
+                _dev_ptr(self.U), self.U.stride(0), _dev_ptr(self.info),
+                _dev_ptr(self.workspace), self.workspace.numel()]
+        if stages is None:
+            st = self.lib.rlu_factor(*args, _stream_ptr(stream))
+        else:
+            ev = stages.get("events")
+            ev_arr, n_ev = None, 0
+            if ev is not None:
+                ev_arr = (ctypes.c_void_p * len(ev))(*[int(e.cuda_event) for e in ev])
+                n_ev = len(ev)
+            so = _StageOutputs(_dev_ptr(stages.get("G")), _dev_ptr(stages.get("Y")),
+                               _dev_ptr(stages.get("Ly")), _dev_ptr(stages.get("B")),
+                               ctypes.cast(ev_arr, ctypes.POINTER(ctypes.c_void_p))
+                               if ev_arr is not None else None, n_ev)
+            st = self.lib.rlu_factor_stages(*args, ctypes.byref(so), _stream_ptr(stream))
+        _check(st, "rlu_factor")
+        return self.P, self.Q, self.L, self.U, self.info
+
+    def stage_buffers(self) -> dict:
+        """Column-/row-major tensors laid out as rlu_stage_outputs expects."""
+        m, n, k, l, dt = self.m, self.n, self.k, self.l, self.dtype
+        return {"G": _colmajor(n, l, dt), "Y": _colmajor(m, l, dt), "Ly": _colmajor(m, k, dt),
+                "B": torch.empty((k, n), dtype=dt, device="cuda")}
+
+
+def factor(A: torch.Tensor, k: int, l: int, seed: int, prec: int | str | None = None,
+           stages: bool = False) -> dict:
+    """One randomized LU of A (CUDA tensor, row-major). Returns P, Q, L, U, info (device
+    tensors) and, with ``stages=True``, the intermediates G, Y, Ly, B."""
+    if prec is None:
+        prec = RLU_PREC_F64 if A.dtype == torch.float64 else RLU_PREC_F32
+    f = Factorizer(A.shape[0], A.shape[1], k, l, prec)
+    st = f.stage_buffers() if stages else None
+    P, Q, L, U, info = f(A, seed, stages=st)
+    out = {"P": P, "Q": Q, "L": L, "U": U, "info": info}
+    if st:
+        out.update(st)
+    return out
+
+
+def timed_step_names() -> list[str]:
+    lib = load_library(require_cuda=False)
+    return [lib.rlu_timed_step_name(i).decode() for i in range(NUM_TIMED_STEPS)]
+
+
+def launch_count() -> int:
+    return int(load_library(require_cuda=False).rlu_launch_count())
+
+
+def reconstruct_error(A: torch.Tensor, P: torch.Tensor, Q: torch.Tensor, L: torch.Tensor,
+                      U: torch.Tensor, power_iters: int = 0, stream=None):
+    """(||PAQ - LU||_F, ||PAQ - LU||_2 estimate or None) as device FP64 scalars."""
+    lib = load_library()
+    m, n = A.shape
+    k = L.shape[1]
+    if L.stride(0) != 1 or U.stride(1) != 1 or A.stride(1) != 1:
+        raise RluError("L must be column-major, U and A row-major")
+    ws = torch.empty(lib.rlu_reconstruct_workspace_size(m, n, k), dtype=torch.uint8,
+                     device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    spec_ptr = _dev_ptr(out) + 8 if power_iters > 0 else None
+    _check(lib.rlu_reconstruct_error(_dev_ptr(A), _DT_OF_TORCH[A.dtype], m, n, A.stride(0), k,
+                                     _dev_ptr(P), _dev_ptr(Q), _dev_ptr(L), L.stride(1),
+                                     _dev_ptr(U), U.stride(0), _DT_OF_TORCH[L.dtype],
+                                     _dev_ptr(out), spec_ptr, power_iters, _dev_ptr(ws),
+                                     ws.numel(), _stream_ptr(stream)),
+           "rlu_reconstruct_error")
+    return out[0], (out[1] if power_iters > 0 else None)

@@ -86,7 +86,18 @@ def prescribed_matrix_torch(m: int, n: int, sigma: np.ndarray, seed_u: int, seed
     return A.to(dtype).contiguous()
 
 
-# The workloads, by size, spectrum and storage (see the design doc for the recipe).
+def lowrank_plus_noise(m: int, n: int, r: int, noise: float, seed: int,
+                       dtype=np.float64) -> np.ndarray:
+    """A = X diag(0.8^i) W^T + noise * E with Gaussian X (m x r), W (n x r), E (m x n):
+    a fast (QR-free) decaying-spectrum matrix for large parity cases."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((m, r))
+    W = rng.standard_normal((n, r))
+    A = (X * 0.8 ** np.arange(r)) @ W.T / np.sqrt(n) + noise * rng.standard_normal((m, n))
+    return np.ascontiguousarray(A.astype(dtype))
+
+
+# The benchmark workloads: size, spectrum, storage and seeds.
 WORKLOADS = {
     "fp64_512": dict(m=512, n=512, k=20, l=25, spectrum="two_level", dtype="f64",
                      seed_u=11, seed_v=12, seed_g=1),

@@ -335,3 +335,37 @@ def test_check_dims():
     for bad in [(10, 8, 0, 3), (10, 8, 4, 3), (10, 8, 3, 9), (5, 8, 3, 6)]:
         with pytest.raises(ValueError):
             O.check_dims(*bad)
+
+
+# ----------------------------------------------------------------------------------------
+# The FP32 transform of the FP32 / BF16 paths against libm and the distribution.
+# ----------------------------------------------------------------------------------------
+
+def test_box_muller_f32_matches_libm():
+    rng = np.random.default_rng(11)
+    xa = rng.integers(0, 2**32, size=200000, dtype=np.uint64)
+    xb = rng.integers(0, 2**32, size=200000, dtype=np.uint64)
+    xa[:4] = [0, 255, 2**32 - 1, 2**31]
+    xb[:4] = [0, 2**29, 2**32 - 1, 3 * 2**29 + 31]
+    z0, z1 = O.box_muller_f32(xa, xb)
+    assert z0.dtype == np.float32 and z1.dtype == np.float32
+    u = ((xa >> 8).astype(np.float64) + 1.0) * 2.0**-24
+    r = np.sqrt(-2.0 * np.log(u))
+    th = 2.0 * np.pi * ((xb >> 5).astype(np.float64) * 2.0**-27)
+    # a few float32 ulps of r (r <= 5.8)
+    assert np.max(np.abs(z0 - r * np.cos(th))) < 8 * np.spacing(np.float32(6.0))
+    assert np.max(np.abs(z1 - r * np.sin(th))) < 8 * np.spacing(np.float32(6.0))
+
+
+def test_gaussian_f32_distribution_and_layout():
+    G = O.gaussian_f32(77, 0, 1000, 1000)
+    assert G.dtype == np.float32
+    z = G.T.reshape(-1).astype(np.float64)
+    N = z.size
+    assert abs(z.mean()) < 5.0 / math.sqrt(N)
+    assert abs(z.var() - 1.0) < 5.0 * math.sqrt(2.0 / N)
+    assert st.kstest(z, "norm").pvalue > 1e-3
+    # close to the FP64 transform of the same words (both are N(0,1) samples of the
+    # same uniforms, up to the FP32 uniform's 24-bit resolution)
+    G64 = O.gaussian(77, 0, 1000, 1000)
+    assert np.median(np.abs(G - G64)) < 1e-5
