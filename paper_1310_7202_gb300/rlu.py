@@ -165,6 +165,9 @@ class Factorizer:
             ev = stages.get("events")
             ev_arr, n_ev = None, 0
             if ev is not None:
+                for e in ev:  # torch creates the CUDA event on its first record
+                    if int(e.cuda_event) == 0:
+                        e.record()
                 ev_arr = (ctypes.c_void_p * len(ev))(*[int(e.cuda_event) for e in ev])
                 n_ev = len(ev)
             so = _StageOutputs(_dev_ptr(stages.get("G")), _dev_ptr(stages.get("Y")),
