@@ -161,6 +161,24 @@ int32_t rlu_reconstruct_error(const void* A, int32_t dtype, int64_t m, int64_t n
                               int32_t power_iters, void* workspace, size_t ws_bytes,
                               void* stream);
 
+/* rlu_reconstruct_error without a workspace argument. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory themselves (a host
+ * framework that owns all device memory through its own pool, or a path where a cudaMalloc
+ * or cudaFree would synchronise the device). Its scratch is a fixed 8 MiB array in the
+ * library's device memory, present on every GPU that loads the library until the process
+ * exits; it makes no allocating call. The first call on a device looks up that array's
+ * address (with the device current): make it before any stream capture. Problems needing
+ * more than 8 MiB of scratch (rlu_reconstruct_workspace_size() > 8 MiB) return RLU_ENOMEM
+ * before anything is enqueued. All calls share the array: calls that overlap on the GPU
+ * race, so order them (one stream, or events). Other arguments, outputs and errors as in
+ * rlu_reconstruct_error. */
+int32_t rlu_reconstruct_error_static(const void* A, int32_t dtype, int64_t m, int64_t n,
+                                     int64_t lda, int32_t k, const int32_t* P,
+                                     const int32_t* Q, const void* L, int64_t ldl,
+                                     const void* U, int64_t ldu, int32_t lu_dtype,
+                                     double* err_fro, double* err_spec, int32_t power_iters,
+                                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

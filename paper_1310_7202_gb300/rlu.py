@@ -26,7 +26,8 @@ _TORCH_OF_PREC = {RLU_PREC_F64: torch.float64, RLU_PREC_F32: torch.float32}
 # Every symbol include/rlu.h declares.
 EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian",
             "rlu_workspace_size", "rlu_factor", "rlu_factor_stages", "rlu_timed_step_name",
-            "rlu_launch_count", "rlu_reconstruct_workspace_size", "rlu_reconstruct_error")
+            "rlu_launch_count", "rlu_reconstruct_workspace_size", "rlu_reconstruct_error",
+            "rlu_reconstruct_error_static")
 
 
 class RluError(RuntimeError):
@@ -82,6 +83,9 @@ def load_library(require_cuda: bool = True) -> ctypes.CDLL:
     lib.rlu_reconstruct_error.restype = i32
     lib.rlu_reconstruct_error.argtypes = [vp, i32, i64, i64, i64, i32, vp, vp, vp, i64, vp, i64,
                                           i32, vp, vp, i32, vp, sz, vp]
+    lib.rlu_reconstruct_error_static.restype = i32
+    lib.rlu_reconstruct_error_static.argtypes = [vp, i32, i64, i64, i64, i32, vp, vp, vp, i64,
+                                                 vp, i64, i32, vp, vp, i32, vp]
     _lib = lib
     return lib
 
@@ -227,4 +231,25 @@ def reconstruct_error(A: torch.Tensor, P: torch.Tensor, Q: torch.Tensor, L: torc
                                      _dev_ptr(out), spec_ptr, power_iters, _dev_ptr(ws),
                                      ws.numel(), _stream_ptr(stream)),
            "rlu_reconstruct_error")
+    return out[0], (out[1] if power_iters > 0 else None)
+
+
+def reconstruct_error_static(A: torch.Tensor, P: torch.Tensor, Q: torch.Tensor,
+                             L: torch.Tensor, U: torch.Tensor, power_iters: int = 0,
+                             stream=None):
+    """reconstruct_error without a workspace: the library's fixed 8 MiB device scratch is
+    used instead, for callers that must not allocate device memory (only the two-double
+    result tensor is allocated here, by this Python convenience wrapper)."""
+    lib = load_library()
+    m, n = A.shape
+    k = L.shape[1]
+    if L.stride(0) != 1 or U.stride(1) != 1 or A.stride(1) != 1:
+        raise RluError("L must be column-major, U and A row-major")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    spec_ptr = _dev_ptr(out) + 8 if power_iters > 0 else None
+    _check(lib.rlu_reconstruct_error_static(
+        _dev_ptr(A), _DT_OF_TORCH[A.dtype], m, n, A.stride(0), k, _dev_ptr(P), _dev_ptr(Q),
+        _dev_ptr(L), L.stride(1), _dev_ptr(U), U.stride(0), _DT_OF_TORCH[L.dtype],
+        _dev_ptr(out), spec_ptr, power_iters, _stream_ptr(stream)),
+        "rlu_reconstruct_error_static")
     return out[0], (out[1] if power_iters > 0 else None)
