@@ -37,7 +37,9 @@ typedef enum {
   RLU_EINVAL = 1,        /* an argument is out of range, NULL or misaligned */
   RLU_ENOMEM = 2,        /* workspace smaller than *_workspace_size() */
   RLU_EUNSUPPORTED = 3,  /* dtype / precision combination not provided */
-  RLU_ECUDA = 4          /* a CUDA runtime call failed (launch, attribute, event) */
+  RLU_ECUDA = 4,         /* a CUDA runtime call failed (launch, attribute, event) */
+  RLU_ETIMEOUT = 5       /* device side only (rlu_info.status): a wait between the CTAs of
+                            a cluster gave up after about one second; results are invalid */
 } rlu_status;
 
 typedef enum { RLU_F64 = 0, RLU_F32 = 1, RLU_BF16 = 2 } rlu_dtype;

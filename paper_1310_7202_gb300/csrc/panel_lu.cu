@@ -366,6 +366,9 @@ static int32_t launch_lu_t(const LuArgs& in, cudaStream_t s) {
 
 int32_t launch_cluster_lu(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s) {
   if (a.R < a.C || a.C < 1) return RLU_EINVAL;
+  bool launched = false;
+  RLU_TRY(launch_lu_reg(dtype, crout, a, s, &launched));
+  if (launched) return RLU_OK;
   if (dtype == RLU_F64) return crout ? launch_lu_t<double, true>(a, s) : launch_lu_t<double, false>(a, s);
   if (dtype == RLU_F32) return crout ? launch_lu_t<float, true>(a, s) : launch_lu_t<float, false>(a, s);
   return RLU_EUNSUPPORTED;

@@ -14,9 +14,13 @@ struct LuArgs {
   int32_t* perm;       // [R] out: row at final position p
   int32_t* zero_step;  // out: first step with a zero pivot, -1 if none (may be NULL)
   int32_t* nonfinite;  // out: OR-ed with 1 when a NaN/Inf is met (may be NULL)
+  int32_t* status;     // out: set to RLU_ETIMEOUT if a cluster wait gave up (may be NULL)
 };
 
 // crout = false: Doolittle (step 3, LU of Y); crout = true: pivot row scaled (step 6 on B^T).
 int32_t launch_cluster_lu(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s);
+
+// Register-resident variant (lu_reg.cu); *launched is false when the shape does not fit it.
+int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s, bool* launched);
 
 }  // namespace rlu

@@ -67,7 +67,11 @@ static int32_t side_stream(SideStream** out) {
   SideStream& ss = per_dev[dev];
   std::lock_guard<std::mutex> lock(ss.mu);
   if (ss.side == nullptr) {
-    RLU_CUDA_TRY(cudaStreamCreateWithFlags(&ss.side, cudaStreamNonBlocking));
+    // highest priority: the Cholesky cluster must get its SMs before the concurrent GEMM
+    // fills the GPU, otherwise it only starts when that GEMM drains
+    int lo = 0, hi = 0;
+    RLU_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    RLU_CUDA_TRY(cudaStreamCreateWithPriority(&ss.side, cudaStreamNonBlocking, hi));
     RLU_CUDA_TRY(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
     RLU_CUDA_TRY(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
   }
@@ -137,7 +141,7 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   p.off_Lt = carve(cur, (size_t)p.ldl * k * e);
   p.off_Lp = carve(cur, (size_t)p.ldl * k * e);
   p.off_M = carve(cur, (size_t)k * k * 8);
-  p.off_Rinv = carve(cur, (size_t)k * k * 8);
+  p.off_Rinv = carve(cur, (size_t)k * (k + 1) * 8);  // R^{-1} and 1/diag(L)
   p.off_RinvT = carve(cur, (size_t)k * k * e);
   p.off_C = carve(cur, (size_t)k * p.ldb * e);
   p.off_T = carve(cur, (size_t)k * p.ldb * e);
@@ -189,6 +193,7 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
     a.X = Y; a.ldx = p.ldy; a.R = (int)m; a.C = l; a.perm = P;
     a.zero_step = info ? &info->first_zero_pivot_y : nullptr;
     a.nonfinite = info ? &info->nonfinite : nullptr;
+    a.status = info ? &info->status : nullptr;
     RLU_TRY(launch_cluster_lu(p.dt, false, a, s));
   }
   RLU_TRY(tm.rec(2, true, s));
@@ -240,6 +245,7 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
     a.X = Bb; a.ldx = p.ldb; a.R = (int)n; a.C = k; a.perm = Q;
     a.zero_step = info ? &info->first_zero_pivot_b : nullptr;
     a.nonfinite = info ? &info->nonfinite : nullptr;
+    a.status = info ? &info->status : nullptr;
     RLU_TRY(launch_cluster_lu(p.dt, true, a, s));
   }
   RLU_TRY(tm.rec(8, true, s));
@@ -288,6 +294,7 @@ extern "C" const char* rlu_status_string(int32_t status) {
     case RLU_ENOMEM: return "workspace too small";
     case RLU_EUNSUPPORTED: return "unsupported dtype/precision/size";
     case RLU_ECUDA: return "CUDA runtime error";
+    case RLU_ETIMEOUT: return "device-side wait timed out";
     default: return "unknown status";
   }
 }

@@ -3,10 +3,13 @@
 //  * build_ly (steps 4-5): from the swap-free factored Y and its position map, L_y in pivot
 //    row order (Lp, for step 7) and L~ = P^T L_y in original row order (Lt, so that
 //    L_y^T P A = L~^T A without permuting A).
-//  * chol_inv (step 5, remark after Algorithm 1): M = L_y^T L_y = R^T R (FP64 Cholesky,
-//    upper R), then R^{-1} by back substitution; written in FP64 and in the path's type.
+//  * chol_inv (step 5, remark after Algorithm 1): M = L_y^T L_y = L L^T (FP64 Cholesky on a
+//    thread-block cluster), then R^{-1} = L^{-T} (R = L^T) by forward substitution, one warp
+//    per column; written in FP64 and in the path's type.
 //  * gather_lb / gather_u (steps 6 and 8): L_b and U_b read out of the swap-free factored
 //    B^T with the column permutation Q.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "small.cuh"
 
@@ -40,55 +43,199 @@ template int32_t build_ly<float>(const float*, int64_t, int64_t, int, const int3
 template int32_t build_ly<double>(const double*, int64_t, int64_t, int, const int32_t*, double*,
                                   double*, int64_t, cudaStream_t);
 
-// One CTA. M (k x k, row-major, FP64) is overwritten by R in its upper triangle.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_chol_inv(double* __restrict__ M, int k,
-                                                   double* __restrict__ Rinv,
-                                                   T* __restrict__ RinvT,
-                                                   int32_t* __restrict__ status) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+// Cholesky M = L L^T (FP64) on one thread-block cluster. M (k x k, row-major, global) is
+// read once; block columns of width CB are dealt round-robin to the cluster's CTAs and kept
+// in their shared memory. Block step J: the owner factors its panel (rows >= CB*J), one
+// cluster barrier, every CTA copies that panel from the owner's shared memory and applies
+// the rank-CB update to the block columns it owns. L (lower) is written back over M.
+static constexpr int CH_CB = 8;
+static constexpr int CH_NT = 256;
+
+// 1/sqrt(d) in FP64 without the long-latency FP64 sqrt and divide: an FP32 seed refined by
+// two Newton steps y <- y + y/2 (1 - d y^2) (error ~2^-23 -> ~2^-46 -> rounding level).
+// Magnitudes outside the FP32 range take the IEEE path.
+__device__ __forceinline__ double rsqrt_fp64(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double r = fma(-d * y, y, 1.0);
+    y = fma(0.5 * y, r, y);
+  }
+  return y;
+}
+
+__global__ void __launch_bounds__(CH_NT, 1) k_chol_cluster(double* __restrict__ M, int k,
+                                                         double* __restrict__ rdiag,
+                                                         int32_t* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int nc = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  const int nblk = (k + CH_CB - 1) / CH_CB;
+  const int mine = (nblk - me + nc - 1) / nc;  // number of block columns this CTA owns
+  extern __shared__ __align__(16) double ch_smem[];
+  double* panels = ch_smem;                              // [mine][k][CB]
+  double* buf = ch_smem + (size_t)mine * k * CH_CB;      // [k][CB] copy of the current panel
   __shared__ int s_bad;
   if (tid == 0) s_bad = 0;
-  __syncthreads();
-  for (int j = 0; j < k; ++j) {
-    const double d = M[(int64_t)j * k + j];
-    if (!(d > 0.0)) {
-      if (tid == 0) s_bad = 1;
+  for (int q = 0; q < mine; ++q) {
+    const int J = me + q * nc;
+    double* P = panels + (size_t)q * k * CH_CB;
+    for (int e = tid; e < k * CH_CB; e += CH_NT) {
+      const int i = e / CH_CB, c = e % CH_CB, col = J * CH_CB + c;
+      P[e] = (col < k && i >= J * CH_CB) ? M[(int64_t)i * k + col] : 0.0;
     }
-    const double r = d > 0.0 ? sqrt(d) : 1.0;
-    __syncthreads();
-    for (int c = j + 1 + tid; c < k; c += nt) M[(int64_t)j * k + c] /= r;
-    __syncthreads();
-    if (tid == 0) M[(int64_t)j * k + j] = r;
-    const int w = k - j - 1;
-    for (int64_t e = tid; e < (int64_t)w * w; e += nt) {
-      const int a = (int)(e / w), b = (int)(e % w);
-      if (b < a) continue;  // upper triangle of the trailing block only
-      const int i = j + 1 + a, c = j + 1 + b;
-      M[(int64_t)i * k + c] -= M[(int64_t)j * k + i] * M[(int64_t)j * k + c];
-    }
-    __syncthreads();
   }
-  // R^{-1}: column c solves R x = e_c by back substitution (one thread per column)
-  for (int c = tid; c < k; c += nt) {
-    for (int i = k - 1; i >= 0; --i) {
-      double v = 0.0;
-      if (i <= c) {
-        double s = (i == c) ? 1.0 : 0.0;
-        for (int t = i + 1; t <= c; ++t) s -= M[(int64_t)i * k + t] * Rinv[(int64_t)t * k + c];
-        v = s / M[(int64_t)i * k + i];
+  cl.sync();
+  for (int J = 0; J < nblk; ++J) {
+    const int j0 = J * CH_CB, bw = min(CH_CB, k - j0);
+    if (J % nc == me) {
+      double* P = panels + (size_t)(J / nc) * k * CH_CB;
+      for (int t = 0; t < bw; ++t) {
+        const double d = P[(j0 + t) * CH_CB + t];
+        if (!(d > 0.0) && tid == 0) s_bad = 1;
+        const double inv = d > 0.0 ? rsqrt_fp64(d) : 1.0;  // 1 / L[j0+t][j0+t]
+        const double r = d > 0.0 ? d * inv : 1.0;          // L[j0+t][j0+t]
+        __syncthreads();
+        for (int i = j0 + t + 1 + tid; i < k; i += CH_NT) P[i * CH_CB + t] *= inv;
+        if (tid == 0) {
+          P[(j0 + t) * CH_CB + t] = r;
+          rdiag[j0 + t] = inv;
+        }
+        __syncthreads();
+        const int rows = k - (j0 + t + 1), cols = bw - t - 1;
+        for (int e = tid; e < rows * cols; e += CH_NT) {
+          const int i = j0 + t + 1 + e / cols, c = t + 1 + e % cols;
+          P[i * CH_CB + c] -= P[i * CH_CB + t] * P[(j0 + c) * CH_CB + t];
+        }
+        __syncthreads();
       }
-      Rinv[(int64_t)i * k + c] = v;
+    }
+    cl.sync();
+    {
+      const double* src = cl.map_shared_rank(panels + (size_t)(J / nc) * k * CH_CB, J % nc);
+      for (int e = j0 * CH_CB + tid; e < k * CH_CB; e += CH_NT) buf[e] = src[e];
+    }
+    __syncthreads();
+    for (int q = 0; q < mine; ++q) {
+      const int K = me + q * nc;
+      if (K <= J) continue;
+      double* P = panels + (size_t)q * k * CH_CB;
+      const int k0 = K * CH_CB, kw = min(CH_CB, k - k0);
+      const int rows = k - k0;
+      for (int e = tid; e < rows * kw; e += CH_NT) {
+        const int i = k0 + e / kw, c = e % kw;
+        double acc = P[i * CH_CB + c];
+#pragma unroll
+        for (int t = 0; t < CH_CB; ++t)
+          if (t < bw) acc = fma(-buf[i * CH_CB + t], buf[(k0 + c) * CH_CB + t], acc);
+        P[i * CH_CB + c] = acc;
+      }
+    }
+    __syncthreads();  // the next owner reads its freshly updated panel
+  }
+  cl.sync();
+  for (int q = 0; q < mine; ++q) {
+    const int J = me + q * nc;
+    const double* P = panels + (size_t)q * k * CH_CB;
+    for (int e = tid; e < k * CH_CB; e += CH_NT) {
+      const int i = e / CH_CB, c = e % CH_CB, col = J * CH_CB + c;
+      if (col < k) M[(int64_t)i * k + col] = (i >= col) ? P[e] : 0.0;
     }
   }
-  __syncthreads();
-  for (int64_t e = tid; e < (int64_t)k * k; e += nt) RinvT[e] = (T)Rinv[e];
   if (tid == 0 && s_bad && status) *status = RLU_EINVAL;
+  cl.sync();
+}
+
+// R^{-1} = L^{-T}: one warp per column j of L^{-1} (forward substitution over i >= j, the
+// dot products split across the lanes and summed by shuffles, the diagonal applied as the
+// reciprocal computed by the Cholesky); row j of R^{-1} is column j of L^{-1}. Written in
+// FP64 (Rinv) and in the path's type (RinvT), both row-major k x k. When the packed lower
+// triangle fits, every CTA first copies it into shared memory.
+static constexpr int TI_WARPS = 8;
+
+template <typename T, bool PACKED>
+__global__ void __launch_bounds__(TI_WARPS * 32) k_tri_inverse(const double* __restrict__ Lm,
+                                                              const double* __restrict__ rdiag,
+                                                              int k, double* __restrict__ Rinv,
+                                                              T* __restrict__ RinvT) {
+  extern __shared__ double ti_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * TI_WARPS + warp;
+  double* Lp = ti_smem;                                            // packed rows (PACKED)
+  double* xs = ti_smem + (PACKED ? (size_t)k * (k + 1) / 2 : 0) + (size_t)warp * k;
+  if (PACKED) {
+    for (int i = 0; i < k; ++i) {
+      const size_t base = (size_t)i * (i + 1) / 2;
+      for (int t = threadIdx.x; t <= i; t += TI_WARPS * 32) Lp[base + t] = Lm[(int64_t)i * k + t];
+    }
+    __syncthreads();
+  }
+  if (j >= k) return;
+  for (int i = lane; i < j; i += 32) {
+    Rinv[(int64_t)j * k + i] = 0.0;
+    RinvT[(int64_t)j * k + i] = T(0);
+  }
+  for (int i = j; i < k; ++i) {
+    const double* row = PACKED ? Lp + (size_t)i * (i + 1) / 2 : Lm + (int64_t)i * k;
+    double s = 0.0;
+    for (int t = j + lane; t < i; t += 32) s = fma(row[t], xs[t], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const double xi = ((i == j) ? 1.0 - s : -s) * rdiag[i];
+    if (lane == 0) {
+      xs[i] = xi;
+      Rinv[(int64_t)j * k + i] = xi;
+      RinvT[(int64_t)j * k + i] = (T)xi;
+    }
+    __syncwarp();
+  }
 }
 
 template <typename T>
 int32_t chol_inv(double* M, int k, double* Rinv, T* RinvT, int32_t* status, cudaStream_t s) {
-  k_chol_inv<T><<<1, 1024, 0, s>>>(M, k, Rinv, RinvT, status);
+  double* rdiag = Rinv + (size_t)k * k;  // k extra doubles after R^{-1}
+  const int nblk = (k + CH_CB - 1) / CH_CB;
+  int nc = nblk < 16 ? nblk : 16;
+  int dev = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  int optin = 0;
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  auto bytes_for = [&](int c) {
+    const int mine = (nblk + c - 1) / c;
+    return (size_t)(mine + 1) * k * CH_CB * sizeof(double);
+  };
+  while (nc < 16 && bytes_for(nc) + 1024 > (size_t)optin) ++nc;
+  const size_t bytes = bytes_for(nc);
+  if (bytes + 1024 > (size_t)optin) return RLU_EUNSUPPORTED;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(nc);
+  cfg.blockDim = dim3(CH_NT);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_chol_cluster, M, k, rdiag, status));
+  RLU_TRY(last_launch_status());
+  const size_t xbytes = (size_t)TI_WARPS * k * sizeof(double);
+  const size_t pbytes = (size_t)k * (k + 1) / 2 * sizeof(double) + xbytes;
+  const unsigned grid = (unsigned)ceil_div(k, TI_WARPS);
+  if (pbytes + 1024 <= (size_t)optin) {
+    RLU_CUDA_TRY(cudaFuncSetAttribute(k_tri_inverse<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pbytes));
+    k_tri_inverse<T, true><<<grid, TI_WARPS * 32, pbytes, s>>>(M, rdiag, k, Rinv, RinvT);
+  } else {
+    if (xbytes > 48 * 1024)
+      RLU_CUDA_TRY(cudaFuncSetAttribute(k_tri_inverse<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xbytes));
+    k_tri_inverse<T, false><<<grid, TI_WARPS * 32, xbytes, s>>>(M, rdiag, k, Rinv, RinvT);
+  }
   return last_launch_status();
 }
 template int32_t chol_inv<float>(double*, int, double*, float*, int32_t*, cudaStream_t);

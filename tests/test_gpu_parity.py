@@ -102,6 +102,8 @@ def test_fp64_deterministic(fp64_512):
     (300, 20000, 30, 40),      # B^T needs several panels (Crout form)
     (200, 500, 10, 15),        # wide A
     (64, 40, 40, 40),          # l = min(m, n)
+    (1500, 700, 20, 30),       # 3-CTA cluster for Y, 2-CTA for B^T
+    (40000, 64, 10, 16),       # more rows than the register kernel holds: the smem kernel
 ])
 def test_fp64_shapes(m, n, k, l):
     A = synth.lowrank_plus_noise(m, n, min(60, min(m, n)), 1e-6, seed=m + n)
