@@ -45,6 +45,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--input", choices=["spectrum", "gaussian"], default="spectrum",
+                    help="gaussian: i.i.d. N(0,1) A without the QR setup (for profiler runs; "
+                         "no accuracy check)")
     return ap.parse_args()
 
 
@@ -185,9 +189,13 @@ def dram_traffic(stage: str, workload: str):
 
 
 # ---------------------------------------------------------------------------------------
-def make_input(w: dict, device: str):
+def make_input(w: dict, device: str, kind: str = "spectrum"):
     sigma = synth.spectrum(w["spectrum"], min(w["m"], w["n"]), w["k"])
     dt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[w["dtype"]]
+    if kind == "gaussian":
+        g = torch.Generator(device=device)
+        g.manual_seed(w["seed_u"])
+        return torch.randn(w["m"], w["n"], generator=g, device=device).to(dt), None
     A = synth.prescribed_matrix_torch(w["m"], w["n"], sigma, w["seed_u"], w["seed_v"], dt,
                                       device=device)
     return A, sigma
@@ -233,7 +241,7 @@ def run_ours(args):
     m, n, k, l = w["m"], w["n"], w["k"], w["l"]
     prec = precision_of(w)
     esz = 8 if prec == "f64" else 4
-    A, sigma = make_input(w, "cuda")
+    A, sigma = make_input(w, "cuda", args.input)
     fz = rlu.Factorizer(m, n, k, l, prec)
     ns = rlu.NUM_TIMED_STEPS
     names = rlu.timed_step_names()
@@ -283,28 +291,32 @@ def run_ours(args):
         outs["L"].copy_(L, non_blocking=True)
         outs["U"].copy_(U, non_blocking=True)
 
-    for _ in range(max(1, min(W, 3))):
-        e2e_step()
-    torch.cuda.synchronize()
-    barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(K):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
-    e2e = {"value": world * K / (e2e_ms / 1e3), "unit": "LU/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(max(1, min(W, 3))):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": world * K / (e2e_ms / 1e3), "unit": "LU/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
 
     # ---- accuracy of the last factorization (outside the timed region) -----------------
     P, Q, L, U, info = fz(A, w["seed_g"])
-    fro_d, _ = rlu.reconstruct_error(A, P, Q, L, U)
-    torch.cuda.synchronize()
-    err = {"fro": fro_d.item(), "rel_fro": fro_d.item() / float(np.sqrt(np.sum(sigma ** 2))),
-           "sigma_1": float(sigma[0]), "sigma_k1": float(sigma[k]),
-           "info": info.cpu().tolist()}
+    err = {"info": None}
+    if sigma is not None:
+        fro_d, _ = rlu.reconstruct_error(A, P, Q, L, U)
+        torch.cuda.synchronize()
+        err = {"fro": fro_d.item(), "rel_fro": fro_d.item() / float(np.sqrt(np.sum(sigma ** 2))),
+               "sigma_1": float(sigma[0]), "sigma_k1": float(sigma[k]),
+               "info": info.cpu().tolist()}
 
     if rank != 0:
         if world > 1:
@@ -340,7 +352,7 @@ def run_ours(args):
     gemm_tflops = 2.0 * m * n * (l + k) / (gemm_ms / 1e3) / 1e12
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and sigma is not None:
         A_host = A.double().cpu().numpy()
         cpu, ores = cpu_baseline(A_host, w)
         fro_o, _ = O.reconstruct_error(A_host, ores["P"], ores["Q"], ores["L"], ores["U"],

@@ -5,7 +5,7 @@
  * Aizenbud and Averbuch, "Randomized LU Decomposition" (Section 4): for an m x n matrix A
  * and integers k <= l it returns row and column permutations P, Q, a unit lower
  * trapezoidal L (m x k) and an upper trapezoidal U (k x n) with
- *     || P A Q - L U || = O(sigma_{k+1}(A))            (Eq. 1 and Theorem 4.1).
+ *     || P A Q - L U || = O(sigma_{k+1}(A))            (Eq. lu_error and theorem trm:rand_lu_err, Section 4).
  *
  * Conventions shared by every entry point
  *   - All matrix and vector pointers are DEVICE pointers owned by the caller. The library
@@ -89,7 +89,7 @@ size_t rlu_workspace_size(int64_t m, int64_t n, int32_t k, int32_t l, int32_t pr
 
 /* Algorithm 1, steps 1-8: randomized LU of A (m x n, row-major, lda >= n).
  *   k, l      : 1 <= k <= l <= min(m, n) (Algorithm 1 input; l <= min(m, n) as in the
- *               lemmas behind Theorem 4.1).
+ *               lemmas behind theorem trm:rand_lu_err).
  *   seed      : Philox key for G (stream id 0).
  *   P (m), Q (n): int32 gather permutations (outputs).
  *   L (m x k, column-major, ldl >= m), U (k x n, row-major, ldu >= n): outputs, FP64 for

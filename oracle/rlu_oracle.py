@@ -1,6 +1,6 @@
 """Plain, slow, FP64 restatement of Algorithm 1 ("Randomized LU Decomposition") of
 Shabat, Shmueli, Aizenbud and Averbuch, plus the error measures of Eq. (1) / Eq. (relErr)
-and the bound of Theorem 4.1 (trm:rand_lu_err).
+and the bound of the error theorem of Section 4 (trm:rand_lu_err).
 
 TEST INFRASTRUCTURE ONLY: used by tests/, __graft_entry__.smoke() and bench.py's CPU
 baseline; never by the product path. Shares no code with the CUDA implementation.
@@ -352,7 +352,7 @@ def _solve_upper(Um, X):
 
 
 def check_dims(m: int, n: int, k: int, l: int) -> None:
-    """Algorithm 1 input: l >= k >= 1; the lemmas behind Theorem 4.1 need l <= min(m, n)."""
+    """Algorithm 1 input: l >= k >= 1; the lemmas behind theorem trm:rand_lu_err need l <= min(m, n)."""
     if not (1 <= k <= l <= min(m, n)):
         raise ValueError(f"need 1 <= k <= l <= min(m, n); got m={m} n={n} k={k} l={l}")
 
@@ -412,7 +412,7 @@ def reconstruct_error(A, P, Q, L, U, spectral: bool = True):
 
 
 # ---------------------------------------------------------------------------------------
-# Theorem 4.1 (trm:rand_lu_err): error constant and success probability xi.
+# the error theorem of Section 4 (trm:rand_lu_err): error constant and success probability xi.
 # ---------------------------------------------------------------------------------------
 
 def theorem1_constant(n: int, k: int, l: int, beta: float, gamma: float) -> float:

@@ -83,7 +83,7 @@ def test_fp64_reconstruction_error(fp64_512):
     fro_d, spec_d = rlu.reconstruct_error(At, P, Q, L, U, power_iters=200)
     assert abs(fro_d.item() - fro_g) <= 1e-10 * fro_g
     assert abs(spec_d.item() - spec_g) <= 1e-3 * spec_g
-    # Theorem 4.1 lower bound: sigma_{k+1} = 1e-3 for this spectrum
+    # Eckart-Young lower bound: sigma_{k+1} = 1e-3 for this spectrum
     assert spec_g >= 1e-3 * (1 - 1e-9)
 
 

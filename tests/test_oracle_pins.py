@@ -222,7 +222,7 @@ def test_pinv_apply_matches_lstsq():
 
 
 # ----------------------------------------------------------------------------------------
-# End to end: closed forms, the identity in the proof of Theorem 4.1, brute force.
+# End to end: closed forms, the identity in the proof of theorem trm:rand_lu_err, brute force.
 # ----------------------------------------------------------------------------------------
 
 def _check_structure(res, m, n, k):
@@ -255,7 +255,7 @@ def test_full_rank_k_equals_n_is_exact_lu():
 
 
 def test_proof_identity_eq_main_bound():
-    # LU - PAQ = (L_y L_y^+ - I) P A Q  (proof of Theorem 4.1, Eq. main_bound_proof)
+    # LU - PAQ = (L_y L_y^+ - I) P A Q  (proof of theorem trm:rand_lu_err, Eq. main_bound_proof, Section 4.2)
     m, n, k, l = 90, 70, 8, 11
     A = synth.prescribed_matrix(m, n, synth.spectrum("inv_square", min(m, n)), 3, 4)
     res = O.rlu_factor(A, k, l, seed=8)
@@ -264,14 +264,14 @@ def test_proof_identity_eq_main_bound():
     lhs = L @ U - PAQ
     rhs = (Ly @ np.linalg.pinv(Ly) - np.eye(m)) @ PAQ
     assert np.max(np.abs(lhs - rhs)) < 1e-12
-    # ||L_y L_y^+|| <= 1 and L_y^+ L_y = I (used in the proof of Lemma 4.2)
+    # ||L_y L_y^+|| <= 1 and L_y^+ L_y = I (used in the proof of lemma lem:rand_lu_bound1)
     assert np.linalg.norm(Ly @ np.linalg.pinv(Ly), 2) <= 1 + 1e-12
     assert np.allclose(np.linalg.pinv(Ly) @ Ly, np.eye(k), atol=1e-12)
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
 def test_brute_force_bounds_tiny(seed):
-    # sigma_{k+1} <= ||LU - PAQ||_2 <= C(n,k,l,beta=5,gamma=5) sigma_{k+1} (Theorem 4.1;
+    # sigma_{k+1} <= ||LU - PAQ||_2 <= C(n,k,l,beta=5,gamma=5) sigma_{k+1} (theorem trm:rand_lu_err;
     # the lower bound is Eckart-Young). sigma by full SVD of A.
     m, n, k, l = 48, 40, 6, 9
     rng = np.random.default_rng(seed)
@@ -305,7 +305,7 @@ def test_power_iteration_matches_svd():
 
 
 # ----------------------------------------------------------------------------------------
-# Theorem 4.1: the success probability against Table 1 of the paper.
+# Theorem trm:rand_lu_err: the success probability against Table 1 of the paper.
 # ----------------------------------------------------------------------------------------
 
 def test_theorem1_xi_matches_table1():
