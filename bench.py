@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--prec", choices=["f32", "mixed", "f64"], default=None,
+                    help="arithmetic of the path (default: the workload's storage type)")
     ap.add_argument("--input", choices=["spectrum", "gaussian"], default="spectrum",
                     help="gaussian: i.i.d. N(0,1) A without the QR setup (for profiler runs; "
                          "no accuracy check)")
@@ -239,7 +241,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     w = synth.WORKLOADS[args.workload]
     m, n, k, l = w["m"], w["n"], w["k"], w["l"]
-    prec = precision_of(w)
+    prec = args.prec or precision_of(w)
     esz = 8 if prec == "f64" else 4
     A, sigma = make_input(w, "cuda", args.input)
     fz = rlu.Factorizer(m, n, k, l, prec)

@@ -48,8 +48,14 @@ typedef enum { RLU_F64 = 0, RLU_F32 = 1, RLU_BF16 = 2 } rlu_dtype;
  *   RLU_PREC_F64: A, G, Y, B, L, U in FP64, FP64 arithmetic everywhere. A must be RLU_F64.
  *   RLU_PREC_F32: "plain FP32". A, G, Y, B, L, U in FP32; FP32 SIMT GEMMs and LUs; the
  *                 k x k Gram matrix is reduced in FP64 and factored (Cholesky) in FP64.
- *                 A must be RLU_F32. */
-typedef enum { RLU_PREC_F64 = 0, RLU_PREC_F32 = 1 } rlu_precision;
+ *                 A must be RLU_F32.
+ *   RLU_PREC_MIXED: as RLU_PREC_F32, but the projection Y = A G (step 2) runs on the tensor
+ *                 cores with TF32 inputs and FP32 accumulation (the random range finder
+ *                 tolerates the rounding of A and G to TF32). A must be RLU_F32. The
+ *                 tensor-core projection reads A with TMA, which needs 16-byte aligned
+ *                 rows (A aligned, lda a multiple of 4); otherwise step 2 runs on the
+ *                 FP32 SIMT GEMM. */
+typedef enum { RLU_PREC_F64 = 0, RLU_PREC_F32 = 1, RLU_PREC_MIXED = 2 } rlu_precision;
 
 /* Device-resident status written by rlu_factor (the caller reads it after the stream
  * completes). */

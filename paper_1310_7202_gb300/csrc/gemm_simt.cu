@@ -11,6 +11,7 @@
 // loads without bank conflicts.
 #include "common.cuh"
 #include "gemm_simt.cuh"
+#include "umma.cuh"
 
 namespace rlu {
 
@@ -217,6 +218,26 @@ template int32_t gemm_simt<float, double>(const GemmOp&, cudaStream_t);
 template int32_t gemm_simt<double, double>(const GemmOp&, cudaStream_t);
 template size_t gemm_partial_bytes<float>(int64_t, int64_t, int);
 template size_t gemm_partial_bytes<double>(int64_t, int64_t, int);
+
+int32_t splitk_reduce_f32(const float* part, int splits, int64_t M, int64_t N, float* out,
+                          int64_t ldo, bool out_rowmajor, cudaStream_t s) {
+  const int threads = 256;
+  int64_t blocks = ceil_div(M * N, threads);
+  if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+  k_splitk_reduce<float, float><<<(unsigned)blocks, threads, 0, s>>>(part, splits, M, N, M * N,
+                                                                    out, ldo, out_rowmajor);
+  return last_launch_status();
+}
+
+int32_t splitk_reduce_f64(const float* part, int splits, int64_t M, int64_t N, double* out,
+                          int64_t ldo, cudaStream_t s) {
+  const int threads = 256;
+  int64_t blocks = ceil_div(M * N, threads);
+  if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+  k_splitk_reduce<float, double><<<(unsigned)blocks, threads, 0, s>>>(part, splits, M, N, M * N,
+                                                                     out, ldo, true);
+  return last_launch_status();
+}
 
 int gemm_tile_m(int32_t dtype) { return dtype == RLU_F64 ? GemmCfg<double>::BM : GemmCfg<float>::BM; }
 int gemm_tile_n(int32_t dtype) { return dtype == RLU_F64 ? GemmCfg<double>::BN : GemmCfg<float>::BN; }

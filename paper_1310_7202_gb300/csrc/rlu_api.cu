@@ -18,6 +18,7 @@
 #include "panel_lu.cuh"
 #include "residual.cuh"
 #include "small.cuh"
+#include "umma.cuh"
 
 namespace rlu {
 
@@ -91,6 +92,7 @@ static int split_for(int64_t M, int64_t N, int64_t K, int bm, int bn) {
 
 // Workspace layout of rlu_factor for one size / precision.
 struct Plan {
+  int32_t prec = RLU_PREC_F32;
   int32_t dt = RLU_F32;
   size_t esz = 4;
   int64_t m = 0, n = 0;
@@ -98,7 +100,8 @@ struct Plan {
   int64_t ldg = 0, ldy = 0, ldl = 0, ldb = 0;
   int split_y = 1, split_g = 1, split_c = 1;
   size_t off_G = 0, off_Y = 0, off_Lt = 0, off_Lp = 0, off_M = 0, off_Rinv = 0, off_RinvT = 0,
-         off_C = 0, off_T = 0, off_B = 0, off_Lb = 0, off_part = 0, total = 0;
+         off_C = 0, off_T = 0, off_B = 0, off_Lb = 0, off_part = 0, off_Lhi = 0, off_Llo = 0,
+         total = 0;
 };
 
 static size_t carve(size_t& cur, size_t bytes) {
@@ -108,15 +111,17 @@ static size_t carve(size_t& cur, size_t bytes) {
 }
 
 static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p) {
+  p.prec = prec;
   if (prec == RLU_PREC_F64) {
     p.dt = RLU_F64;
     p.esz = 8;
-  } else if (prec == RLU_PREC_F32) {
+  } else if (prec == RLU_PREC_F32 || prec == RLU_PREC_MIXED) {
     p.dt = RLU_F32;
     p.esz = 4;
   } else {
     return false;
   }
+  if (prec == RLU_PREC_MIXED && l > 256) return false;  // one TMEM accumulator for Y
   if (!(k >= 1 && k <= l && l <= m && l <= n)) return false;
   if (m > INT32_MAX / 2 || n > INT32_MAX / 2) return false;
   p.m = m; p.n = n; p.k = k; p.l = l;
@@ -126,13 +131,20 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   p.ldb = round_up(n, 8);
   const int bm = gemm_tile_m(p.dt), bn = gemm_tile_n(p.dt);
   p.split_y = split_for(m, l, n, bm, bn);
+  if (prec == RLU_PREC_MIXED) {  // tensor-core products: 128-row tiles, split-K fills the SMs
+    p.split_y = umma3_splits(m, n);
+  }
   p.split_g = split_for(k, k, m, bm, bn);
   if (p.dt == RLU_F32 && p.split_g < 2) p.split_g = 2;  // FP32 partials, FP64 reduction
   p.split_c = split_for(k, n, m, bm, bn);
+  if (prec == RLU_PREC_MIXED) {
+    p.split_g = umma3_splits(k, m);
+    p.split_c = umma3_splits(n, m);
+  }
   size_t part = 0;
   auto upd = [&](size_t b) { part = b > part ? b : part; };
   if (p.split_y > 1) upd((size_t)p.split_y * m * l * p.esz);
-  upd((size_t)p.split_g * k * k * p.esz);
+  upd((size_t)(p.split_g + 1) * k * k * p.esz);
   if (p.split_c > 1) upd((size_t)p.split_c * k * n * p.esz);
   size_t cur = 0;
   const size_t e = p.esz;
@@ -148,6 +160,10 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   p.off_B = carve(cur, (size_t)k * p.ldb * e);
   p.off_Lb = carve(cur, (size_t)k * k * e);
   p.off_part = carve(cur, part);
+  if (prec == RLU_PREC_MIXED) {
+    p.off_Lhi = carve(cur, (size_t)p.ldl * k * e);
+    p.off_Llo = carve(cur, (size_t)p.ldl * k * e);
+  }
   p.total = cur;
   return true;
 }
@@ -180,7 +196,25 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
   if (st && st->G) RLU_TRY(copy_cm<T>(G, p.ldg, static_cast<T*>(st->G), n, n, l, s));
   // step 2: Y (m x l, col-major) = A (row-major) * G (col-major)
   RLU_TRY(tm.rec(1, false, s));
-  {
+  // the tensor-core projection reads A with TMA: rows must start on 16-byte boundaries
+  const bool tma_ok = ((uintptr_t)A & 15u) == 0 && (lda * (int64_t)sizeof(T)) % 16 == 0;
+  if (p.prec == RLU_PREC_MIXED && tma_ok) {
+    Umma3Op op{};
+    op.A0 = reinterpret_cast<const float*>(A);
+    op.lda = lda;
+    op.B0 = reinterpret_cast<const float*>(G);
+    op.ldb = p.ldg;
+    op.M = m;
+    op.N = l;
+    op.K = n;
+    op.out = reinterpret_cast<float*>(Y);
+    op.ldo = p.ldy;
+    op.out_colmajor = true;
+    op.splits = p.split_y;
+    op.partial = reinterpret_cast<float*>(part);
+    op.status = info ? &info->status : nullptr;
+    RLU_TRY(umma3_gemm(U3_MODE_Y2, op, s));
+  } else {
     GemmOp op{A, lda, true, G, p.ldg, true, Y, p.ldy, false, m, l, n, p.split_y, part, false};
     RLU_TRY((gemm_simt<T, T>(op, s)));
   }
@@ -199,12 +233,33 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
   RLU_TRY(tm.rec(2, true, s));
   // step 4
   RLU_TRY(tm.rec(3, false, s));
-  RLU_TRY(build_ly<T>(Y, p.ldy, m, k, P, Lt, Lp, p.ldl, s));
+  T* Lhi = p.off_Lhi ? reinterpret_cast<T*>(ws + p.off_Lhi) : nullptr;
+  T* Llo = p.off_Llo ? reinterpret_cast<T*>(ws + p.off_Llo) : nullptr;
+  RLU_TRY(build_ly<T>(Y, p.ldy, m, k, P, Lt, Lp, p.ldl, s, Lhi, Llo));
   RLU_TRY(tm.rec(3, true, s));
   if (st && st->Ly) RLU_TRY(copy_cm<T>(Lp, p.ldl, static_cast<T*>(st->Ly), m, m, k, s));
   // step 5: Gram M = L~^T L~ in FP64
   RLU_TRY(tm.rec(4, false, s));
-  {
+  if (Lhi) {  // tensor cores, 3 TF32 products; FP32 partials summed in FP64
+    Umma3Op op{};
+    op.A0 = reinterpret_cast<const float*>(Lhi);
+    op.A1 = reinterpret_cast<const float*>(Llo);
+    op.lda = p.ldl;
+    op.B0 = op.A0;
+    op.B1 = op.A1;
+    op.ldb = p.ldl;
+    op.M = k;
+    op.N = k;
+    op.K = m;
+    op.out = nullptr;
+    op.splits = p.split_g;
+    op.partial = reinterpret_cast<float*>(part);
+    op.status = info ? &info->status : nullptr;
+    RLU_TRY(umma3_gemm(U3_MODE_G3, op, s));
+    const int kc = (int)round_up(ceil_div(m, p.split_g), 32);
+    RLU_TRY(splitk_reduce_f64(reinterpret_cast<const float*>(part), (int)ceil_div(m, kc), k, k,
+                              M, k, s));
+  } else {
     GemmOp op{Lt, p.ldl, true, Lt, p.ldl, true, M, k, true, k, k, m, p.split_g, part, false};
     RLU_TRY((gemm_simt<T, double>(op, s)));
   }
@@ -221,8 +276,27 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
     RLU_CUDA_TRY(cudaEventRecord(ss->join, ss->side));
     // C = L~^T A (k x n, row-major)
     RLU_TRY(tm.rec(6, false, s));
-    GemmOp op{Lt, p.ldl, true, A, lda, false, Cb, p.ldb, true, k, n, m, p.split_c, part, false};
-    RLU_TRY((gemm_simt<T, T>(op, s)));
+    if (Lhi && tma_ok) {  // C^T = A^T L~ on the tensor cores, 3 TF32 products
+      Umma3Op op{};
+      op.A0 = reinterpret_cast<const float*>(A);
+      op.lda = lda;
+      op.B0 = reinterpret_cast<const float*>(Lhi);
+      op.B1 = reinterpret_cast<const float*>(Llo);
+      op.ldb = p.ldl;
+      op.M = n;
+      op.N = k;
+      op.K = m;
+      op.out = reinterpret_cast<float*>(Cb);
+      op.ldo = p.ldb;
+      op.out_colmajor = true;  // D row = column of A, D column = row of C
+      op.splits = p.split_c;
+      op.partial = reinterpret_cast<float*>(part);
+      op.status = info ? &info->status : nullptr;
+      RLU_TRY(umma3_gemm(U3_MODE_C3, op, s));
+    } else {
+      GemmOp op{Lt, p.ldl, true, A, lda, false, Cb, p.ldb, true, k, n, m, p.split_c, part, false};
+      RLU_TRY((gemm_simt<T, T>(op, s)));
+    }
     RLU_TRY(tm.rec(6, true, s));
     RLU_CUDA_TRY(cudaStreamWaitEvent(s, ss->join, 0));
   }
@@ -270,8 +344,10 @@ static int32_t validate(const void* A, int32_t dtype, int64_t m, int64_t n, int6
   if (m < 1 || n < 1 || k < 1 || k > l || l > m || l > n) return RLU_EINVAL;
   if (lda < n || ldl < m || ldu < n) return RLU_EINVAL;
   if (prec == RLU_PREC_F64 && dtype != RLU_F64) return RLU_EUNSUPPORTED;
-  if (prec == RLU_PREC_F32 && dtype != RLU_F32) return RLU_EUNSUPPORTED;
-  if (prec != RLU_PREC_F64 && prec != RLU_PREC_F32) return RLU_EUNSUPPORTED;
+  if ((prec == RLU_PREC_F32 || prec == RLU_PREC_MIXED) && dtype != RLU_F32)
+    return RLU_EUNSUPPORTED;
+  if (prec != RLU_PREC_F64 && prec != RLU_PREC_F32 && prec != RLU_PREC_MIXED)
+    return RLU_EUNSUPPORTED;
   return RLU_OK;
 }
 

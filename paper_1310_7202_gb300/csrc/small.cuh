@@ -7,7 +7,7 @@ namespace rlu {
 
 template <typename T>
 int32_t build_ly(const T* Y, int64_t ldy, int64_t m, int k, const int32_t* perm, T* Lt, T* Lp,
-                 int64_t ldl, cudaStream_t s);
+                 int64_t ldl, cudaStream_t s, T* Lhi = nullptr, T* Llo = nullptr);
 
 template <typename T>
 int32_t chol_inv(double* M, int k, double* Rinv, T* RinvT, int32_t* status, cudaStream_t s);

@@ -1,0 +1,81 @@
+// Interface of the tcgen05 TF32 GEMM (see umma.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace rlu {
+
+// Kernel arguments (by value).
+struct UmmaArgs {
+  float* out;
+  int64_t ldo;
+  size_t split_stride;
+  int M, N, K, BN, kchunk;
+  bool out_colmajor;
+  int32_t* status;
+};
+
+// D (M x N) = A (M x K, row-major, lda) * B (N x K, row-major, ldb)^T, TF32 multiplies.
+// N <= 256. out: column-major (ldo >= M) or row-major (ldo >= N). splits > 1 writes
+// row-major partial slices (splits * M * N floats) reduced in a fixed order.
+struct UmmaOp {
+  const float* A;
+  int64_t lda;
+  const float* B;
+  int64_t ldb;
+  int64_t M, N, K;
+  float* out;
+  int64_t ldo;
+  bool out_colmajor;
+  int splits;
+  float* partial;
+  int32_t* status;
+};
+
+int32_t umma_tf32_gemm(const UmmaOp& op, cudaStream_t s);
+size_t umma_smem_bytes(int BN);
+
+// FP32-accurate tensor-core products from exact TF32 splits (see umma3.cu).
+enum { U3_MODE_Y2 = 0, U3_MODE_C3 = 1, U3_MODE_G3 = 2 };
+
+struct Umma3Args {
+  float* out;
+  int64_t ldo;
+  size_t split_stride;
+  int M, N, K, BN, kchunk, stages;
+  bool out_colmajor;
+  int32_t* status;
+};
+
+// Y2: A0 = A (M x K row-major, lda), B0 = G^T (N x K row-major, ldb).
+// C3: A0 = A stored K x M row-major (lda), B0/B1 = hi/lo of B (N x K row-major, ldb).
+// G3: A0/A1 = hi/lo of A (M x K, lda), B0/B1 = hi/lo of B (N x K, ldb).
+// out == nullptr: only the row-major FP32 partial slices (splits x M x N) are written.
+struct Umma3Op {
+  const float* A0;
+  const float* A1;
+  int64_t lda;
+  const float* B0;
+  const float* B1;
+  int64_t ldb;
+  int64_t M, N, K;
+  float* out;
+  int64_t ldo;
+  bool out_colmajor;
+  int splits;
+  float* partial;
+  int32_t* status;
+};
+
+int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s);
+int umma3_splits(int64_t M, int64_t K);
+
+// Fixed-order sum of row-major FP32 partial slices into out (row- or column-major).
+int32_t splitk_reduce_f32(const float* part, int splits, int64_t M, int64_t N, float* out,
+                          int64_t ldo, bool out_rowmajor, cudaStream_t s);
+
+// Fixed-order FP64 sum of row-major FP32 partial slices into a row-major FP64 matrix.
+int32_t splitk_reduce_f64(const float* part, int splits, int64_t M, int64_t N, double* out,
+                          int64_t ldo, cudaStream_t s);
+
+}  // namespace rlu

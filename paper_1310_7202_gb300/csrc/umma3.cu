@@ -1,0 +1,421 @@
+// FP32-accurate tensor-core GEMMs on tcgen05/TMEM (sm_103a) for the mixed path, built
+// from exact TF32 splits: x = hi + lo with hi = x with its 13 low mantissa bits cleared
+// (exactly representable in TF32) and lo = x - hi (exact in FP32; its own TF32 rounding
+// costs ~2^-22 of x). D (M x N, FP32 accumulation in TMEM) = A (M x K) * B (N x K)^T:
+//
+//   MODE_Y2  Y = A G (step 2): A row-major (K-major), split on chip; G not split (rounding
+//            G only changes the Gaussian test matrix). Products hi(A) G + lo(A) G.
+//   MODE_C3  C^T = A^T L~ (step 5): the A tile arrives n-contiguous (MN-major) and is
+//            transposed and split on chip into K-major tiles; L~ comes pre-split (hi, lo).
+//            Products Ahi Lhi + Alo Lhi + Ahi Llo.
+//   MODE_G3  Gram L~^T L~ (step 5): both operands pre-split, three products.
+//
+// Warp roles: warp 0 TMA producer (ring of STAGES slots, full/empty mbarriers), warp 1
+// TMEM allocation and MMA issue, warps 2..5 epilogue (tcgen05.ld), warps 6..9 converter
+// (MODE_Y2 / MODE_C3): one thread per tile row, writes the 128-byte-swizzled K-major hi/lo
+// tiles, fences them to the async proxy and arrives on a per-slot mbarrier. Every wait is
+// bounded (~1 s) and records an error instead of hanging.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace rlu {
+
+static constexpr int U3_BM = 128;
+static constexpr int U3_BK = 32;
+static constexpr int U3_THREADS = 320;
+static constexpr int U3_MAXST = 4;
+
+struct U3Smem {
+  uint64_t full[U3_MAXST];
+  uint64_t conv[U3_MAXST];
+  uint64_t empty[U3_MAXST];
+  uint64_t accum;
+  uint32_t tmem_base;
+  int32_t err;
+};
+
+namespace u3 {
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mb_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+               ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n"
+               ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mb_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity) {
+  if (mb_try(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (!mb_try(bar, parity))
+    if (now_ns() - t0 > 1000000000ull) return false;
+  return true;
+}
+__device__ __forceinline__ void tma2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                      uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+               ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;
+}
+}  // namespace u3
+
+__host__ __device__ constexpr uint32_t u3_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// Shared-memory plan of one ring slot (bytes, all multiples of 1024).
+struct U3Layout {
+  uint32_t a0, a1, a2, b0, b1, stage;
+};
+__host__ __device__ inline U3Layout u3_layout(int mode, int BN) {
+  U3Layout L{};
+  const uint32_t at = U3_BM * 128, bt = (uint32_t)BN * 128;
+  if (mode == U3_MODE_Y2) {         // a0: TMA A -> hi in place, a1: lo, b0: G
+    L.a0 = 0; L.a1 = at; L.b0 = 2 * at; L.b1 = L.b0; L.a2 = 0; L.stage = 2 * at + bt;
+  } else if (mode == U3_MODE_C3) {  // a2: raw A (n-contiguous), a0 hi, a1 lo, b0 Lhi, b1 Llo
+    L.a2 = 0; L.a0 = at; L.a1 = 2 * at; L.b0 = 3 * at; L.b1 = 3 * at + bt; L.stage = 3 * at + 2 * bt;
+  } else {                          // G3: a0 hi, a1 lo, b0 hi, b1 lo (all TMA)
+    L.a0 = 0; L.a1 = at; L.b0 = 2 * at; L.b1 = 2 * at + bt; L.a2 = 0; L.stage = 2 * at + 2 * bt;
+  }
+  L.stage = (L.stage + 1023u) & ~1023u;
+  return L;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(U3_THREADS, 1)
+k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+        const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+        Umma3Args a) {
+  using namespace u3;
+  extern __shared__ __align__(1024) unsigned char u3_smem[];
+  U3Smem& sh = *reinterpret_cast<U3Smem*>(u3_smem);
+  const uint32_t tiles = (su32(u3_smem) + sizeof(U3Smem) + 1023u) & ~1023u;
+  const U3Layout lay = u3_layout(MODE, a.BN);
+  const int S = a.stages;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * U3_BM;
+  const int kz = blockIdx.y;
+  const int k_begin = kz * a.kchunk;
+  const int k_end = min(a.K, k_begin + a.kchunk);
+  const int nk = (k_end - k_begin + U3_BK - 1) / U3_BK;
+  constexpr bool CONV = (MODE != U3_MODE_G3);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mb_init(su32(&sh.full[s]), 1);
+      mb_init(su32(&sh.conv[s]), 128);
+      mb_init(su32(&sh.empty[s]), 1);
+    }
+    mb_init(su32(&sh.accum), 1);
+    sh.err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n"
+                 ::"r"(su32(&sh.tmem_base)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = sh.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ------------------------------------------------------------------
+    uint32_t tx = lay.stage;
+    if (MODE == U3_MODE_Y2) tx = 2 * 0 + U3_BM * 128 + (uint32_t)a.BN * 128;
+    if (MODE == U3_MODE_C3) tx = U3_BM * 128 + 2 * (uint32_t)a.BN * 128;
+    if (MODE == U3_MODE_G3) tx = 2 * U3_BM * 128 + 2 * (uint32_t)a.BN * 128;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % S;
+      if (kt >= S && !mb_wait(su32(&sh.empty[s]), (uint32_t)(((kt / S) - 1) & 1))) {
+        sh.err = 1;
+        break;
+      }
+      const uint32_t base = tiles + s * lay.stage;
+      const uint32_t bar = su32(&sh.full[s]);
+      mb_expect_tx(bar, tx);
+      const int kx = k_begin + kt * U3_BK;
+      if (MODE == U3_MODE_Y2) {
+        tma2d(base + lay.a0, &mA0, kx, m0, bar);
+        tma2d(base + lay.b0, &mB0, kx, 0, bar);
+      } else if (MODE == U3_MODE_C3) {
+        tma2d(base + lay.a2, &mA0, m0, kx, bar);   // raw A: x = n (128 wide), y = m
+        tma2d(base + lay.b0, &mB0, kx, 0, bar);
+        tma2d(base + lay.b1, &mB1, kx, 0, bar);
+      } else {
+        tma2d(base + lay.a0, &mA0, kx, m0, bar);
+        tma2d(base + lay.a1, &mA1, kx, m0, bar);
+        tma2d(base + lay.b0, &mB0, kx, 0, bar);
+        tma2d(base + lay.b1, &mB1, kx, 0, bar);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer --------------------------------------------------------------------
+    const uint32_t idesc = u3_idesc(U3_BM, a.BN);
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % S;
+      const uint32_t par = (uint32_t)((kt / S) & 1);
+      if (!mb_wait(su32(CONV ? &sh.conv[s] : &sh.full[s]), par)) {
+        sh.err = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t base = tiles + s * lay.stage;
+#pragma unroll
+      for (int kk = 0; kk < U3_BK / 8; ++kk) {
+        const uint32_t off = kk * 32;
+        const uint64_t ah = desc_sw128(base + lay.a0 + off), al = desc_sw128(base + lay.a1 + off);
+        const uint64_t bh = desc_sw128(base + lay.b0 + off), bl = desc_sw128(base + lay.b1 + off);
+        mma_tf32(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, al, bh, idesc, 1u);
+        if (MODE != U3_MODE_Y2) mma_tf32(tmem, ah, bl, idesc, 1u);
+      }
+      commit(su32(&sh.empty[s]));
+    }
+    commit(su32(&sh.accum));
+  } else if (warp >= 2 && warp < 6) {
+    // ---- epilogue ------------------------------------------------------------------------
+    const bool ok = mb_wait(su32(&sh.accum), 0u);
+    if (!ok) sh.err = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int quarter = warp & 3;
+    const int row = m0 + quarter * 32 + lane;
+    float* __restrict__ out = a.out + (size_t)kz * a.split_stride;
+    for (int c0 = 0; c0 < a.BN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+          "%28, %29, %30, %31}, [%32];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (ok && row < a.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = c0 + j;
+          if (col < a.N) {
+            const float f = __uint_as_float(v[j]);
+            if (a.out_colmajor)
+              out[(size_t)col * a.ldo + row] = f;
+            else
+              out[(size_t)row * a.ldo + col] = f;
+          }
+        }
+      }
+    }
+  } else if (CONV && warp >= 6) {
+    // ---- converter: one thread per tile row (128 rows) ------------------------------------
+    const int r = threadIdx.x - 192;  // 0..127
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % S;
+      if (!mb_wait(su32(&sh.full[s]), (uint32_t)((kt / S) & 1))) {
+        sh.err = 1;
+        break;
+      }
+      const uint32_t base = tiles + s * lay.stage;
+      if (MODE == U3_MODE_Y2) {
+        // row r of the swizzled A tile: 8 chunks of 16 bytes, position-preserving split
+        float* hi = reinterpret_cast<float*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 32;
+        float* lo = reinterpret_cast<float*>(u3_smem + (base + lay.a1 - su32(u3_smem))) + r * 32;
+        // chunks visited in a row-rotated order so that each 8-thread phase of a warp
+        // touches 8 different 16-byte bank groups
+#pragma unroll
+        for (int c0 = 0; c0 < 8; ++c0) {
+          const int c = (c0 + r) & 7;
+          float4 v = *reinterpret_cast<float4*>(hi + 4 * c);
+          float4 h, l;
+          split_tf32(v.x, h.x, l.x);
+          split_tf32(v.y, h.y, l.y);
+          split_tf32(v.z, h.z, l.z);
+          split_tf32(v.w, h.w, l.w);
+          *reinterpret_cast<float4*>(hi + 4 * c) = h;
+          *reinterpret_cast<float4*>(lo + 4 * c) = l;
+        }
+      } else {
+        // raw tile: 32 rows (K) x 128 floats (M), row-major; output row r (M index r):
+        // its 32 K values, 16-byte chunk c stored at chunk position c ^ (r & 7)
+        const float* raw = reinterpret_cast<const float*>(u3_smem + (base + lay.a2 - su32(u3_smem)));
+        float* hi = reinterpret_cast<float*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 32;
+        float* lo = reinterpret_cast<float*>(u3_smem + (base + lay.a1 - su32(u3_smem))) + r * 32;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float4 h, l;
+          split_tf32(raw[(4 * c + 0) * U3_BM + r], h.x, l.x);
+          split_tf32(raw[(4 * c + 1) * U3_BM + r], h.y, l.y);
+          split_tf32(raw[(4 * c + 2) * U3_BM + r], h.z, l.z);
+          split_tf32(raw[(4 * c + 3) * U3_BM + r], h.w, l.w);
+          const int pc = c ^ (r & 7);
+          *reinterpret_cast<float4*>(hi + 4 * pc) = h;
+          *reinterpret_cast<float4*>(lo + 4 * pc) = l;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mb_arrive(su32(&sh.conv[s]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
+  }
+  if (threadIdx.x == 0 && sh.err && a.status) atomicExch(a.status, RLU_ETIMEOUT);
+}
+
+// ---------------------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// FP32 row-major (rows x cols, ld) tensor map with a box of box_x columns x box_y rows.
+static int32_t map2d(CUtensorMap* map, const float* base, int64_t rows, int64_t cols,
+                     int64_t ld, int box_x, int box_y, bool swizzle) {
+  auto enc = encode_fn();
+  if (!enc) return RLU_ECUDA;
+  if (((uintptr_t)base & 15u) != 0 || (ld * 4) % 16 != 0) return RLU_EINVAL;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RLU_OK : RLU_ECUDA;
+}
+
+template <int MODE>
+static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
+  if (op.M <= 0 || op.N <= 0 || op.N > 256 || op.K <= 0) return RLU_EINVAL;
+  const int BN = (int)round_up(op.N, 16);
+  const U3Layout lay = u3_layout(MODE, BN);
+  int dev = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  int optin = 0;
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int ctrl = 2048;
+  int stages = (int)((optin - ctrl) / (int)lay.stage);
+  if (stages > U3_MAXST) stages = U3_MAXST;
+  if (stages < 2) return RLU_EUNSUPPORTED;
+  const size_t smem = (size_t)ctrl + (size_t)stages * lay.stage;
+  CUtensorMap m0{}, m1{}, n0{}, n1{};
+  if (MODE == U3_MODE_Y2) {
+    RLU_TRY(map2d(&m0, op.A0, op.M, op.K, op.lda, U3_BK, U3_BM, true));
+    RLU_TRY(map2d(&n0, op.B0, op.N, op.K, op.ldb, U3_BK, BN, true));
+    m1 = m0;
+    n1 = n0;
+  } else if (MODE == U3_MODE_C3) {
+    // A stored row-major K x M (rows = K index, M contiguous): box 128 (M) x 32 (K)
+    RLU_TRY(map2d(&m0, op.A0, op.K, op.M, op.lda, U3_BM, U3_BK, false));
+    RLU_TRY(map2d(&n0, op.B0, op.N, op.K, op.ldb, U3_BK, BN, true));
+    RLU_TRY(map2d(&n1, op.B1, op.N, op.K, op.ldb, U3_BK, BN, true));
+    m1 = m0;
+  } else {
+    RLU_TRY(map2d(&m0, op.A0, op.M, op.K, op.lda, U3_BK, U3_BM, true));
+    RLU_TRY(map2d(&m1, op.A1, op.M, op.K, op.lda, U3_BK, U3_BM, true));
+    RLU_TRY(map2d(&n0, op.B0, op.N, op.K, op.ldb, U3_BK, BN, true));
+    RLU_TRY(map2d(&n1, op.B1, op.N, op.K, op.ldb, U3_BK, BN, true));
+  }
+  int splits = op.splits < 1 ? 1 : op.splits;
+  const int kchunk = (int)round_up(ceil_div(op.K, splits), U3_BK);
+  splits = (int)ceil_div(op.K, kchunk);
+  Umma3Args a{};
+  a.M = (int)op.M;
+  a.N = (int)op.N;
+  a.K = (int)op.K;
+  a.BN = BN;
+  a.kchunk = kchunk;
+  a.stages = stages;
+  a.status = op.status;
+  if (splits == 1 && op.out) {
+    a.out = op.out;
+    a.ldo = op.ldo;
+    a.out_colmajor = op.out_colmajor;
+  } else {
+    if (!op.partial) return RLU_ENOMEM;
+    a.out = op.partial;
+    a.ldo = op.N;
+    a.out_colmajor = false;
+    a.split_stride = (size_t)op.M * op.N;
+  }
+  auto kern = k_umma3<MODE>;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)ceil_div(op.M, U3_BM), (unsigned)splits);
+  kern<<<grid, U3_THREADS, smem, s>>>(m0, m1, n0, n1, a);
+  RLU_TRY(last_launch_status());
+  if (a.out == op.partial && op.out)
+    return splitk_reduce_f32(op.partial, splits, op.M, op.N, op.out, op.ldo, !op.out_colmajor, s);
+  return RLU_OK;
+}
+
+int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s) {
+  if (mode == U3_MODE_Y2) return launch_u3<U3_MODE_Y2>(op, s);
+  if (mode == U3_MODE_C3) return launch_u3<U3_MODE_C3>(op, s);
+  if (mode == U3_MODE_G3) return launch_u3<U3_MODE_G3>(op, s);
+  return RLU_EINVAL;
+}
+
+int umma3_splits(int64_t M, int64_t K) {
+  const int64_t tiles = ceil_div(M, U3_BM);
+  int64_t s = (int64_t)sm_count() / (tiles > 0 ? tiles : 1);
+  const int64_t kmax = K / 256 > 1 ? K / 256 : 1;
+  return (int)(s < 1 ? 1 : (s > kmax ? kmax : s));
+}
+
+}  // namespace rlu
