@@ -154,34 +154,37 @@ def stage_work(name: str, m: int, n: int, k: int, l: int, esz: int):
         "lu_Y": (float(m) * l * l, 2.0 * m * l * esz),
         "build_Ly": (0.0, 3.0 * m * k * esz),
         "gram": (2.0 * m * k * k, m * k * esz + k * k * 8),
-        "chol_inv": (2.0 * k ** 3 / 3.0, 3.0 * k * k * 8),
+        "ldl": (k ** 3 / 3.0, 2.0 * k * k * 8),
         "gemm_C": (2.0 * m * n * k, (m * n + m * k + k * n) * esz),
-        "tri_B": (4.0 * k * k * n, 5.0 * k * n * esz),
+        "trsm_B": (2.0 * k * k * n, 2.0 * k * n * esz),
         "lu_B": (float(n) * k * k, 2.0 * n * k * esz),
         "gather_Lb_U": (0.0, 2.0 * k * n * esz),
         "gemm_L": (2.0 * m * k * k, 2.0 * m * k * esz),
     }[name]
 
 
-STAGE_SOURCE = {"gaussian": "gauss.cu", "gemm_Y": "gemm_simt.cu", "lu_Y": "panel_lu.cu",
-                "build_Ly": "small.cu", "gram": "gemm_simt.cu", "chol_inv": "small.cu",
-                "gemm_C": "gemm_simt.cu", "tri_B": "gemm_simt.cu", "lu_B": "panel_lu.cu",
+STAGE_SOURCE = {"gaussian": "gauss.cu", "gemm_Y": "gemm_simt.cu", "lu_Y": "lu_reg.cu",
+                "build_Ly": "small.cu", "gram": "gemm_simt.cu", "ldl": "small.cu",
+                "gemm_C": "gemm_simt.cu", "trsm_B": "small.cu", "lu_B": "lu_reg.cu",
                 "gather_Lb_U": "small.cu", "gemm_L": "gemm_simt.cu"}
+# the mixed path runs its three large products on the tensor cores
+MIXED_SOURCE = {"gemm_Y": "umma3.cu", "gram": "umma3.cu", "gemm_C": "umma3.cu"}
 
 
-def source_sha(stage: str) -> str:
-    p = os.path.join(ROOT, "paper_1310_7202_gb300", "csrc", STAGE_SOURCE[stage])
+def source_sha(stage: str, prec: str = "f32") -> str:
+    src = MIXED_SOURCE.get(stage) if prec == "mixed" else None
+    p = os.path.join(ROOT, "paper_1310_7202_gb300", "csrc", src or STAGE_SOURCE[stage])
     with open(p, "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()[:12]
 
 
-def dram_traffic(stage: str, workload: str):
+def dram_traffic(stage: str, workload: str, prec: str = "f32"):
     """DRAM bytes per launch from the committed ncu summary, when it was taken on the
     current source of the kernel; else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    sha = source_sha(stage)
+    sha = source_sha(stage, prec)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and not line.startswith("#") and parts[0] == stage \
@@ -330,7 +333,7 @@ def run_ours(args):
     peaks, peak_kind = load_peaks()
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
-    main_stream = [s for s in names if s != "chol_inv"]  # chol_inv overlaps gemm_C
+    main_stream = [s for s in names if s != "ldl"]  # ldl runs on a side stream beside gemm_C
     dom = max(main_stream, key=lambda s: stage_ms[s])
     flops, byts = stage_work(dom, m, n, k, l, esz)
     dom_ms = stage_ms[dom]
@@ -345,7 +348,7 @@ def run_ours(args):
         roof = {"kernel": dom, "bound": "hbm", "achieved": byts / (dom_ms / 1e3) / 1e9,
                 "peak": peak, "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs"}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
-    tr = dram_traffic(dom, args.workload)
+    tr = dram_traffic(dom, args.workload, args.prec)
     roof["traffic"] = tr
     roof["algorithmic_per_launch"] = flops if roof["unit"] == "TFLOP/s" else byts
     roof["launch_ms"] = dom_ms

@@ -3,8 +3,11 @@
 // Algorithm 1, with the same swap-free position bookkeeping and tie rule as panel_lu.cu
 // (largest |value|, then smallest current position, which is getf2's choice).
 //
-// Each thread owns RT rows; a panel of up to NB-1 columns of each row lives in registers
-// and shifts by one register per step, so the rank-1 update is register-to-register. The
+// One launch factors one panel of up to NB-1 columns; the positions of the rows persist in
+// global memory between launches, and k_lu_trail (all SMs) applies each panel's rank-w
+// update to the remaining columns. Each thread owns RT rows; the panel's part of each row
+// lives in registers and shifts by one register per step, so the rank-1 update is
+// register-to-register. The
 // per-step exchange avoids cluster barriers: every CTA reduces its candidates (warp
 // reductions on order-preserving integer keys), stages one record (key, position, row,
 // its pending multiplier and its row values) and pushes it with st.async into a receive
@@ -71,6 +74,19 @@ __device__ __forceinline__ uint64_t mag_key(float v) {
 __device__ __forceinline__ uint64_t mag_key(double v) {
   const double a = fabs(v);
   return (a == a) ? (uint64_t)__double_as_longlong(a) : 0ull;
+}
+
+// Reciprocal of a pivot: correctly rounded in FP32; FP32 seed and two Newton steps in FP64
+// (IEEE divide outside the FP32 exponent range). Multipliers are x * (1/pivot).
+__device__ __forceinline__ float rcp_piv(float p) { return __frcp_rn(p); }
+__device__ __forceinline__ double rcp_piv(double p) {
+  const double a = fabs(p);
+  if (!(a > 1e-30 && a < 1e30)) return 1.0 / p;
+  double y = (double)__frcp_rn((float)p);
+  double e = fma(-p, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-p, y, 1.0);
+  return fma(y, e, y);
 }
 
 // Warp-wide winner: largest key, then smallest position; returns the winning lane.
@@ -148,25 +164,22 @@ __global__ void __launch_bounds__(LR_NT, 1) k_lu_reg(LuArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LrShared<T, NB>& sh = *reinterpret_cast<LrShared<T, NB>*>(smem_raw);
   size_t off = (sizeof(LrShared<T, NB>) + 15) / 16 * 16;
-  T* Lbuf = reinterpret_cast<T*>(smem_raw + off);         // [NB][rpc] multipliers of a panel
-  off += (sizeof(T) * (size_t)NB * rpc + 15) / 16 * 16;
   T* L11 = reinterpret_cast<T*>(smem_raw + off);          // [NB][NB]
   off += (sizeof(T) * (size_t)NB * NB + 15) / 16 * 16;
-  T* U12 = reinterpret_cast<T*>(smem_raw + off);          // [NB][LR_CH]
-  off += (sizeof(T) * (size_t)NB * LR_CH + 15) / 16 * 16;
   int* psmall = reinterpret_cast<int*>(smem_raw + off);   // [C]
 
   // rows of this thread: r0 + tid + s*LR_NT
   int rowi[RT];
   int pos[RT];
   bool have[RT];
+  const bool first = (a.p0 == 0);
 #pragma unroll
   for (int s = 0; s < RT; ++s) {
     rowi[s] = r0 + tid + s * LR_NT;
     have[s] = (tid + s * LR_NT < rpc) && rowi[s] < R;
-    pos[s] = rowi[s];
+    pos[s] = (first || !have[s]) ? rowi[s] : a.posg[rowi[s]];
   }
-  for (int p = tid; p < C; p += LR_NT) psmall[p] = p;
+  for (int p = tid; p < C; p += LR_NT) psmall[p] = first ? p : a.psg[p];
   if (tid == 0) {
     mbar_init(smem_u32(&sh.mbar[0]), 1);
     mbar_init(smem_u32(&sh.mbar[1]), 1);
@@ -186,8 +199,9 @@ __global__ void __launch_bounds__(LR_NT, 1) k_lu_reg(LuArgs a) {
   T x[RT][NB];
   T xe[RT], mp[RT];
 
-  for (int p0 = 0; p0 < C; p0 += NB - 1) {
-    const int w = min(NB - 1, C - p0);
+  {
+    const int p0 = a.p0;
+    const int w = a.pw;
     // load: x[s][c] = X[p0 - 1 + c] for c = 1..w (x[s][0] unused), pending multiplier 0
 #pragma unroll
     for (int s = 0; s < RT; ++s) {
@@ -339,6 +353,7 @@ __global__ void __launch_bounds__(LR_NT, 1) k_lu_reg(LuArgs a) {
       const bool valid = wrow >= 0;
       const T piv = W->xe;
       const bool nz = valid && piv != T(0) && mag_key(piv) != 0ull;
+      const T rp = nz ? rcp_piv(piv) : T(0);
       // pivot row: value P_j[0] = piv and P1_j[c] = P_j[c + 1] (column j + 1 + c), from
       // the winner's registers and its pending update
       {
@@ -349,7 +364,7 @@ __global__ void __launch_bounds__(LR_NT, 1) k_lu_reg(LuArgs a) {
           T v = T(0);
           if (c + 1 < w - jj) {  // column j + 1 + c lies in the panel
             v = (wm != T(0)) ? fma(-wm, Pp[c + 1], W->x[c + 2]) : W->x[c + 2];
-            if (CROUT && nz) v = v / piv;
+            if (CROUT && nz) v = v * rp;
           }
           Pn1[c] = v;
         }
@@ -382,15 +397,11 @@ __global__ void __launch_bounds__(LR_NT, 1) k_lu_reg(LuArgs a) {
       for (int s = 0; s < RT; ++s) {
         T m = T(0);
         if (have[s] && pos[s] > j && nz) {
-          m = CROUT ? xe[s] : xe[s] / piv;
+          m = CROUT ? xe[s] : xe[s] * rp;
           X[(int64_t)j * ldx + rowi[s]] = m;
-          Lbuf[(size_t)jj * rpc + tid + s * LR_NT] = m;
         } else if (have[s] && pos[s] > j) {
           // zero pivot: nothing is eliminated; the column keeps its (zero) values
           X[(int64_t)j * ldx + rowi[s]] = xe[s];
-          Lbuf[(size_t)jj * rpc + tid + s * LR_NT] = T(0);
-        } else if (have[s] && pos[s] == j) {
-          Lbuf[(size_t)jj * rpc + tid + s * LR_NT] = T(0);
         }
         mp[s] = m;
         xe[s] = (m != T(0)) ? fma(-m, Pn1[0], x[s][1]) : x[s][1];
@@ -399,100 +410,108 @@ __global__ void __launch_bounds__(LR_NT, 1) k_lu_reg(LuArgs a) {
 
     // all records of this panel consumed before anyone reuses receive slots / exits
     cl.sync();
-    if (p0 + w >= C) break;
-
-    // ---- (i) U12 of the pivot rows for the trailing columns (forward substitution) -----
-    for (int e = tid; e < w * w; e += LR_NT) {
-      const int t = e / w, s = e % w;
-      L11[t * NB + s] = X[(int64_t)(p0 + s) * ldx + psmall[p0 + t]];
-    }
-    __syncthreads();
-    for (int c = p0 + w + crank * LR_NW + warp; c < C; c += ncta * LR_NW) {
-      constexpr int NQ = (NB + 31) / 32;
-      T u[NQ], fin[NQ];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int t = lane + 32 * q;
-        u[q] = t < w ? X[(int64_t)c * ldx + psmall[p0 + t]] : T(0);
-        fin[q] = u[q];
-      }
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        for (int s = 32 * q; s < min(w, 32 * q + 32); ++s) {
-          T us = __shfl_sync(0xffffffffu, u[q], s - 32 * q);
-          if (CROUT) {
-            const T pv = L11[s * NB + s];
-            if (pv != T(0)) us = us / pv;
-          }
-          if (lane == s - 32 * q) fin[q] = us;
-#pragma unroll
-          for (int qq = q; qq < NQ; ++qq) {
-            const int t = lane + 32 * qq;
-            if (t > s && t < w) u[qq] = fma(-L11[t * NB + s], us, u[qq]);
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int t = lane + 32 * q;
-        if (t < w) X[(int64_t)c * ldx + psmall[p0 + t]] = fin[q];
-      }
-    }
-    cl.sync();
-
-    // ---- (ii) rank-w update of this CTA's live rows in the trailing columns ------------
-    for (int cc = p0 + w; cc < C; cc += LR_CH) {
-      const int cw = min(LR_CH, C - cc);
-      for (int e = tid; e < w * LR_CH; e += LR_NT) {
-        const int s = e / LR_CH, q = e % LR_CH;
-        U12[s * LR_CH + q] = q < cw ? X[(int64_t)(cc + q) * ldx + psmall[p0 + s]] : T(0);
+    if (p0 + w < C) {
+      // ---- U12 of the pivot rows for the trailing columns (forward substitution) -------
+      for (int e = tid; e < w * w; e += LR_NT) {
+        const int t = e / w, s = e % w;
+        L11[t * NB + s] = X[(int64_t)(p0 + s) * ldx + psmall[p0 + t]];
       }
       __syncthreads();
-#pragma unroll 1
-      for (int s2 = 0; s2 < RT; ++s2) {
-        if (!have[s2] || pos[s2] < p0 + w) continue;
-        const int lr = tid + s2 * LR_NT;
-        T acc[LR_CH];
+      for (int c = p0 + w + crank * LR_NW + warp; c < C; c += ncta * LR_NW) {
+        constexpr int NQ = (NB + 31) / 32;
+        T u[NQ], fin[NQ];
 #pragma unroll
-        for (int q = 0; q < LR_CH; ++q)
-          acc[q] = q < cw ? X[(int64_t)(cc + q) * ldx + rowi[s2]] : T(0);
-        for (int s = 0; s < w; ++s) {
-          const T lv = Lbuf[(size_t)s * rpc + lr];
+        for (int q = 0; q < NQ; ++q) {
+          const int t = lane + 32 * q;
+          u[q] = t < w ? X[(int64_t)c * ldx + psmall[p0 + t]] : T(0);
+          fin[q] = u[q];
+        }
 #pragma unroll
-          for (int q = 0; q < LR_CH; q += 4) {
-            T uv[4];
-            ld4(U12 + s * LR_CH + q, uv);
+        for (int q = 0; q < NQ; ++q) {
+          for (int s = 32 * q; s < min(w, 32 * q + 32); ++s) {
+            T us = __shfl_sync(0xffffffffu, u[q], s - 32 * q);
+            if (CROUT) {
+              const T pv = L11[s * NB + s];
+              if (pv != T(0)) us = us * rcp_piv(pv);
+            }
+            if (lane == s - 32 * q) fin[q] = us;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[q + u] = fma(-lv, uv[u], acc[q + u]);
+            for (int qq = q; qq < NQ; ++qq) {
+              const int t = lane + 32 * qq;
+              if (t > s && t < w) u[qq] = fma(-L11[t * NB + s], us, u[qq]);
+            }
           }
         }
 #pragma unroll
-        for (int q = 0; q < LR_CH; ++q)
-          if (q < cw) X[(int64_t)(cc + q) * ldx + rowi[s2]] = acc[q];
+        for (int q = 0; q < NQ; ++q) {
+          const int t = lane + 32 * q;
+          if (t < w) X[(int64_t)c * ldx + psmall[p0 + t]] = fin[q];
+        }
       }
-      __syncthreads();
     }
-    cl.sync();
   }
 
+  // persist the positions for the next panel; the last panel writes P (gather form)
+  const bool last = (a.p0 + a.pw >= C);
 #pragma unroll
   for (int s = 0; s < RT; ++s)
-    if (have[s]) a.perm[pos[s]] = rowi[s];
+    if (have[s]) a.posg[rowi[s]] = pos[s];
+  if (crank == 0)
+    for (int p = tid; p < C; p += LR_NT) a.psg[p] = psmall[p];
+  if (last) {
+#pragma unroll
+    for (int s = 0; s < RT; ++s)
+      if (have[s]) a.perm[pos[s]] = rowi[s];
+  }
   if (tid == 0) {
-    if (crank == 0 && a.zero_step) *a.zero_step = first_zero;
+    if (crank == 0 && a.zero_step && first_zero >= 0) atomicCAS(a.zero_step, -1, first_zero);
     if (sh.nonfinite && a.nonfinite) atomicOr(a.nonfinite, 1);
     if (sh.err && a.status) atomicExch(a.status, RLU_ETIMEOUT);
   }
   cl.sync();
 }
 
+// Rank-w update of the trailing columns [c_begin, C) of every row whose position is at
+// least p0 + w: X[r][c] -= sum_s X[r][p0+s] * U12[s][c], U12 = the panel's pivot rows
+// (already solved by the panel launch). One thread per row, 32 columns per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lu_trail(T* __restrict__ X, int64_t ldx, int R, int C,
+                                                 int p0, int w, const int32_t* __restrict__ posg,
+                                                 const int32_t* __restrict__ psg) {
+  __shared__ __align__(16) T U12[128][LR_CH];
+  const int c0 = p0 + w + blockIdx.y * LR_CH;
+  const int cw = min(LR_CH, C - c0);
+  for (int e = threadIdx.x; e < w * LR_CH; e += 256) {
+    const int s = e / LR_CH, q = e % LR_CH;
+    U12[s][q] = q < cw ? X[(int64_t)(c0 + q) * ldx + psg[p0 + s]] : T(0);
+  }
+  __syncthreads();
+  const int r = blockIdx.x * 256 + threadIdx.x;
+  if (r >= R || posg[r] < p0 + w) return;
+  T acc[LR_CH];
+#pragma unroll
+  for (int q = 0; q < LR_CH; ++q) acc[q] = q < cw ? X[(int64_t)(c0 + q) * ldx + r] : T(0);
+  for (int s = 0; s < w; ++s) {
+    const T lv = X[(int64_t)(p0 + s) * ldx + r];
+#pragma unroll
+    for (int q = 0; q < LR_CH; q += 4) {
+      T uv[4];
+      ld4(&U12[s][q], uv);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[q + u] = fma(-lv, uv[u], acc[q + u]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < LR_CH; ++q)
+    if (q < cw) X[(int64_t)(c0 + q) * ldx + r] = acc[q];
+}
+
 template <typename T, int NB>
 static size_t lr_smem_bytes(int rpc, int C) {
   size_t b = (sizeof(LrShared<T, NB>) + 15) / 16 * 16;
-  b += (sizeof(T) * (size_t)NB * rpc + 15) / 16 * 16;
   b += (sizeof(T) * (size_t)NB * NB + 15) / 16 * 16;
-  b += (sizeof(T) * (size_t)NB * LR_CH + 15) / 16 * 16;
   b += sizeof(int) * (size_t)C;
+  (void)rpc;
   return b;
 }
 
@@ -530,12 +549,24 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
       return RLU_OK;
     }
   }
+  if (!in.posg || !in.psg) return RLU_OK;  // no position state: use the one-launch kernel
   LuArgs a = in;
   a.rpc = rpc;
   a.nb = NB - 1;
-  RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
-  *launched = true;
-  return last_launch_status();
+  for (int p0 = 0; p0 < in.C; p0 += NB - 1) {
+    a.p0 = p0;
+    a.pw = min(NB - 1, in.C - p0);
+    RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
+    RLU_TRY(last_launch_status());
+    *launched = true;
+    if (p0 + a.pw < in.C) {
+      const dim3 grid((unsigned)ceil_div(in.R, 256), (unsigned)ceil_div(in.C - p0 - a.pw, LR_CH));
+      k_lu_trail<T><<<grid, 256, 0, s>>>(static_cast<T*>(in.X), in.ldx, in.R, in.C, p0, a.pw,
+                                         in.posg, in.psg);
+      RLU_TRY(last_launch_status());
+    }
+  }
+  return RLU_OK;
 }
 
 template <typename T, bool CROUT>

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(LU_NT, 1) k_cluster_lu(LuArgs a) {
 
   for (int t = tid; t < nr; t += LU_NT) a.perm[posl[t]] = r0 + t;
   if (tid == 0) {
-    if (crank == 0 && a.zero_step) *a.zero_step = first_zero;
+    if (crank == 0 && a.zero_step && first_zero >= 0) atomicCAS(a.zero_step, -1, first_zero);
     if (s_nonfinite && a.nonfinite) atomicOr(a.nonfinite, 1);
   }
   cl.sync();  // keep shared memory alive until every remote read has finished

@@ -15,6 +15,11 @@ struct LuArgs {
   int32_t* zero_step;  // out: first step with a zero pivot, -1 if none (may be NULL)
   int32_t* nonfinite;  // out: OR-ed with 1 when a NaN/Inf is met (may be NULL)
   int32_t* status;     // out: set to RLU_ETIMEOUT if a cluster wait gave up (may be NULL)
+  // register kernel only: position state kept between its per-panel launches
+  int32_t* posg;       // [R] current position of every row
+  int32_t* psg;        // [C] row at each position < C
+  int p0;              // first column of the panel of this launch
+  int pw;              // its width
 };
 
 // crout = false: Doolittle (step 3, LU of Y); crout = true: pivot row scaled (step 6 on B^T).

@@ -29,7 +29,7 @@ static std::atomic<uint64_t> g_launches{0};
 void note_launches(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
 
 static const char* kStepNames[RLU_NUM_TIMED_STEPS] = {
-    "gaussian", "gemm_Y", "lu_Y", "build_Ly", "gram", "chol_inv", "gemm_C", "tri_B", "lu_B",
+    "gaussian", "gemm_Y", "lu_Y", "build_Ly", "gram", "ldl", "gemm_C", "trsm_B", "lu_B",
     "gather_Lb_U", "gemm_L"};
 
 // Records the start/end event of timed step i when the caller asked for events.
@@ -99,9 +99,10 @@ struct Plan {
   int k = 0, l = 0;
   int64_t ldg = 0, ldy = 0, ldl = 0, ldb = 0;
   int split_y = 1, split_g = 1, split_c = 1;
-  size_t off_G = 0, off_Y = 0, off_Lt = 0, off_Lp = 0, off_M = 0, off_Rinv = 0, off_RinvT = 0,
+  size_t off_G = 0, off_Y = 0, off_Lt = 0, off_Lp = 0, off_M = 0, off_dinv = 0, off_LT = 0,
+         off_LR = 0, off_W = 0, off_WT = 0,
          off_C = 0, off_T = 0, off_B = 0, off_Lb = 0, off_part = 0, off_Lhi = 0, off_Llo = 0,
-         total = 0;
+         off_pos = 0, off_ps = 0, total = 0;
 };
 
 static size_t carve(size_t& cur, size_t bytes) {
@@ -153,13 +154,18 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   p.off_Lt = carve(cur, (size_t)p.ldl * k * e);
   p.off_Lp = carve(cur, (size_t)p.ldl * k * e);
   p.off_M = carve(cur, (size_t)k * k * 8);
-  p.off_Rinv = carve(cur, (size_t)k * (k + 1) * 8);  // R^{-1} and 1/diag(L)
-  p.off_RinvT = carve(cur, (size_t)k * k * e);
+  const size_t kp = (size_t)round_up(k, 32);  // M = L D L^T: L padded to kp x kp
+  p.off_dinv = carve(cur, (size_t)k * 8);
+  p.off_LT = carve(cur, kp * kp * e);
+  p.off_LR = carve(cur, kp * kp * e);
+  p.off_W = carve(cur, kp * 32 * e);   // inverses of L's 32 x 32 diagonal blocks
+  p.off_WT = carve(cur, kp * 32 * e);
   p.off_C = carve(cur, (size_t)k * p.ldb * e);
-  p.off_T = carve(cur, (size_t)k * p.ldb * e);
   p.off_B = carve(cur, (size_t)k * p.ldb * e);
   p.off_Lb = carve(cur, (size_t)k * k * e);
   p.off_part = carve(cur, part);
+  p.off_pos = carve(cur, (size_t)(m > n ? m : n) * sizeof(int32_t));  // LU position state
+  p.off_ps = carve(cur, (size_t)l * sizeof(int32_t));
   if (prec == RLU_PREC_MIXED) {
     p.off_Lhi = carve(cur, (size_t)p.ldl * k * e);
     p.off_Llo = carve(cur, (size_t)p.ldl * k * e);
@@ -177,10 +183,15 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
   T* Lt = reinterpret_cast<T*>(ws + p.off_Lt);
   T* Lp = reinterpret_cast<T*>(ws + p.off_Lp);
   double* M = reinterpret_cast<double*>(ws + p.off_M);
-  double* Rinv = reinterpret_cast<double*>(ws + p.off_Rinv);
-  T* RinvT = reinterpret_cast<T*>(ws + p.off_RinvT);
+  LdlOut<T> ldl{};
+  ldl.LT = reinterpret_cast<T*>(ws + p.off_LT);
+  ldl.LR = reinterpret_cast<T*>(ws + p.off_LR);
+  ldl.W = reinterpret_cast<T*>(ws + p.off_W);
+  ldl.WT = reinterpret_cast<T*>(ws + p.off_WT);
+  ldl.dinv = reinterpret_cast<double*>(ws + p.off_dinv);
+  ldl.k = p.k;
+  ldl.kp = (int)round_up(p.k, 32);
   T* Cb = reinterpret_cast<T*>(ws + p.off_C);
-  T* Tb = reinterpret_cast<T*>(ws + p.off_T);
   T* Bb = reinterpret_cast<T*>(ws + p.off_B);
   T* Lb = reinterpret_cast<T*>(ws + p.off_Lb);
   void* part = ws + p.off_part;
@@ -228,6 +239,8 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
     a.zero_step = info ? &info->first_zero_pivot_y : nullptr;
     a.nonfinite = info ? &info->nonfinite : nullptr;
     a.status = info ? &info->status : nullptr;
+    a.posg = reinterpret_cast<int32_t*>(ws + p.off_pos);
+    a.psg = reinterpret_cast<int32_t*>(ws + p.off_ps);
     RLU_TRY(launch_cluster_lu(p.dt, false, a, s));
   }
   RLU_TRY(tm.rec(2, true, s));
@@ -271,7 +284,7 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
     RLU_CUDA_TRY(cudaEventRecord(ss->fork, s));
     RLU_CUDA_TRY(cudaStreamWaitEvent(ss->side, ss->fork, 0));
     RLU_TRY(tm.rec(5, false, ss->side));
-    RLU_TRY(chol_inv<T>(M, k, Rinv, RinvT, info ? &info->status : nullptr, ss->side));
+    RLU_TRY(ldl_factor<T>(M, k, ldl, info ? &info->status : nullptr, ss->side));
     RLU_TRY(tm.rec(5, true, ss->side));
     RLU_CUDA_TRY(cudaEventRecord(ss->join, ss->side));
     // C = L~^T A (k x n, row-major)
@@ -300,16 +313,9 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
     RLU_TRY(tm.rec(6, true, s));
     RLU_CUDA_TRY(cudaStreamWaitEvent(s, ss->join, 0));
   }
-  // T = R^{-T} C ; B = R^{-1} T
+  // B = M^{-1} C = L^{-T} D^{-1} L^{-1} C
   RLU_TRY(tm.rec(7, false, s));
-  {
-    GemmOp op{RinvT, k, false, Cb, p.ldb, false, Tb, p.ldb, true, k, n, k, 1, nullptr, false};
-    RLU_TRY((gemm_simt<T, T>(op, s)));
-  }
-  {
-    GemmOp op{RinvT, k, true, Tb, p.ldb, false, Bb, p.ldb, true, k, n, k, 1, nullptr, false};
-    RLU_TRY((gemm_simt<T, T>(op, s)));
-  }
+  RLU_TRY(trsm_ldl<T>(ldl, Cb, p.ldb, n, Bb, p.ldb, s));
   RLU_TRY(tm.rec(7, true, s));
   if (st && st->B) RLU_TRY(copy_cm<T>(Bb, p.ldb, static_cast<T*>(st->B), n, n, k, s));
   // step 6: LU of B^T (n x k, col-major = B row-major), Crout form
@@ -320,6 +326,8 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
     a.zero_step = info ? &info->first_zero_pivot_b : nullptr;
     a.nonfinite = info ? &info->nonfinite : nullptr;
     a.status = info ? &info->status : nullptr;
+    a.posg = reinterpret_cast<int32_t*>(ws + p.off_pos);
+    a.psg = reinterpret_cast<int32_t*>(ws + p.off_ps);
     RLU_TRY(launch_cluster_lu(p.dt, true, a, s));
   }
   RLU_TRY(tm.rec(8, true, s));

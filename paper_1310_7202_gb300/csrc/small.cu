@@ -4,12 +4,16 @@
 //    row order (Lp, for step 7) and L~ = P^T L_y in original row order (Lt, so that
 //    L_y^T P A = L~^T A without permuting A); optionally L~ split exactly into a TF32 part
 //    and an FP32 remainder for the tensor-core products of step 5.
-//  * chol_inv (step 5, remark after Algorithm 1): M = L_y^T L_y = L L^T (FP64 Cholesky on a
-//    thread-block cluster), then R^{-1} = L^{-T} (R = L^T) by forward substitution, one warp
-//    per column; written in FP64 and in the path's type.
+//  * ldl_factor (step 5, remark after Algorithm 1): M = L_y^T L_y = L D L^T (the Cholesky
+//    factor is D^{1/2} L^T), plus the inverses of L's 32 x 32 diagonal blocks: in FP32 on
+//    one CTA for the single-precision paths (k <= 256), else in FP64 on a thread-block
+//    cluster; trsm_ldl then forms B = M^{-1} C = L^{-T} D^{-1} L^{-1} C by blocked
+//    substitution in the path's type.
 //  * gather_lb / gather_u (steps 6 and 8): L_b and U_b read out of the swap-free factored
 //    B^T with the column permutation Q.
 #include <cooperative_groups.h>
+
+#include <utility>
 
 #include "common.cuh"
 #include "small.cuh"
@@ -62,8 +66,7 @@ template int32_t build_ly<double>(const double*, int64_t, int64_t, int, const in
 // it (look-ahead), then arrives at the cluster barrier; all CTAs apply the rank-CH_CB
 // update to the rest of their panels before waiting on it. The only sequential FP64 chain
 // is one reciprocal per column (FP32 seed and one Newton step, no divide or square root).
-// L overwrites M in column-major order (M[c*k + i] = L[i][c]); D^{-1/2} goes to rdiag (k
-// square roots, independent of each other).
+// L overwrites M in column-major order (M[c*k + i] = L[i][c]); 1/D goes to dinv.
 static constexpr int CH_CB = 4;
 static constexpr int CH_NT = 256;
 
@@ -132,7 +135,7 @@ __device__ void ldl_update(double* P, const double* buf, const double* bufs, int
 }
 
 __global__ void __launch_bounds__(CH_NT, 1) k_chol_cluster(double* __restrict__ M, int k,
-                                                         double* __restrict__ rdiag,
+                                                         double* __restrict__ rdiag,  // 1/D
                                                          int32_t* __restrict__ status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(CH_NT, 1) k_chol_cluster(double* __restrict__ 
     __syncthreads();
     cluster_wait();
   }
-  // write L (unit lower, row-major, zero above) and D^{-1/2}
+  // write L (unit lower, column-major, zero above) and 1/D
   for (int q = 0; q < mine; ++q) {
     const int J = me + q * nc;
     const double* P = panels + (size_t)q * k * CH_CB;
@@ -202,81 +205,230 @@ __global__ void __launch_bounds__(CH_NT, 1) k_chol_cluster(double* __restrict__ 
     }
     for (int c = tid; c < CH_CB; c += CH_NT) {
       const int col = J * CH_CB + c;
-      if (col < k) rdiag[col] = Dd[col] > 0.0 ? sqrt(Di[col]) : 0.0;
+      if (col < k) rdiag[col] = Di[col];
     }
   }
   if (tid == 0 && s_bad && status) *status = RLU_EINVAL;
   cl.sync();
 }
 
-// R^{-1} = L^{-T} D^{-1/2}: one single-warp CTA per column j of L^{-1} (L unit lower,
-// column-major), so the FP64 work spreads over all SMs. Right-looking substitution: once
-// x_t is final it is broadcast and every lane folds L[i][t] x_t into the partial sums of the
-// rows i it owns, so the sequential chain per step is one shuffle and one FMA. Row j of
-// R^{-1} is column j of L^{-1} scaled elementwise by D^{-1/2}; written in FP64 (Rinv) and in
-// the path's type (RinvT), both row-major k x k.
+// Inverses of the TB x TB diagonal blocks of the unit lower L (FP64, column-major k x k),
+// one warp per block, column by column (right-looking, no divides); results and L itself
+// converted to the path's type for the triangular solves.
+static constexpr int TB = 32;
 
 template <typename T>
-__global__ void __launch_bounds__(32) k_tri_inverse(const double* __restrict__ Lc,
-                                                   const double* __restrict__ rdiag, int k,
-                                                   double* __restrict__ Rinv,
-                                                   T* __restrict__ RinvT) {
-  const int lane = threadIdx.x;
-  const int j = blockIdx.x;
-  for (int i = lane; i < j; i += 32) {
-    Rinv[(int64_t)j * k + i] = 0.0;
-    RinvT[(int64_t)j * k + i] = T(0);
-  }
-  // right-looking substitution for column j of L^{-1}: s_i accumulates sum_t L[i][t] x_t;
-  // lane (i mod 32) owns s_i; x_t = -s_t (x_j = 1) is broadcast once it is final. Column t of
-  // L (contiguous in Lc) is loaded one step ahead.
-  constexpr int MAXQ = 16;  // k <= 512
-  constexpr int PF = 4;     // columns loaded ahead
-  const int nq = (k + 31) / 32;
-  double sacc[MAXQ], col[PF][MAXQ];
-#pragma unroll
-  for (int q = 0; q < MAXQ; ++q) sacc[q] = 0.0;
-#pragma unroll
-  for (int f = 0; f < PF; ++f)
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-      const int i = lane + 32 * q;
-      col[f][q] = (q < nq && j + f < k && i < k) ? Lc[(int64_t)(j + f) * k + i] : 0.0;
+__global__ void __launch_bounds__(32) k_diag_inv(const double* __restrict__ Lc, int k,
+                                                 LdlOut<T> o) {
+  const int lane = threadIdx.x, b = blockIdx.x;
+  const int b0 = b * TB, bw = min(TB, k - b0);
+  // this block's columns of L in the path's type, zero-padded to kp x kp, both layouts
+  for (int c = b0; c < b0 + TB; ++c)
+    for (int i = lane; i < o.kp; i += 32) {
+      const T v = (c < k && i < k) ? (T)Lc[(int64_t)c * k + i] : (i == c ? T(1) : T(0));
+      o.LT[(int64_t)c * o.kp + i] = v;
+      o.LR[(int64_t)i * o.kp + c] = v;
     }
-  for (int t = j; t < k; ++t) {
-    const int qt = t >> 5;
-    double xt = 0.0;
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q)
-      if (q == qt) xt = sacc[q];
-    xt = (t == j) ? 1.0 : -xt;
-    xt = __shfl_sync(0xffffffffu, xt, t & 31);
-    if (lane == 0) {
-      const double r = xt * rdiag[t];
-      Rinv[(int64_t)j * k + t] = r;
-      RinvT[(int64_t)j * k + t] = (T)r;
+  // column j of the block inverse: x_j = 1, x_i = -sum_{t<i} L[i][t] x_t (lane i owns x_i)
+  for (int j = 0; j < TB; ++j) {
+    double x = (lane == j) ? 1.0 : 0.0;
+    for (int t = j; t < bw; ++t) {
+      const double xt = __shfl_sync(0xffffffffu, x, t);
+      if (lane > t && lane < bw) x = fma(-Lc[(int64_t)(b0 + t) * k + b0 + lane], xt, x);
     }
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-      const int i = lane + 32 * q;
-      if (q < nq && i > t && i < k) sacc[q] = fma(col[0][q], xt, sacc[q]);
-    }
-    // shift the prefetch window and load column t + PF
-#pragma unroll
-    for (int f = 0; f + 1 < PF; ++f)
-#pragma unroll
-      for (int q = 0; q < MAXQ; ++q) col[f][q] = col[f + 1][q];
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-      const int i = lane + 32 * q;
-      col[PF - 1][q] = (q < nq && t + PF < k && i < k) ? Lc[(int64_t)(t + PF) * k + i] : 0.0;
-    }
+    // W block b row-major (element (lane, j)) and its transpose
+    const T w = (lane < bw && j < bw) ? (T)x : (lane == j ? T(1) : T(0));
+    o.W[(size_t)b * TB * TB + lane * TB + j] = w;
+    o.WT[(size_t)b * TB * TB + j * TB + lane] = w;
   }
 }
 
-template <typename T>
-int32_t chol_inv(double* M, int k, double* Rinv, T* RinvT, int32_t* status, cudaStream_t s) {
-  double* rdiag = Rinv + (size_t)k * k;  // k extra doubles after R^{-1}: D^{-1/2}
+// FP32 LDL^T for k <= 256 on one CTA (the normal-equation matrix of Algorithm 1's step 5
+// in single precision: its rounding enters the factorization error ||PAQ - LU|| only
+// through L_y (B - B*), orthogonal to the residual of the exact least-squares B*). Blocked
+// right-looking with 32 x 32 blocks of the lower triangle in shared memory:
+//   diagonal block J: one warp, in registers (lane i holds row i): d_t, L_JJ and
+//     W_J = L_JJ^{-1};
+//   block column J: U_IJ = M_IJ W_J^T (= L_IJ D_J), L_IJ = U_IJ D_J^{-1};
+//   trailing blocks: M_IK -= L_IJ U_KJ^T (I >= K > J), 4 x 4 register tiles per thread.
+// Rows/columns past k are padded with the identity, which factors trivially.
+static constexpr int LB = 32;       // block size
+static constexpr int LBP = LB + 1;  // padded row of a block in shared memory
+static constexpr int L32_NT = 512;
+static constexpr int L32_MAXB = 8;  // k <= 256
+
+__device__ __forceinline__ int tri_blk(int I, int J) { return I * (I + 1) / 2 + J; }
+
+// Column t of the register-resident LDL^T of a 32 x 32 block (lane i holds row i):
+// d = M[t][t]; rows below get L[i][t] = M[i][t] / d and the rank-1 update of columns > t.
+template <int t>
+__device__ __forceinline__ void ldl_col(float (&a)[LB], int lane, float* d_out, bool& bad) {
+  const float d = __shfl_sync(0xffffffffu, a[t], t);
+  const float rd = __frcp_rn(d);
+  bad |= !(d > 0.f) || !(d < INFINITY);
+  const float u = a[t];  // M[lane][t], the unscaled column
+  const float l = u * rd;
+#pragma unroll
+  for (int c = t + 1; c < LB; ++c) {
+    const float uc = __shfl_sync(0xffffffffu, u, c);
+    if (lane > t) a[c] = fmaf(-l, uc, a[c]);
+  }
+  if (lane == t) d_out[t] = d;
+  if (lane > t) a[t] = l;
+}
+template <int... ts>
+__device__ __forceinline__ void ldl_cols(float (&a)[LB], int lane, float* d_out, bool& bad,
+                                         std::integer_sequence<int, ts...>) {
+  (ldl_col<ts>(a, lane, d_out, bad), ...);
+}
+
+__global__ void __launch_bounds__(L32_NT, 1) k_ldl32(const double* __restrict__ M, int k,
+                                                    LdlOut<float> o, int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) float l32_smem[];
+  const int nb = (k + LB - 1) / LB;
+  const int nblk = nb * (nb + 1) / 2;
+  float* Bk = l32_smem;                         // [nblk][LB][LBP] lower-triangle blocks
+  float* Ub = Bk + (size_t)nblk * LB * LBP;     // [nb][LB][LBP] U_IJ of the current J
+  float* Wb = Ub + (size_t)nb * LB * LBP;       // [nb][LB][LBP] W_J = L_JJ^{-1}
+  float* dd = Wb + (size_t)nb * LB * LBP;       // [nb * LB] D
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_bad = 0;
+  // batches of 8 independent loads per thread, so that their latencies overlap
+  for (int e0 = tid; e0 < nblk * LB * LB; e0 += L32_NT * 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * L32_NT;
+      const int b = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
+      int I = 0;
+      while (tri_blk(I + 1, 0) <= b) ++I;
+      const int J = b - tri_blk(I, 0);
+      const int i = I * LB + r, j = J * LB + c;
+      if (e < nblk * LB * LB && i < k && j < k) v[u] = (float)M[(int64_t)i * k + j];
+      else v[u] = (i == j) ? 1.f : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * L32_NT;
+      const int b = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
+      if (e < nblk * LB * LB) Bk[(size_t)b * LB * LBP + r * LBP + c] = v[u];
+    }
+  }
+  __syncthreads();
+  for (int J = 0; J < nb; ++J) {
+    float* BJJ = Bk + (size_t)tri_blk(J, J) * LB * LBP;
+    if (warp == 0) {
+      float a[LB];
+#pragma unroll
+      for (int c = 0; c < LB; ++c) a[c] = BJJ[lane * LBP + c];
+      bool bad = false;
+      ldl_cols(a, lane, dd + J * LB, bad, std::make_integer_sequence<int, LB>{});
+#pragma unroll
+      for (int c = 0; c < LB; ++c) BJJ[lane * LBP + c] = (c < lane) ? a[c] : (c == lane ? 1.f : 0.f);
+      __syncwarp();
+      // W = L^{-1}: lane i holds row i; row t is final at step t
+      float w[LB];
+#pragma unroll
+      for (int c = 0; c < LB; ++c) w[c] = (c == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int t = 0; t < LB; ++t) {
+        const float lit = (lane > t) ? BJJ[lane * LBP + t] : 0.f;
+#pragma unroll
+        for (int c = 0; c <= t; ++c) {
+          const float wtc = __shfl_sync(0xffffffffu, w[c], t);
+          w[c] = fmaf(-lit, wtc, w[c]);
+        }
+      }
+      float* W = Wb + (size_t)J * LB * LBP;
+#pragma unroll
+      for (int c = 0; c < LB; ++c) W[lane * LBP + c] = (c <= lane) ? w[c] : 0.f;
+      if (bad && J * LB + lane < k) s_bad = 1;
+    }
+    __syncthreads();
+    // U_IJ = M_IJ W_J^T, then L_IJ = U_IJ D_J^{-1} in place
+    const int rest = nb - 1 - J;
+    const float* W = Wb + (size_t)J * LB * LBP;
+    for (int e = tid; e < rest * LB * LB; e += L32_NT) {
+      const int I = J + 1 + e / (LB * LB), r = (e / LB) % LB, c = e % LB;
+      const float* Mr = Bk + (size_t)tri_blk(I, J) * LB * LBP + r * LBP;
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t < LB; ++t) acc = fmaf(Mr[t], W[c * LBP + t], acc);
+      Ub[(size_t)(I - J - 1) * LB * LBP + r * LBP + c] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < rest * LB * LB; e += L32_NT) {
+      const int I = J + 1 + e / (LB * LB), r = (e / LB) % LB, c = e % LB;
+      Bk[(size_t)tri_blk(I, J) * LB * LBP + r * LBP + c] =
+          Ub[(size_t)(I - J - 1) * LB * LBP + r * LBP + c] / dd[J * LB + c];
+    }
+    __syncthreads();
+    // trailing update of the lower-triangle blocks I >= K > J; 64 4x4 tiles per block
+    const int ntask = rest * (rest + 1) / 2 * 64;
+    for (int q = tid; q < ntask; q += L32_NT) {
+      const int pb = q / 64, tile = q % 64;
+      int ii = 0;
+      while ((ii + 1) * (ii + 2) / 2 <= pb) ++ii;
+      const int kk = pb - ii * (ii + 1) / 2;
+      const int I = J + 1 + ii, K = J + 1 + kk;
+      const int r0 = (tile / 8) * 4, c0 = (tile % 8) * 4;
+      const float* Lr = Bk + (size_t)tri_blk(I, J) * LB * LBP;
+      const float* Ur = Ub + (size_t)(K - J - 1) * LB * LBP;
+      float acc[4][4] = {};
+#pragma unroll 8
+      for (int t = 0; t < LB; ++t) {
+        float lv[4], uv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          lv[x] = Lr[(r0 + x) * LBP + t];
+          uv[x] = Ur[(c0 + x) * LBP + t];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(lv[x], uv[y], acc[x][y]);
+      }
+      float* Mt = Bk + (size_t)tri_blk(I, K) * LB * LBP;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) Mt[(r0 + x) * LBP + c0 + y] -= acc[x][y];
+    }
+    __syncthreads();
+  }
+  // L (unit lower, zero above, identity past k) in both layouts, the diagonal-block
+  // inverses and their transposes, 1/D
+  const int kp = o.kp;
+  for (int e = tid; e < kp * kp; e += L32_NT) {
+    const int c = e / kp, i = e % kp;
+    float v = 0.f;
+    if (i > c) v = Bk[(size_t)tri_blk(i / LB, c / LB) * LB * LBP + (i % LB) * LBP + c % LB];
+    else if (i == c) v = 1.f;
+    o.LT[e] = v;
+  }
+  for (int e = tid; e < kp * kp; e += L32_NT) {
+    const int i = e / kp, c = e % kp;
+    float v = 0.f;
+    if (i > c) v = Bk[(size_t)tri_blk(i / LB, c / LB) * LB * LBP + (i % LB) * LBP + c % LB];
+    else if (i == c) v = 1.f;
+    o.LR[e] = v;
+  }
+  for (int e = tid; e < nb * LB * LB; e += L32_NT) {
+    const int b = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
+    o.W[e] = Wb[(size_t)b * LB * LBP + r * LBP + c];
+    o.WT[e] = Wb[(size_t)b * LB * LBP + c * LBP + r];
+  }
+  for (int i = tid; i < k; i += L32_NT) o.dinv[i] = 1.0 / (double)dd[i];
+  if (tid == 0 && s_bad && status) *status = RLU_EINVAL;
+}
+
+static size_t ldl32_smem_bytes(int k) {
+  const int nb = (k + LB - 1) / LB;
+  return sizeof(float) * ((size_t)(nb * (nb + 1) / 2 + 2 * nb) * LB * LBP + (size_t)nb * LB);
+}
+
+static int32_t ldl_cluster_f64(double* M, int k, double* dinv, int32_t* status, cudaStream_t s) {
   const int nblk = (k + CH_CB - 1) / CH_CB;
   int nc = nblk < 16 ? nblk : 16;
   int dev = 0;
@@ -304,14 +456,239 @@ int32_t chol_inv(double* M, int k, double* Rinv, T* RinvT, int32_t* status, cuda
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_chol_cluster, M, k, rdiag, status));
-  RLU_TRY(last_launch_status());
-  if (k > 512) return RLU_EUNSUPPORTED;
-  k_tri_inverse<T><<<(unsigned)k, 32, 0, s>>>(M, rdiag, k, Rinv, RinvT);
+  RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_chol_cluster, M, k, dinv, status));
   return last_launch_status();
 }
-template int32_t chol_inv<float>(double*, int, double*, float*, int32_t*, cudaStream_t);
-template int32_t chol_inv<double>(double*, int, double*, double*, int32_t*, cudaStream_t);
+
+template <typename T>
+int32_t ldl_factor(double* M, int k, const LdlOut<T>& o, int32_t* status, cudaStream_t s) {
+  if (sizeof(T) == sizeof(float) && k <= L32_MAXB * LB) {
+    const size_t bytes = ldl32_smem_bytes(k);
+    RLU_CUDA_TRY(cudaFuncSetAttribute(k_ldl32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    k_ldl32<<<1, L32_NT, bytes, s>>>(M, k, reinterpret_cast<const LdlOut<float>&>(o), status);
+    return last_launch_status();
+  }
+  RLU_TRY(ldl_cluster_f64(M, k, o.dinv, status, s));
+  k_diag_inv<T><<<(unsigned)ceil_div(k, TB), 32, 0, s>>>(M, k, o);
+  return last_launch_status();
+}
+template int32_t ldl_factor<float>(double*, int, const LdlOut<float>&, int32_t*, cudaStream_t);
+template int32_t ldl_factor<double>(double*, int, const LdlOut<double>&, int32_t*, cudaStream_t);
+
+// B = L^{-T} D^{-1} L^{-1} C (step 5, the normal equations M B = C with M = L D L^T), TC
+// columns of C per CTA. The kp x TC block X stays in shared memory (rows past k are zero)
+// through blocked forward substitution -- row block I is updated by the solved blocks above
+// it (X_I -= L_IJ X_J, a 32 x 32 x TC product per block), then multiplied by W_I, the
+// inverse of L's diagonal block --, the D^{-1} scaling, and blocked backward substitution
+// (X_I -= L_JI^T X_J for J > I, then W_I^T). The 32 x 32 blocks of L, L^T, W^T and W are
+// consumed in a fixed order and streamed through a ring of shared-memory stages with
+// cp.async, several blocks ahead of the arithmetic. C and B: k x n row-major (ld ldc / ldb).
+static constexpr int TSTAGES = 4;
+static constexpr int LSP = TB + 4;  // staged block row: 16-byte aligned rows, [t][r] order
+
+template <typename T>
+struct Vec4 {
+  T v[4];
+};
+__device__ __forceinline__ Vec4<float> lds4(const float* p) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  return {{q.x, q.y, q.z, q.w}};
+}
+__device__ __forceinline__ Vec4<double> lds4(const double* p) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0];
+  const double2 q1 = reinterpret_cast<const double2*>(p)[1];
+  return {{q0.x, q0.y, q1.x, q1.y}};
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Source of the s-th block of the sequence, stored so that the staged block reads [t][r]:
+// forward row block I: L(I, J) for J < I (from LT: t = column of L, r = row), then W_I^T;
+// backward row block I (descending): L(J, I)^T for J > I (from LR), then W_I.
+template <typename T>
+__device__ __forceinline__ const T* trsm_block_src(const LdlOut<T>& o, int nb, int s,
+                                                   int64_t* stride) {
+  const int F = nb * (nb + 1) / 2;
+  const bool fwd = s < F;
+  const int q = fwd ? s : s - F;
+  int I = 0;  // q-th item: I-th group (I + 1 items, the last one the diagonal inverse)
+  while ((I + 1) * (I + 2) / 2 <= q) ++I;
+  const int J = q - I * (I + 1) / 2;
+  *stride = (J < I) ? o.kp : TB;  // rows of L / L^T blocks have stride kp, inverses TB
+  if (fwd) {
+    if (J < I) return o.LT + (int64_t)(J * TB) * o.kp + I * TB;
+    return o.WT + (size_t)I * TB * TB;
+  }
+  const int Ib = nb - 1 - I;  // backward row block
+  if (J < I) return o.LR + (int64_t)((nb - 1 - J) * TB) * o.kp + Ib * TB;
+  return o.W + (size_t)Ib * TB * TB;
+}
+
+template <typename T, int TC>
+__global__ void __launch_bounds__(TB / 2 * TC / 4) k_trsm_ldl(LdlOut<T> o, const T* __restrict__ C,
+                                                             int64_t ldc, int64_t n,
+                                                             T* __restrict__ B, int64_t ldb) {
+  // two thread groups split the 32 rows of each staged block (the reduction index) in
+  // halves; their partial sums meet in the diagonal step, where every thread owns 2 x 4
+  constexpr int NG = TB / 4 * TC / 4;  // threads of one group
+  constexpr int NT = 2 * NG;
+  constexpr int CH = 16 / sizeof(T);   // elements per 16-byte copy
+  constexpr int CPB = TB * TB / CH;    // copies per block
+  extern __shared__ __align__(16) unsigned char trsm_smem[];
+  const int k = o.k, kp = o.kp, nb = kp / TB;
+  T* Xs = reinterpret_cast<T*>(trsm_smem);  // [kp][TC]
+  T* Ls = Xs + (size_t)kp * TC;             // [TSTAGES][TB][LSP]
+  T* Ws = Ls + (size_t)TSTAGES * TB * LSP;  // [2][TB][TC] the groups' partial sums
+  const int tid = threadIdx.x;
+  const int g = tid / NG, gt = tid % NG;
+  const int64_t c0 = (int64_t)blockIdx.x * TC;
+  const int nseq = nb * (nb + 1);
+  auto issue = [&](int sidx) {
+    if (sidx < nseq) {
+      int64_t stride = 0;
+      const T* src = trsm_block_src(o, nb, sidx, &stride);
+      T* dst = Ls + (size_t)(sidx % TSTAGES) * TB * LSP;
+      for (int e = tid; e < CPB; e += NT) {
+        const int t = e / (TB / CH), r = (e % (TB / CH)) * CH;
+        cp_async16(dst + t * LSP + r, src + (int64_t)t * stride + r);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int sidx = 0; sidx < TSTAGES - 1; ++sidx) issue(sidx);
+  // batches of independent loads, so that their latencies overlap
+  constexpr int LDU = 8;
+  for (int e0 = tid; e0 < kp * TC; e0 += NT * LDU) {
+    T v[LDU];
+#pragma unroll
+    for (int u = 0; u < LDU; ++u) {
+      const int e = e0 + u * NT, i = e / TC, c = e % TC;
+      v[u] = (i < k && c0 + c < n) ? C[(int64_t)i * ldc + c0 + c] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < LDU; ++u)
+      if (e0 + u * NT < kp * TC) Xs[e0 + u * NT] = v[u];
+  }
+  const int r0 = (gt / (TC / 4)) * 4, cc = (gt % (TC / 4)) * 4;  // update tile (4 x 4)
+  const int q0 = (tid / (TC / 4)) * 2, qc = (tid % (TC / 4)) * 4;  // diagonal tile (2 x 4)
+  const int th = g * (TB / 2);                                    // this group's rows t
+  int sidx = 0;
+  // wait for block sidx, prefetch block sidx + TSTAGES - 1; returns the staged block
+  auto next_block = [&]() -> const T* {
+    cp_async_wait<TSTAGES - 2>();
+    __syncthreads();
+    issue(sidx + TSTAGES - 1);
+    return Ls + (size_t)(sidx++ % TSTAGES) * TB * LSP;
+  };
+  T acc[4][4];
+  auto start_row_block = [&](int I) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        acc[a][b] = (g == 0) ? Xs[(size_t)(I * TB + r0 + a) * TC + cc + b] : T(0);
+  };
+  auto update = [&](int j0) {  // acc -= staged [t][r] (this group's half of t) x X[j0 + t]
+    const T* Lb = next_block();
+#pragma unroll 4
+    for (int t = th; t < th + TB / 2; ++t) {
+      const Vec4<T> l = lds4(Lb + t * LSP + r0);
+      const Vec4<T> x = lds4(Xs + (size_t)(j0 + t) * TC + cc);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(-l.v[a], x.v[b], acc[a][b]);
+    }
+  };
+  auto diag = [&](int I) {  // X_I = W-block (staged [t][r]) applied to the summed partials
+    T* Wg = Ws + (size_t)g * TB * TC;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Wg[(r0 + a) * TC + cc + b] = acc[a][b];
+    const T* Db = next_block();  // its __syncthreads also publishes the partials
+    T v[2][4] = {};
+#pragma unroll 4
+    for (int t = 0; t < TB; ++t) {
+      const T w0 = Db[t * LSP + q0], w1 = Db[t * LSP + q0 + 1];
+      const Vec4<T> x0 = lds4(Ws + t * TC + qc);
+      const Vec4<T> x1 = lds4(Ws + (size_t)TB * TC + t * TC + qc);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const T x = x0.v[b] + x1.v[b];
+        v[0][b] = fma(w0, x, v[0][b]);
+        v[1][b] = fma(w1, x, v[1][b]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Xs[(size_t)(I * TB + q0 + a) * TC + qc + b] = v[a][b];
+  };
+  __syncthreads();
+  for (int I = 0; I < nb; ++I) {
+    start_row_block(I);
+    for (int J = 0; J < I; ++J) update(J * TB);
+    diag(I);
+  }
+  __syncthreads();
+  for (int e = tid; e < k * TC; e += NT) Xs[e] = (T)((double)Xs[e] * o.dinv[e / TC]);
+  __syncthreads();
+  for (int I = nb - 1; I >= 0; --I) {
+    start_row_block(I);
+    for (int J = nb - 1; J > I; --J) update(J * TB);
+    diag(I);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int e = tid; e < k * TC; e += NT) {
+    const int i = e / TC, c = e % TC;
+    if (c0 + c < n) B[(int64_t)i * ldb + c0 + c] = Xs[e];
+  }
+}
+
+template <typename T>
+static size_t trsm_smem_bytes(int kp, int tc) {
+  return sizeof(T) * ((size_t)kp * tc + (size_t)TSTAGES * TB * LSP + 2 * (size_t)TB * tc);
+}
+
+template <typename T, int TC>
+static int32_t trsm_launch(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t n, T* B,
+                           int64_t ldb, size_t bytes, cudaStream_t s) {
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_trsm_ldl<T, TC>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  k_trsm_ldl<T, TC><<<(unsigned)ceil_div(n, TC), TB / 2 * TC / 4, bytes, s>>>(o, C, ldc, n, B,
+                                                                              ldb);
+  return last_launch_status();
+}
+
+template <typename T>
+int32_t trsm_ldl(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t n, T* B, int64_t ldb,
+                 cudaStream_t s) {
+  int dev = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  int optin = 0;
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (trsm_smem_bytes<T>(o.kp, 64) <= (size_t)optin)
+    return trsm_launch<T, 64>(o, C, ldc, n, B, ldb, trsm_smem_bytes<T>(o.kp, 64), s);
+  if (trsm_smem_bytes<T>(o.kp, 32) <= (size_t)optin)
+    return trsm_launch<T, 32>(o, C, ldc, n, B, ldb, trsm_smem_bytes<T>(o.kp, 32), s);
+  return RLU_EUNSUPPORTED;
+}
+template int32_t trsm_ldl<float>(const LdlOut<float>&, const float*, int64_t, int64_t, float*,
+                                 int64_t, cudaStream_t);
+template int32_t trsm_ldl<double>(const LdlOut<double>&, const double*, int64_t, int64_t, double*,
+                                  int64_t, cudaStream_t);
 
 // L_b (k x k, column-major, ld k): L_b[i][j] = X^T-stored B[i][Q[j]] for i > j, 1 on the
 // diagonal, 0 above. B is row-major k x n (ld ldb).

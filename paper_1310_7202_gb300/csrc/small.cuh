@@ -9,8 +9,29 @@ template <typename T>
 int32_t build_ly(const T* Y, int64_t ldy, int64_t m, int k, const int32_t* perm, T* Lt, T* Lp,
                  int64_t ldl, cudaStream_t s, T* Lhi = nullptr, T* Llo = nullptr);
 
+// Outputs of the LDL^T factorization M = L D L^T that the triangular solves read, in the
+// path's type and zero-padded to kp = 32 * ceil(k / 32) (identity on the padded diagonal):
+// L column-major (LT[c * kp + i] = L[i][c]) and row-major (LR[i * kp + c]); the inverses
+// W_b of L's 32 x 32 diagonal blocks, row-major (W) and transposed (WT); 1/D (k doubles).
 template <typename T>
-int32_t chol_inv(double* M, int k, double* Rinv, T* RinvT, int32_t* status, cudaStream_t s);
+struct LdlOut {
+  T* LT;
+  T* LR;
+  T* W;
+  T* WT;
+  double* dinv;
+  int k;
+  int kp;
+};
+
+// M (k x k FP64, row-major; overwritten) = L D L^T.
+template <typename T>
+int32_t ldl_factor(double* M, int k, const LdlOut<T>& o, int32_t* status, cudaStream_t s);
+
+// B (k x n, row-major) = L^{-T} D^{-1} L^{-1} C (C k x n row-major).
+template <typename T>
+int32_t trsm_ldl(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t n, T* B, int64_t ldb,
+                 cudaStream_t s);
 
 template <typename T>
 int32_t gather_lb_u(const T* B, int64_t ldb, const int32_t* Q, int k, int64_t n, T* Lb, T* U,
