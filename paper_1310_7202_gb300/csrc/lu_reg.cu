@@ -29,8 +29,6 @@ namespace cg = cooperative_groups;
 
 namespace rlu {
 
-static constexpr int LR_NT = 512;
-static constexpr int LR_NW = LR_NT / 32;
 static constexpr int LR_CH = 32;  // trailing-update column chunk
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -48,12 +46,14 @@ __device__ __forceinline__ void mbar_arm(uint32_t bar, uint32_t tx) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
                ::"r"(bar), "r"(tx) : "memory");
 }
+// Test for completion of the phase of the given parity; the warp may sleep in the
+// instruction up to the hinted time (ns) instead of spinning on issue slots.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile("{\n .reg .pred p;\n"
-               " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+               " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
                " selp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+               : "=r"(ok) : "r"(bar), "r"(parity), "r"(20000u) : "memory");
   return ok != 0;
 }
 __device__ __forceinline__ void st_async16(uint32_t raddr, uint4 v, uint32_t rbar) {
@@ -69,34 +69,52 @@ __device__ __forceinline__ uint64_t gtimer() {
 // Order-preserving 64-bit key of |v| (0 for NaN, so that a NaN never beats a number).
 __device__ __forceinline__ uint64_t mag_key(float v) {
   const float a = fabsf(v);
-  return (a == a) ? (uint64_t)__float_as_uint(a) : 0ull;
+  return (a == a) ? ((uint64_t)__float_as_uint(a) << 32) : 0ull;
 }
 __device__ __forceinline__ uint64_t mag_key(double v) {
   const double a = fabs(v);
   return (a == a) ? (uint64_t)__double_as_longlong(a) : 0ull;
 }
 
-// Reciprocal of a pivot: correctly rounded in FP32; FP32 seed and two Newton steps in FP64
-// (IEEE divide outside the FP32 exponent range). Multipliers are x * (1/pivot).
-__device__ __forceinline__ float rcp_piv(float p) { return __frcp_rn(p); }
+// Reciprocal of a pivot: the hardware approximation refined by Newton-Raphson steps
+// (y' = y + y (1 - p y)): one step in FP32 (within an ulp or so), two from the FP32 seed in
+// FP64 (IEEE divide outside the FP32 exponent range). Multipliers are x * (1/pivot).
+__device__ __forceinline__ float rcp_approx(float p) {
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(p));
+  return y;
+}
+__device__ __forceinline__ float rcp_piv(float p) {
+  const float y = rcp_approx(p);
+  if (!isfinite(y)) return y;
+  return fmaf(y, fmaf(-p, y, 1.0f), y);
+}
 __device__ __forceinline__ double rcp_piv(double p) {
   const double a = fabs(p);
   if (!(a > 1e-30 && a < 1e30)) return 1.0 / p;
-  double y = (double)__frcp_rn((float)p);
+  double y = (double)rcp_approx((float)p);
   double e = fma(-p, y, 1.0);
   y = fma(y, e, y);
   e = fma(-p, y, 1.0);
   return fma(y, e, y);
 }
 
-// Warp-wide winner: largest key, then smallest position; returns the winning lane.
+// Warp-wide winner: largest key, then smallest position; returns the winning lane. The
+// common case (one lane holds the largest high word) costs one reduction and one ballot.
 __device__ __forceinline__ int warp_winner(uint64_t key, int pos) {
   const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
   const uint32_t mhi = __reduce_max_sync(0xffffffffu, hi);
-  const uint32_t mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
-  const bool top = (hi == mhi) && (lo == mlo);
-  const int mpos = (int)__reduce_min_sync(0xffffffffu, top ? (uint32_t)pos : 0x7fffffffu);
-  const uint32_t who = __ballot_sync(0xffffffffu, top && pos == mpos);
+  bool top = hi == mhi;
+  uint32_t who = __ballot_sync(0xffffffffu, top);
+  if (__popc(who) > 1) {
+    const uint32_t mlo = __reduce_max_sync(0xffffffffu, top ? lo : 0u);
+    top = top && lo == mlo;
+    who = __ballot_sync(0xffffffffu, top);
+    if (__popc(who) > 1) {
+      const int mpos = (int)__reduce_min_sync(0xffffffffu, top ? (uint32_t)pos : 0x7fffffffu);
+      who = __ballot_sync(0xffffffffu, top && pos == mpos);
+    }
+  }
   return __ffs(who) - 1;
 }
 
@@ -133,53 +151,54 @@ struct LrRec {  // one candidate record, 16-byte chunks
 template <typename T, int NB>
 __host__ __device__ constexpr int rec_bytes() { return (int)((sizeof(LrRec<T, NB>) + 15) / 16 * 16); }
 
-template <typename T, int NB>
+template <typename T, int NB, int NW>
 struct LrShared {
   uint64_t mbar[2];
   int32_t err;
   int32_t nonfinite;
-  uint32_t wkhi[LR_NW], wklo[LR_NW];
-  int32_t wpos[LR_NW], wrow[LR_NW];
+  uint32_t wkhi[2][NW], wklo[2][NW];  // per-warp candidates, by step parity
+  int32_t wpos[2][NW], wrow[2][NW];
   alignas(16) unsigned char stage[rec_bytes<T, NB>()];
   alignas(16) unsigned char recv[2][16][rec_bytes<T, NB>()];
-  T pval[2];                               // pivot value of the step of that parity
-  alignas(16) T prow[2][Pad4<NB>::value + 4];  // P1[c] = pivot row at offset c + 1
+  // per-warp copies of the pivot row, by step parity: P1[c] = pivot row at offset c + 1
+  alignas(16) T prow[NW][2][Pad4<NB>::value + 4];
 };
 
-template <typename T, bool CROUT, int RT, int NB>
-__global__ void __launch_bounds__(LR_NT, 1) k_lu_reg(LuArgs a) {
+template <typename T, bool CROUT, int RT, int NB, int NT>
+__global__ void __launch_bounds__(NT, 1) k_lu_reg(LuArgs a) {
+  constexpr int NW = NT / 32;
   cg::cluster_group cl = cg::this_cluster();
   const int ncta = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int rpc = a.rpc;  // = LR_NT * RT (rows per CTA)
+  const int rpc = a.rpc;  // = NT * RT (rows per CTA)
   const int r0 = crank * rpc;
   const int C = a.C, R = a.R;
   const int64_t ldx = a.ldx;
   T* __restrict__ X = static_cast<T*>(a.X);
   constexpr int RB = rec_bytes<T, NB>();
   constexpr int NCHUNK = RB / 16;
+  constexpr int PW = Pad4<NB>::value + 4;
   static_assert(NCHUNK <= 32, "record must fit one warp's 16-byte chunks");
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  LrShared<T, NB>& sh = *reinterpret_cast<LrShared<T, NB>*>(smem_raw);
-  size_t off = (sizeof(LrShared<T, NB>) + 15) / 16 * 16;
+  LrShared<T, NB, NW>& sh = *reinterpret_cast<LrShared<T, NB, NW>*>(smem_raw);
+  size_t off = (sizeof(LrShared<T, NB, NW>) + 15) / 16 * 16;
   T* L11 = reinterpret_cast<T*>(smem_raw + off);          // [NB][NB]
   off += (sizeof(T) * (size_t)NB * NB + 15) / 16 * 16;
-  int* psmall = reinterpret_cast<int*>(smem_raw + off);   // [C]
+  int* prows = reinterpret_cast<int*>(smem_raw + off);    // [NB] this panel's pivot rows
 
-  // rows of this thread: r0 + tid + s*LR_NT
+  // rows of this thread: r0 + tid + s*NT
   int rowi[RT];
   int pos[RT];
   bool have[RT];
   const bool first = (a.p0 == 0);
 #pragma unroll
   for (int s = 0; s < RT; ++s) {
-    rowi[s] = r0 + tid + s * LR_NT;
-    have[s] = (tid + s * LR_NT < rpc) && rowi[s] < R;
+    rowi[s] = r0 + tid + s * NT;
+    have[s] = (tid + s * NT < rpc) && rowi[s] < R;
     pos[s] = (first || !have[s]) ? rowi[s] : a.posg[rowi[s]];
   }
-  for (int p = tid; p < C; p += LR_NT) psmall[p] = first ? p : a.psg[p];
   if (tid == 0) {
     mbar_init(smem_u32(&sh.mbar[0]), 1);
     mbar_init(smem_u32(&sh.mbar[1]), 1);
@@ -187,10 +206,9 @@ __global__ void __launch_bounds__(LR_NT, 1) k_lu_reg(LuArgs a) {
     sh.err = 0;
     sh.nonfinite = 0;
   }
-  for (int i = tid; i < 2 * (Pad4<NB>::value + 4); i += LR_NT) (&sh.prow[0][0])[i] = T(0);
+  for (int i = tid; i < NW * 2 * PW; i += NT) (&sh.prow[0][0][0])[i] = T(0);
   cl.sync();
 
-  const uint32_t stage_a = smem_u32(sh.stage);
   const uint32_t recv_a = smem_u32(&sh.recv[0][0][0]);
   const uint32_t mbar_a = smem_u32(&sh.mbar[0]);
   int first_zero = -1;
@@ -198,266 +216,251 @@ __global__ void __launch_bounds__(LR_NT, 1) k_lu_reg(LuArgs a) {
 
   T x[RT][NB];
   T xe[RT], mp[RT];
+  const int p0 = a.p0;
+  const int w = a.pw;
+  // load: x[s][c] = X[p0 - 1 + c] for c = 1..w (x[s][0] unused), pending multiplier 0
+#pragma unroll
+  for (int s = 0; s < RT; ++s) {
+    x[s][0] = T(0);
+#pragma unroll
+    for (int c = 1; c < NB; ++c)
+      x[s][c] = (have[s] && c <= w) ? X[(int64_t)(p0 - 1 + c) * ldx + rowi[s]] : T(0);
+    xe[s] = x[s][1];
+    mp[s] = T(0);
+  }
 
-  {
-    const int p0 = a.p0;
-    const int w = a.pw;
-    // load: x[s][c] = X[p0 - 1 + c] for c = 1..w (x[s][0] unused), pending multiplier 0
+  for (int jj = 0; jj < w; ++jj) {
+    const int j = p0 + jj;
+    // receive slots and mbarriers alternate by the step's parity within this launch; the
+    // mbarriers start at phase 0 in every launch, so step jj waits on phase (jj / 2) & 1
+    const int par = jj & 1;
+    const int live = w - jj;  // columns j .. p0 + w - 1
+    if (tid == 0) mbar_arm(mbar_a + 8 * par, (uint32_t)(ncta * RB));
+    // ---- candidates: thread, warp ----------------------------------------------------------
+    uint64_t key = 0;
+    int kpos = 0x7fffffff, krow = -1;
 #pragma unroll
     for (int s = 0; s < RT; ++s) {
-      x[s][0] = T(0);
-#pragma unroll
-      for (int c = 1; c < NB; ++c)
-        x[s][c] = (have[s] && c <= w) ? X[(int64_t)(p0 - 1 + c) * ldx + rowi[s]] : T(0);
-      xe[s] = x[s][1];
-      mp[s] = T(0);
+      if (have[s] && pos[s] >= j) {
+        if (!is_finite_val(xe[s])) sh.nonfinite = 1;
+        const uint64_t kk = mag_key(xe[s]);
+        if (krow < 0 || kk > key || (kk == key && pos[s] < kpos)) {
+          key = kk;
+          kpos = pos[s];
+          krow = rowi[s];
+        }
+      }
     }
-    for (int i = tid; i < Pad4<NB>::value + 4; i += LR_NT) {
-      sh.prow[0][i] = T(0);
-      sh.prow[1][i] = T(0);
+    {
+      // empty candidates lose to every real one: key 0 and the largest position
+      const int wl = warp_winner(key, kpos);
+      if (lane == wl) {
+        sh.wkhi[par][warp] = (uint32_t)(key >> 32);
+        sh.wklo[par][warp] = (uint32_t)key;
+        sh.wpos[par][warp] = kpos;
+        sh.wrow[par][warp] = krow;
+      }
     }
     __syncthreads();
-
-    for (int jj = 0; jj < w; ++jj) {
-      const int j = p0 + jj;
-      const int par = j & 1;
-      const int a_row = psmall[j];
-      if (tid == 0) mbar_arm(mbar_a + 8 * par, (uint32_t)(ncta * RB));
-      // ---- candidates: thread, warp, CTA ------------------------------------------------
-      uint64_t key = 0;
-      int kpos = 0x7fffffff, ks = 0;
-      bool anyc = false;
-#pragma unroll
-      for (int s = 0; s < RT; ++s) {
-        if (have[s] && pos[s] >= j) {
-          if (!is_finite_val(xe[s])) sh.nonfinite = 1;
-          const uint64_t kk = mag_key(xe[s]);
-          if (!anyc || kk > key || (kk == key && pos[s] < kpos)) {
-            key = kk;
-            kpos = pos[s];
-            ks = s;
-          }
-          anyc = true;
-        }
-      }
-      int krow = anyc ? rowi[ks] : -1;
-      if (!anyc) key = 0;
-      {
-        // empty candidates lose to every real one: give them the largest position
-        const int wl = warp_winner(anyc ? key : 0ull, anyc ? kpos : 0x7fffffff);
-        const uint64_t wk = __shfl_sync(0xffffffffu, key, wl);
-        const int wp = __shfl_sync(0xffffffffu, anyc ? kpos : 0x7fffffff, wl);
-        const int wr = __shfl_sync(0xffffffffu, krow, wl);
-        if (lane == 0) {
-          sh.wkhi[warp] = (uint32_t)(wk >> 32);
-          sh.wklo[warp] = (uint32_t)wk;
-          sh.wpos[warp] = wp;
-          sh.wrow[warp] = wr;
-        }
-      }
-      __syncthreads();
-      int cta_row, cta_pos;
-      uint64_t cta_key;
-      {
-        const uint64_t k2 = lane < LR_NW ? (((uint64_t)sh.wkhi[lane] << 32) | sh.wklo[lane]) : 0ull;
-        const int p2 = lane < LR_NW ? sh.wpos[lane] : 0x7fffffff;
-        const int wl = warp_winner(k2, p2);
-        cta_key = __shfl_sync(0xffffffffu, k2, wl);
-        cta_pos = __shfl_sync(0xffffffffu, p2, wl);
-        cta_row = sh.wrow[wl < LR_NW ? wl : 0];
-      }
-      // the thread that owns the CTA's candidate stages its record
-#pragma unroll
-      for (int s = 0; s < RT; ++s) {
-        if (have[s] && rowi[s] == cta_row) {
-          LrRec<T, NB>* rec = reinterpret_cast<LrRec<T, NB>*>(sh.stage);
-          rec->khi = (uint32_t)(cta_key >> 32);
-          rec->klo = (uint32_t)cta_key;
-          rec->pos = cta_pos;
-          rec->row = cta_row;
-          rec->xe = xe[s];
-          rec->mp = mp[s];
-#pragma unroll
-          for (int c = 0; c + 3 < NB; c += 4)
-            st4(&rec->x[c], x[s][c], x[s][c + 1], x[s][c + 2], x[s][c + 3]);
-#pragma unroll
-          for (int c = NB / 4 * 4; c < NB; ++c) rec->x[c] = x[s][c];
-        }
-      }
-      if (cta_row < 0 && tid == 0) {  // no live row in this CTA
+    // ---- CTA winner, in every warp; its warp stages the record and pushes it -------------
+    {
+      const uint64_t k2 = lane < NW ? (((uint64_t)sh.wkhi[par][lane] << 32) | sh.wklo[par][lane]) : 0ull;
+      const int p2 = lane < NW ? sh.wpos[par][lane] : 0x7fffffff;
+      const int ow = warp_winner(k2, p2);  // owner warp
+      if (warp == ow) {
+        const int cta_row = sh.wrow[par][ow];
         LrRec<T, NB>* rec = reinterpret_cast<LrRec<T, NB>*>(sh.stage);
-        rec->khi = 0;
-        rec->klo = 0;
-        rec->pos = 0x7fffffff;
-        rec->row = -1;
-        rec->xe = T(0);
-        rec->mp = T(0);
-      }
-      __syncthreads();
-      // ---- push the record to every CTA (warp w -> CTA w) ------------------------------
-      if (warp < ncta && lane < NCHUNK) {
-        const uint4 v = *reinterpret_cast<const uint4*>(sh.stage + 16 * lane);
-        const uint32_t dst = map_rank(recv_a + (uint32_t)((par * 16 + crank) * RB + 16 * lane), warp);
-        const uint32_t bar = map_rank(mbar_a + 8 * par, warp);
-        st_async16(dst, v, bar);
-      }
-      // ---- meanwhile: the deferred part of the previous step's update ------------------
-      if (jj > 0) {
-        const T* P1 = sh.prow[par ^ 1];  // P1[c] = previous pivot row at offset c + 1
-#pragma unroll
-        for (int c0 = 0; c0 < NB - 1; c0 += 4) {
-          T pv[4];
-          ld4(P1 + c0, pv);
+        if (cta_row < 0) {
+          if (lane == 0) {  // no live row in this CTA
+            rec->khi = 0;
+            rec->klo = 0;
+            rec->pos = 0x7fffffff;
+            rec->row = -1;
+            rec->xe = T(0);
+            rec->mp = T(0);
+          }
+        } else {
 #pragma unroll
           for (int s = 0; s < RT; ++s) {
+            if (have[s] && rowi[s] == cta_row) {
+              rec->khi = sh.wkhi[par][ow];
+              rec->klo = sh.wklo[par][ow];
+              rec->pos = sh.wpos[par][ow];
+              rec->row = cta_row;
+              rec->xe = xe[s];
+              rec->mp = mp[s];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (c0 + u < NB - 1) x[s][c0 + u] = fma(-mp[s], pv[u], x[s][c0 + u + 1]);
-          }
-        }
+              for (int c = 0; c + 3 < NB; c += 4)
+                if (c < live + 2) st4(&rec->x[c], x[s][c], x[s][c + 1], x[s][c + 2], x[s][c + 3]);
 #pragma unroll
-        for (int s = 0; s < RT; ++s) x[s][NB - 1] = T(0);
-      } else {
-#pragma unroll
-        for (int s = 0; s < RT; ++s) {
-#pragma unroll
-          for (int c = 0; c < NB - 1; ++c) x[s][c] = x[s][c + 1];
-          x[s][NB - 1] = T(0);
-        }
-      }
-      // ---- wait for the cluster's records -----------------------------------------------
-      if (!timed_out) {
-        const uint32_t bar = mbar_a + 8 * par;
-        const uint32_t ph = (uint32_t)((j >> 1) & 1);
-        if (!mbar_try(bar, ph)) {
-          const uint64_t t0 = gtimer();
-          while (!mbar_try(bar, ph)) {
-            if (gtimer() - t0 > 1000000000ull) {
-              timed_out = true;
-              sh.err = 1;
-              break;
+              for (int c = NB / 4 * 4; c < NB; ++c) rec->x[c] = x[s][c];
             }
           }
         }
-      }
-      // ---- winner among the cluster's records --------------------------------------------
-      int win;
-      {
-        const LrRec<T, NB>* rr = reinterpret_cast<const LrRec<T, NB>*>(&sh.recv[par][lane < ncta ? lane : 0][0]);
-        const uint64_t k3 = lane < ncta ? (((uint64_t)rr->khi << 32) | rr->klo) : 0ull;
-        const int p3 = lane < ncta ? rr->pos : 0x7fffffff;
-        win = warp_winner(k3, p3);
-      }
-      const LrRec<T, NB>* W = reinterpret_cast<const LrRec<T, NB>*>(&sh.recv[par][win][0]);
-      const int wrow = W->row, wpos = W->pos;
-      const bool valid = wrow >= 0;
-      const T piv = W->xe;
-      const bool nz = valid && piv != T(0) && mag_key(piv) != 0ull;
-      const T rp = nz ? rcp_piv(piv) : T(0);
-      // pivot row: value P_j[0] = piv and P1_j[c] = P_j[c + 1] (column j + 1 + c), from
-      // the winner's registers and its pending update
-      {
-        const T* Pp = sh.prow[par ^ 1];
-        T* Pn1 = sh.prow[par];
-        const T wm = W->mp;
-        for (int c = tid; c < Pad4<NB>::value + 4; c += LR_NT) {
-          T v = T(0);
-          if (c + 1 < w - jj) {  // column j + 1 + c lies in the panel
-            v = (wm != T(0)) ? fma(-wm, Pp[c + 1], W->x[c + 2]) : W->x[c + 2];
-            if (CROUT && nz) v = v * rp;
-          }
-          Pn1[c] = v;
+        __syncwarp();
+        if (lane < NCHUNK) {
+          const uint4 v = *reinterpret_cast<const uint4*>(sh.stage + 16 * lane);
+          const uint32_t dst = recv_a + (uint32_t)((par * 16 + crank) * RB + 16 * lane);
+          const uint32_t bar = mbar_a + 8 * par;
+          for (int r = 0; r < ncta; ++r) st_async16(map_rank(dst, r), v, map_rank(bar, r));
         }
-        if (tid == 0) sh.pval[par] = piv;
-      }
-      if (tid == 0) {
-        if (valid && wrow != a_row) {
-          psmall[j] = wrow;
-          if (wpos < C) psmall[wpos] = a_row;
-        }
-        if (!nz && first_zero < 0) first_zero = j;
-      }
-      __syncthreads();
-      // positions of my rows after the swap of positions j and wpos
-      if (valid && wrow != a_row) {
-#pragma unroll
-        for (int s = 0; s < RT; ++s) {
-          if (rowi[s] == a_row) pos[s] = wpos;
-          if (rowi[s] == wrow) pos[s] = j;
-        }
-      }
-      const T* Pn1 = sh.prow[par];
-      // the pivot row's final entries: columns j .. p0 + w - 1
-      if (valid && wrow >= r0 && wrow < r0 + rpc) {
-        for (int c = tid; c < w - jj; c += LR_NT)
-          X[(int64_t)(j + c) * ldx + wrow] = (c == 0) ? piv : Pn1[c - 1];
-      }
-      // multipliers of my live rows, and the eager update of the next column
-#pragma unroll
-      for (int s = 0; s < RT; ++s) {
-        T m = T(0);
-        if (have[s] && pos[s] > j && nz) {
-          m = CROUT ? xe[s] : xe[s] * rp;
-          X[(int64_t)j * ldx + rowi[s]] = m;
-        } else if (have[s] && pos[s] > j) {
-          // zero pivot: nothing is eliminated; the column keeps its (zero) values
-          X[(int64_t)j * ldx + rowi[s]] = xe[s];
-        }
-        mp[s] = m;
-        xe[s] = (m != T(0)) ? fma(-m, Pn1[0], x[s][1]) : x[s][1];
       }
     }
-
-    // all records of this panel consumed before anyone reuses receive slots / exits
-    cl.sync();
-    if (p0 + w < C) {
-      // ---- U12 of the pivot rows for the trailing columns (forward substitution) -------
-      for (int e = tid; e < w * w; e += LR_NT) {
-        const int t = e / w, s = e % w;
-        L11[t * NB + s] = X[(int64_t)(p0 + s) * ldx + psmall[p0 + t]];
-      }
-      __syncthreads();
-      for (int c = p0 + w + crank * LR_NW + warp; c < C; c += ncta * LR_NW) {
-        constexpr int NQ = (NB + 31) / 32;
-        T u[NQ], fin[NQ];
+    // ---- meanwhile: the deferred part of the previous step's update (live columns only) ---
+    if (jj > 0) {
+      const T* P1 = sh.prow[warp][par ^ 1];  // P1[c] = previous pivot row at offset c + 1
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const int t = lane + 32 * q;
-          u[q] = t < w ? X[(int64_t)c * ldx + psmall[p0 + t]] : T(0);
-          fin[q] = u[q];
-        }
+      for (int b0 = 0; b0 < NB - 1; b0 += 16) {
+        if (b0 < live) {  // uniform: skip whole blocks past the panel's live columns
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          for (int s = 32 * q; s < min(w, 32 * q + 32); ++s) {
-            T us = __shfl_sync(0xffffffffu, u[q], s - 32 * q);
-            if (CROUT) {
-              const T pv = L11[s * NB + s];
-              if (pv != T(0)) us = us * rcp_piv(pv);
-            }
-            if (lane == s - 32 * q) fin[q] = us;
+          for (int c0 = b0; c0 < b0 + 16 && c0 < NB - 1; c0 += 4) {
+            T pv[4];
+            ld4(P1 + c0, pv);
 #pragma unroll
-            for (int qq = q; qq < NQ; ++qq) {
-              const int t = lane + 32 * qq;
-              if (t > s && t < w) u[qq] = fma(-L11[t * NB + s], us, u[qq]);
+            for (int s = 0; s < RT; ++s) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (c0 + u < NB - 1) x[s][c0 + u] = fma(-mp[s], pv[u], x[s][c0 + u + 1]);
             }
           }
         }
+      }
+    } else {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const int t = lane + 32 * q;
-          if (t < w) X[(int64_t)c * ldx + psmall[p0 + t]] = fin[q];
+      for (int s = 0; s < RT; ++s) {
+#pragma unroll
+        for (int c = 0; c < NB - 1; ++c) x[s][c] = x[s][c + 1];
+        x[s][NB - 1] = T(0);
+      }
+    }
+    // ---- wait for the cluster's records -----------------------------------------------------
+    if (!timed_out) {
+      const uint32_t bar = mbar_a + 8 * par;
+      const uint32_t ph = (uint32_t)((jj >> 1) & 1);
+      if (!mbar_try(bar, ph)) {
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(bar, ph)) {
+          if (gtimer() - t0 > 1000000000ull) {
+            timed_out = true;
+            sh.err = 1;
+            break;
+          }
         }
+      }
+    }
+    // ---- winner among the cluster's records, in every warp ----------------------------------
+    int win;
+    {
+      const LrRec<T, NB>* rr = reinterpret_cast<const LrRec<T, NB>*>(&sh.recv[par][lane < ncta ? lane : 0][0]);
+      const uint64_t k3 = lane < ncta ? (((uint64_t)rr->khi << 32) | rr->klo) : 0ull;
+      const int p3 = lane < ncta ? rr->pos : 0x7fffffff;
+      win = warp_winner(k3, p3);
+    }
+    const LrRec<T, NB>* W = reinterpret_cast<const LrRec<T, NB>*>(&sh.recv[par][win][0]);
+    const int wrow = W->row, wpos = W->pos;
+    const bool valid = wrow >= 0;
+    const T piv = W->xe;
+    const bool nz = valid && piv != T(0) && mag_key(piv) != 0ull;
+    const T rp = nz ? rcp_piv(piv) : T(0);
+    // this warp's copy of the pivot row: P1_j[c] = column j + 1 + c, from the winner's
+    // registers and its pending update
+    T* Pn1 = sh.prow[warp][par];
+    {
+      const T* Pp = sh.prow[warp][par ^ 1];
+      const T wm = W->mp;
+      // live entries only (c + 1 < live); the entries past them are stale and reach only
+      // registers of columns that have left the panel
+      for (int c = lane; c + 1 < live; c += 32) {
+        T v = (wm != T(0)) ? fma(-wm, Pp[c + 1], W->x[c + 2]) : W->x[c + 2];
+        if (CROUT && nz) v = v * rp;
+        Pn1[c] = v;
+      }
+    }
+    __syncwarp();
+    if (tid == 0) {
+      prows[jj] = valid ? wrow : -1;
+      if (!nz && first_zero < 0) first_zero = j;
+    }
+    // positions of my rows after the exchange of positions j and wpos
+    if (valid) {
+#pragma unroll
+      for (int s = 0; s < RT; ++s) {
+        if (rowi[s] == wrow) pos[s] = j;
+        else if (pos[s] == j) pos[s] = wpos;
+      }
+    }
+    // the pivot row's final entries: columns j .. p0 + w - 1
+    if (valid && wrow >= r0 && wrow < r0 + rpc) {
+      for (int c = tid; c < live; c += NT)
+        X[(int64_t)(j + c) * ldx + wrow] = (c == 0) ? piv : Pn1[c - 1];
+    }
+    // multipliers of my live rows, and the eager update of the next column
+#pragma unroll
+    for (int s = 0; s < RT; ++s) {
+      T m = T(0);
+      if (have[s] && pos[s] > j && nz) {
+        m = CROUT ? xe[s] : xe[s] * rp;
+        X[(int64_t)j * ldx + rowi[s]] = m;
+      } else if (have[s] && pos[s] > j) {
+        // zero pivot: nothing is eliminated; the column keeps its (zero) values
+        X[(int64_t)j * ldx + rowi[s]] = xe[s];
+      }
+      mp[s] = m;
+      xe[s] = (m != T(0)) ? fma(-m, Pn1[0], x[s][1]) : x[s][1];
+    }
+  }
+
+  // all records of this panel consumed before anyone reuses receive slots / exits; the
+  // panel's columns are final in global memory for the whole cluster
+  cl.sync();
+  if (p0 + w < C) {
+    // ---- U12 of the pivot rows for the trailing columns (forward substitution) -----------
+    for (int e = tid; e < w * w; e += NT) {
+      const int t = e / w, s = e % w;
+      const int pr = prows[t];
+      L11[t * NB + s] = pr >= 0 ? X[(int64_t)(p0 + s) * ldx + pr] : T(0);
+    }
+    __syncthreads();
+    for (int c = p0 + w + crank * NW + warp; c < C; c += ncta * NW) {
+      constexpr int NQ = (NB + 31) / 32;
+      T u[NQ], fin[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int t = lane + 32 * q;
+        u[q] = (t < w && prows[t] >= 0) ? X[(int64_t)c * ldx + prows[t]] : T(0);
+        fin[q] = u[q];
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        for (int s = 32 * q; s < min(w, 32 * q + 32); ++s) {
+          T us = __shfl_sync(0xffffffffu, u[q], s - 32 * q);
+          if (CROUT) {
+            const T pv = L11[s * NB + s];
+            if (pv != T(0)) us = us * rcp_piv(pv);
+          }
+          if (lane == s - 32 * q) fin[q] = us;
+#pragma unroll
+          for (int qq = q; qq < NQ; ++qq) {
+            const int t = lane + 32 * qq;
+            if (t > s && t < w) u[qq] = fma(-L11[t * NB + s], us, u[qq]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int t = lane + 32 * q;
+        if (t < w && prows[t] >= 0) X[(int64_t)c * ldx + prows[t]] = fin[q];
       }
     }
   }
 
   // persist the positions for the next panel; the last panel writes P (gather form)
-  const bool last = (a.p0 + a.pw >= C);
+  const bool last = (p0 + w >= C);
 #pragma unroll
   for (int s = 0; s < RT; ++s)
     if (have[s]) a.posg[rowi[s]] = pos[s];
   if (crank == 0)
-    for (int p = tid; p < C; p += LR_NT) a.psg[p] = psmall[p];
+    for (int t = tid; t < w; t += NT) a.psg[p0 + t] = prows[t];
   if (last) {
 #pragma unroll
     for (int s = 0; s < RT; ++s)
@@ -478,12 +481,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_lu_trail(T* __restrict__ X, int64_t ldx, int R, int C,
                                                  int p0, int w, const int32_t* __restrict__ posg,
                                                  const int32_t* __restrict__ psg) {
-  __shared__ __align__(16) T U12[128][LR_CH];
+  __shared__ __align__(16) T U12[128 + 16][LR_CH];
   const int c0 = p0 + w + blockIdx.y * LR_CH;
   const int cw = min(LR_CH, C - c0);
-  for (int e = threadIdx.x; e < w * LR_CH; e += 256) {
+  const int wpad = (w + 15) / 16 * 16;
+  for (int e = threadIdx.x; e < wpad * LR_CH; e += 256) {
     const int s = e / LR_CH, q = e % LR_CH;
-    U12[s][q] = q < cw ? X[(int64_t)(c0 + q) * ldx + psg[p0 + s]] : T(0);
+    U12[s][q] = (q < cw && s < w) ? X[(int64_t)(c0 + q) * ldx + psg[p0 + s]] : T(0);
   }
   __syncthreads();
   const int r = blockIdx.x * 256 + threadIdx.x;
@@ -491,14 +495,21 @@ __global__ void __launch_bounds__(256) k_lu_trail(T* __restrict__ X, int64_t ldx
   T acc[LR_CH];
 #pragma unroll
   for (int q = 0; q < LR_CH; ++q) acc[q] = q < cw ? X[(int64_t)(c0 + q) * ldx + r] : T(0);
-  for (int s = 0; s < w; ++s) {
-    const T lv = X[(int64_t)(p0 + s) * ldx + r];
+  // the row's multipliers in batches of 16 independent loads, so that their latencies overlap
+  constexpr int LB16 = 16;
+  for (int s0 = 0; s0 < w; s0 += LB16) {
+    T lv[LB16];
 #pragma unroll
-    for (int q = 0; q < LR_CH; q += 4) {
-      T uv[4];
-      ld4(&U12[s][q], uv);
+    for (int u = 0; u < LB16; ++u) lv[u] = (s0 + u < w) ? X[(int64_t)(p0 + s0 + u) * ldx + r] : T(0);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[q + u] = fma(-lv, uv[u], acc[q + u]);
+    for (int u = 0; u < LB16; ++u) {
+#pragma unroll
+      for (int q = 0; q < LR_CH; q += 4) {
+        T uv[4];
+        ld4(&U12[s0 + u][q], uv);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[q + v] = fma(-lv[u], uv[v], acc[q + v]);
+      }
     }
   }
 #pragma unroll
@@ -506,28 +517,29 @@ __global__ void __launch_bounds__(256) k_lu_trail(T* __restrict__ X, int64_t ldx
     if (q < cw) X[(int64_t)(c0 + q) * ldx + r] = acc[q];
 }
 
-template <typename T, int NB>
+template <typename T, int NB, int NT>
 static size_t lr_smem_bytes(int rpc, int C) {
-  size_t b = (sizeof(LrShared<T, NB>) + 15) / 16 * 16;
+  size_t b = (sizeof(LrShared<T, NB, NT / 32>) + 15) / 16 * 16;
   b += (sizeof(T) * (size_t)NB * NB + 15) / 16 * 16;
-  b += sizeof(int) * (size_t)C;
+  b += sizeof(int) * (size_t)NB;
   (void)rpc;
+  (void)C;
   return b;
 }
 
-template <typename T, bool CROUT, int RT, int NB>
+template <typename T, bool CROUT, int RT, int NB, int NT>
 static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
   *launched = false;
-  const int rpc = LR_NT * RT;
+  const int rpc = NT * RT;
   const int ncta = (int)ceil_div(in.R, rpc);
   if (ncta > 16) return RLU_OK;
   int dev = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
   int optin = 0;
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t bytes = lr_smem_bytes<T, NB>(rpc, in.C);
+  const size_t bytes = lr_smem_bytes<T, NB, NT>(rpc, in.C);
   if (bytes > (size_t)optin) return RLU_OK;
-  auto kern = k_lu_reg<T, CROUT, RT, NB>;
+  auto kern = k_lu_reg<T, CROUT, RT, NB, NT>;
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
@@ -537,7 +549,7 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(ncta);
-  cfg.blockDim = dim3(LR_NT);
+  cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = bytes;
   cfg.stream = s;
   cfg.attrs = attr;
@@ -571,13 +583,13 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
 
 template <typename T, bool CROUT>
 static int32_t launch_reg_t(const LuArgs& a, cudaStream_t s, bool* launched) {
-  // rows per thread RT and register panel NB (NB - 1 columns per panel)
+  // rows per thread RT, register panel NB (NB - 1 columns per panel), threads per CTA
   constexpr int W1 = sizeof(T) == 4 ? 77 : 37;
   constexpr int W2 = sizeof(T) == 4 ? 37 : 19;
-  constexpr int W4 = sizeof(T) == 4 ? 17 : 9;
-  if (a.R <= 16 * LR_NT) RLU_TRY((try_launch<T, CROUT, 1, W1>(a, s, launched)));
-  if (!*launched && a.R <= 32 * LR_NT) RLU_TRY((try_launch<T, CROUT, 2, W2>(a, s, launched)));
-  if (!*launched && a.R <= 64 * LR_NT) RLU_TRY((try_launch<T, CROUT, 4, W4>(a, s, launched)));
+  constexpr int W4 = sizeof(T) == 4 ? 17 : 7;
+  if (a.R <= 16 * 512) RLU_TRY((try_launch<T, CROUT, 1, W1, 512>(a, s, launched)));
+  if (!*launched && a.R <= 16 * 1024) RLU_TRY((try_launch<T, CROUT, 2, W2, 512>(a, s, launched)));
+  if (!*launched && a.R <= 16 * 2048) RLU_TRY((try_launch<T, CROUT, 4, W4, 512>(a, s, launched)));
   return RLU_OK;
 }
 

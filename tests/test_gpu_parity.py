@@ -103,6 +103,7 @@ def test_fp64_deterministic(fp64_512):
     (200, 500, 10, 15),        # wide A
     (64, 40, 40, 40),          # l = min(m, n)
     (1500, 700, 20, 30),       # 3-CTA cluster for Y, 2-CTA for B^T
+    (12000, 300, 30, 40),      # 2 rows per thread, panels starting at odd step pairs
     (40000, 64, 10, 16),       # more rows than the register kernel holds: the smem kernel
 ])
 def test_fp64_shapes(m, n, k, l):
@@ -188,6 +189,17 @@ def test_fp32_error_within_tolerance(m, n, k, l):
     At, P, Q, L, U = g["_dev"]
     fro_d, _ = rlu.reconstruct_error(At, P, Q, L, U)
     assert abs(fro_d.item() - fro_g) <= 1e-9 * fro_g
+
+
+@pytest.mark.parametrize("m,n,k,l", [(12000, 300, 30, 40), (20000, 300, 30, 40)])
+def test_fp32_tall_register_configs(m, n, k, l):
+    """Y taller than one row per thread of a 16-CTA cluster: 2 and 4 rows per thread."""
+    A, g, o, sigma = _fp32_case(m, n, k, l, "inv_square", 2)
+    fro_o, _ = O.reconstruct_error(A, o["P"], o["Q"], o["L"], o["U"], spectral=False)
+    fro_g, _ = O.reconstruct_error(A, g["P"], g["Q"], g["L"], g["U"], spectral=False)
+    assert fro_g <= 1.1 * fro_o + 1e-4 * sigma[0], (fro_g, fro_o)
+    assert leading_agreement(g["P"], o["P"], l) >= min(10, l)
+    assert sorted(g["P"].tolist()) == list(range(m))
 
 
 @pytest.mark.slow
