@@ -48,6 +48,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--prec", choices=["f32", "mixed", "f64"], default=None,
                     help="arithmetic of the path (default: the workload's storage type)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-lambdas", default="300,1000,3000",
+                    help="Poisson arrival rates (requests/s) of the serving measurement")
+    ap.add_argument("--serve-secs", type=float, default=2.0, help="arrival window per rate")
     ap.add_argument("--input", choices=["spectrum", "gaussian"], default="spectrum",
                     help="gaussian: i.i.d. N(0,1) A without the QR setup (for profiler runs; "
                          "no accuracy check)")
@@ -232,7 +236,98 @@ def cpu_baseline(A_host: np.ndarray, w: dict, budget_s: float = 15.0):
 
 
 def precision_of(w):
-    return "f64" if w["dtype"] == "f64" else "f32"
+    """Default path: FP64 for FP64 storage; the tensor-core FP32-accurate path for FP32."""
+    return "f64" if w["dtype"] == "f64" else "mixed"
+
+
+# ---------------------------------------------------------------------------------------
+SERVE_POOL = (512, 1024, 2048, 4096, 8192, 16384)
+
+
+def serve_requests(lam: float, secs: float, rng: np.random.Generator):
+    """Poisson arrivals at rate lam over secs seconds; shapes as the serving workload draws
+    them: m, n log-uniform in [256, 16384], k uniform in [16, 256], l = k + 10, k drawn
+    again while l > min(m, n)."""
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / lam)
+        if t >= secs:
+            return out
+        m = int(np.exp(rng.uniform(np.log(256), np.log(16384))))
+        n = int(np.exp(rng.uniform(np.log(256), np.log(16384))))
+        while True:
+            k = int(rng.integers(16, 257))
+            if k + 10 <= min(m, n):
+                break
+        out.append((t, m, n, k, k + 10))
+
+
+def serve_run(lams, secs: float, seed: int = 7):
+    """The serving form: requests arrive by a Poisson process and are submitted to the
+    server at their arrival times; latency = arrival -> completion (host clock)."""
+    from paper_1310_7202_gb300 import rlu
+
+    pool = {}
+    for sz in SERVE_POOL:   # resident inputs, generated before any timing
+        sigma = synth.spectrum("inv_1p5", sz)
+        pool[sz] = synth.prescribed_matrix_torch(sz, sz, sigma, 31 + sz, 32 + sz, torch.float32)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    res = {}
+    srv = rlu.Server(budget_bytes=24 << 30, max_inflight=16)
+    try:
+        # warm-up: one request per pool size
+        for sz in SERVE_POOL:
+            srv.submit(pool[sz], 16, 26, 1, "mixed", m=sz, n=sz)
+        srv.wait_all()
+        for lam in lams:
+            reqs = serve_requests(lam, secs, rng)
+            ids, t_arr = [], []
+            t0 = time.perf_counter_ns()
+            pending = []
+            for (ta, m, n, k, l) in reqs:
+                target = t0 + int(ta * 1e9)
+                while time.perf_counter_ns() < target:
+                    pass
+                sz = next(s for s in SERVE_POOL if s >= max(m, n))
+                rid = srv.submit(pool[sz], k, l, len(ids) + 1, "mixed", m=m, n=n)
+                ids.append(rid)
+                t_arr.append(target)
+                pending.append(rid)
+                if len(pending) > 64:   # let finished outputs go
+                    keep = []
+                    for r in pending:
+                        if srv.poll(r)["state"] >= rlu.RLU_REQ_DONE:
+                            srv.release(r)
+                        else:
+                            keep.append(r)
+                    pending = keep
+            srv.wait_all()
+            lat, done_t, failed = [], [], 0
+            # perf_counter_ns and the server's steady clock are the same monotonic clock on
+            # Linux (CLOCK_MONOTONIC); latencies are differences on it
+            for rid, ta in zip(ids, t_arr):
+                st = srv.poll(rid)
+                srv.release(rid)
+                if st["state"] != rlu.RLU_REQ_DONE:
+                    failed += 1
+                    continue
+                lat.append((st["t_done"] - ta) / 1e6)
+                done_t.append(st["t_done"])
+            span = (max(done_t) - t0) / 1e9 if done_t else float("nan")
+            res[str(int(lam))] = {
+                "requests": len(ids), "failed": failed,
+                "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+                "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+                "throughput_req_s": len(lat) / span if lat else None}
+        stats = srv.stats()
+    finally:
+        srv.close()
+    return {"lambdas": res, "arrival_window_s": secs, "class": "FP32-accuracy (mixed path)",
+            "max_inflight": 16, "budget_GB": 24, "peak_running": stats["peak_running"],
+            "peak_arena_GB": round(stats["peak_arena_bytes"] / 2 ** 30, 2),
+            "inputs": "top-left m x n blocks of resident prescribed-spectrum matrices "
+                      "(sigma_i = i^-1.5) of sizes " + ",".join(map(str, SERVE_POOL))}
 
 
 # ---------------------------------------------------------------------------------------
@@ -356,6 +451,36 @@ def run_ours(args):
     gemm_ms = stage_ms["gemm_Y"] + stage_ms["gemm_C"]
     gemm_tflops = 2.0 * m * n * (l + k) / (gemm_ms / 1e3) / 1e12
 
+    # ---- the plain FP32 path on the same input, for the "vs plain FP32" comparison -----
+    plain = None
+    if prec == "mixed":
+        fp = rlu.Factorizer(m, n, k, l, "f32")
+        pe = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * ns)]
+              for _ in range(max(3, K // 4))]
+        for _ in range(2):
+            fp(A, w["seed_g"])
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for i in range(len(pe)):
+            fp(A, w["seed_g"], stages={"events": pe[i]})
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / len(pe)
+        pg = statistics.mean(pe[s][2].elapsed_time(pe[s][3]) + pe[s][12].elapsed_time(pe[s][13])
+                             for s in range(len(pe)))
+        Pp, Qp, Lp, Up, _ = fp(A, w["seed_g"])
+        fro_p, _ = rlu.reconstruct_error(A, Pp, Qp, Lp, Up)
+        torch.cuda.synchronize()
+        plain = {"value": 1e3 / pms, "unit": "LU/s", "ms_per_step": pms,
+                 "gemm_tflops": 2.0 * m * n * (l + k) / (pg / 1e3) / 1e12,
+                 "fro": fro_p.item(), "speedup_of_mixed": (1e3 / (ms_max / K)) / (1e3 / pms)}
+        del fp
+
+    serve = None
+    if not args.no_serve and args.workload == WORKLOAD:
+        serve = serve_run([float(x) for x in args.serve_lambdas.split(",") if x], args.serve_secs)
+
     cpu = None
     if not args.no_cpu_baseline and sigma is not None:
         A_host = A.double().cpu().numpy()
@@ -372,11 +497,16 @@ def run_ours(args):
         "vs_baseline": None, "dtype": prec, "data": "synthetic",
         "config": {"workload": f"{args.workload}: m={m} n={n} k={k} l={l}, "
                                f"sigma_i={w['spectrum']}, {w['dtype']} storage, "
-                               f"{prec} path (SIMT GEMMs, cluster LUs)",
+                               f"{prec} path",
                    "m": m, "n": n, "k": k, "l": l, "precision": prec,
+                   "path": ("tcgen05 TF32-split GEMMs (FP32-accurate), cluster register LUs, "
+                            "FP32 LDL^T + blocked triangular solves" if prec == "mixed" else
+                            "SIMT GEMMs, cluster register LUs"),
                    "l2": f"inputs larger than L2 (A = {A.numel() * A.element_size() / 1e6:.0f} MB)",
                    "parallelism": f"{world} independent replica(s)"},
         "gemm_tflops": gemm_tflops,
+        "plain_fp32": plain,
+        "serve": serve,
         "clocks": clocks.summary(),
         "e2e": e2e,
         "gpu_launches": int(launches),

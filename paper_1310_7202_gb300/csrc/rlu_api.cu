@@ -11,7 +11,9 @@
 //   step 7  L = L_y L_b                                          gemm_simt.cu
 //   step 8  U = U_b                                              small.cu gather_lb_u
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "common.cuh"
 #include "gemm_simt.cuh"
@@ -53,30 +55,37 @@ int sm_count() {
   return n;
 }
 
-// Helper stream and fork/join events of one device (created on first use).
+// Helper stream and fork/join events of one caller stream on one device (created on first
+// use), so that concurrent factorizations on different streams keep separate helpers.
 struct SideStream {
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   std::mutex mu;
 };
 
-static int32_t side_stream(SideStream** out) {
-  static SideStream per_dev[64];
+static int32_t side_stream(cudaStream_t main, SideStream** out) {
+  static std::mutex table_mu;
+  static std::map<std::pair<int, cudaStream_t>, SideStream*> table;
   int dev = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return RLU_EUNSUPPORTED;
-  SideStream& ss = per_dev[dev];
-  std::lock_guard<std::mutex> lock(ss.mu);
-  if (ss.side == nullptr) {
-    // highest priority: the Cholesky cluster must get its SMs before the concurrent GEMM
-    // fills the GPU, otherwise it only starts when that GEMM drains
+  SideStream* ss = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(table_mu);
+    SideStream*& slot = table[{dev, main}];
+    if (slot == nullptr) slot = new SideStream();
+    ss = slot;
+  }
+  std::lock_guard<std::mutex> lock(ss->mu);
+  if (ss->side == nullptr) {
+    // highest priority: the factorization's CTA(s) must get their SMs before the
+    // concurrent GEMM fills the GPU, otherwise they only start when that GEMM drains
     int lo = 0, hi = 0;
     RLU_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    RLU_CUDA_TRY(cudaStreamCreateWithPriority(&ss.side, cudaStreamNonBlocking, hi));
-    RLU_CUDA_TRY(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
-    RLU_CUDA_TRY(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+    RLU_CUDA_TRY(cudaStreamCreateWithPriority(&ss->side, cudaStreamNonBlocking, hi));
+    RLU_CUDA_TRY(cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming));
+    RLU_CUDA_TRY(cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming));
   }
-  *out = &ss;
+  *out = ss;
   return RLU_OK;
 }
 
@@ -122,7 +131,6 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   } else {
     return false;
   }
-  if (prec == RLU_PREC_MIXED && l > 256) return false;  // one TMEM accumulator for Y
   if (!(k >= 1 && k <= l && l <= m && l <= n)) return false;
   if (m > INT32_MAX / 2 || n > INT32_MAX / 2) return false;
   p.m = m; p.n = n; p.k = k; p.l = l;
@@ -133,14 +141,14 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   const int bm = gemm_tile_m(p.dt), bn = gemm_tile_n(p.dt);
   p.split_y = split_for(m, l, n, bm, bn);
   if (prec == RLU_PREC_MIXED) {  // tensor-core products: 128-row tiles, split-K fills the SMs
-    p.split_y = umma3_splits(m, n);
+    p.split_y = umma3_splits(m, n, l);
   }
   p.split_g = split_for(k, k, m, bm, bn);
   if (p.dt == RLU_F32 && p.split_g < 2) p.split_g = 2;  // FP32 partials, FP64 reduction
   p.split_c = split_for(k, n, m, bm, bn);
   if (prec == RLU_PREC_MIXED) {
-    p.split_g = umma3_splits(k, m);
-    p.split_c = umma3_splits(n, m);
+    p.split_g = umma3_splits(k, m, k);
+    p.split_c = umma3_splits(n, m, k);
   }
   size_t part = 0;
   auto upd = [&](size_t b) { part = b > part ? b : part; };
@@ -278,7 +286,7 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
   }
   RLU_TRY(tm.rec(4, true, s));
   SideStream* ss = nullptr;
-  RLU_TRY(side_stream(&ss));
+  RLU_TRY(side_stream(s, &ss));
   {
     std::lock_guard<std::mutex> lock(ss->mu);
     RLU_CUDA_TRY(cudaEventRecord(ss->fork, s));
@@ -345,7 +353,7 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
   return RLU_OK;
 }
 
-static int32_t validate(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+int32_t validate(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
                         int32_t k, int32_t l, int32_t prec, const int32_t* P, const int32_t* Q,
                         const void* L, int64_t ldl, const void* U, int64_t ldu) {
   if (!A || !P || !Q || !L || !U) return RLU_EINVAL;

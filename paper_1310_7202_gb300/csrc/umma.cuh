@@ -68,7 +68,7 @@ struct Umma3Op {
 };
 
 int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s);
-int umma3_splits(int64_t M, int64_t K);
+int umma3_splits(int64_t M, int64_t K, int64_t N);
 
 // Fixed-order sum of row-major FP32 partial slices into out (row- or column-major).
 int32_t splitk_reduce_f32(const float* part, int splits, int64_t M, int64_t N, float* out,

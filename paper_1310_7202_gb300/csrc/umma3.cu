@@ -135,6 +135,7 @@ k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtenso
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * U3_BM;
   const int kz = blockIdx.y;
+  const int nb0 = blockIdx.z * a.BN;  // first column of this CTA's N tile
   const int k_begin = kz * a.kchunk;
   const int k_end = min(a.K, k_begin + a.kchunk);
   const int nk = (k_end - k_begin + U3_BK - 1) / U3_BK;
@@ -178,16 +179,16 @@ k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtenso
       const int kx = k_begin + kt * U3_BK;
       if (MODE == U3_MODE_Y2) {
         tma2d(base + lay.a0, &mA0, kx, m0, bar);
-        tma2d(base + lay.b0, &mB0, kx, 0, bar);
+        tma2d(base + lay.b0, &mB0, kx, nb0, bar);
       } else if (MODE == U3_MODE_C3) {
         tma2d(base + lay.a2, &mA0, m0, kx, bar);   // raw A: x = n (128 wide), y = m
-        tma2d(base + lay.b0, &mB0, kx, 0, bar);
-        tma2d(base + lay.b1, &mB1, kx, 0, bar);
+        tma2d(base + lay.b0, &mB0, kx, nb0, bar);
+        tma2d(base + lay.b1, &mB1, kx, nb0, bar);
       } else {
         tma2d(base + lay.a0, &mA0, kx, m0, bar);
         tma2d(base + lay.a1, &mA1, kx, m0, bar);
-        tma2d(base + lay.b0, &mB0, kx, 0, bar);
-        tma2d(base + lay.b1, &mB1, kx, 0, bar);
+        tma2d(base + lay.b0, &mB0, kx, nb0, bar);
+        tma2d(base + lay.b1, &mB1, kx, nb0, bar);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -240,7 +241,7 @@ k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtenso
       if (ok && row < a.M) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int col = c0 + j;
+          const int col = nb0 + c0 + j;
           if (col < a.N) {
             const float f = __uint_as_float(v[j]);
             if (a.out_colmajor)
@@ -342,8 +343,10 @@ static int32_t map2d(CUtensorMap* map, const float* base, int64_t rows, int64_t 
 
 template <int MODE>
 static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
-  if (op.M <= 0 || op.N <= 0 || op.N > 256 || op.K <= 0) return RLU_EINVAL;
-  const int BN = (int)round_up(op.N, 16);
+  if (op.M <= 0 || op.N <= 0 || op.K <= 0) return RLU_EINVAL;
+  // N tiles of up to 256 columns (one TMEM accumulator each), one per grid z index
+  const int BN = op.N > 256 ? 256 : (int)round_up(op.N, 16);
+  const int ntiles = (int)ceil_div(op.N, BN);
   const U3Layout lay = u3_layout(MODE, BN);
   int dev = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
@@ -396,7 +399,7 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
   }
   auto kern = k_umma3<MODE>;
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)ceil_div(op.M, U3_BM), (unsigned)splits);
+  dim3 grid((unsigned)ceil_div(op.M, U3_BM), (unsigned)splits, (unsigned)ntiles);
   kern<<<grid, U3_THREADS, smem, s>>>(m0, m1, n0, n1, a);
   RLU_TRY(last_launch_status());
   if (a.out == op.partial && op.out)
@@ -411,8 +414,8 @@ int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s) {
   return RLU_EINVAL;
 }
 
-int umma3_splits(int64_t M, int64_t K) {
-  const int64_t tiles = ceil_div(M, U3_BM);
+int umma3_splits(int64_t M, int64_t K, int64_t N) {
+  const int64_t tiles = ceil_div(M, U3_BM) * ceil_div(N, 256);
   int64_t s = (int64_t)sm_count() / (tiles > 0 ? tiles : 1);
   const int64_t kmax = K / 256 > 1 ? K / 256 : 1;
   return (int)(s < 1 ? 1 : (s > kmax ? kmax : s));

@@ -1,4 +1,5 @@
-"""Python binding of the C ABI in include/rlu.h (ctypes; argument marshalling only).
+"""Python binding of the C ABI in include/rlu.h and include/rlu_server.h (ctypes; argument
+marshalling only).
 
 Every computation runs in librlu.so's CUDA kernels. PyTorch only provides device memory
 (the tensors passed in and the outputs allocated here) and the current CUDA stream.
@@ -24,15 +25,27 @@ _DT_OF_TORCH = {torch.float64: RLU_F64, torch.float32: RLU_F32, torch.bfloat16: 
 _TORCH_OF_PREC = {RLU_PREC_F64: torch.float64, RLU_PREC_F32: torch.float32,
                   RLU_PREC_MIXED: torch.float32}
 
-# Every symbol include/rlu.h declares.
+# Every symbol include/*.h declares.
 EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian",
             "rlu_workspace_size", "rlu_factor", "rlu_factor_stages", "rlu_timed_step_name",
             "rlu_launch_count", "rlu_reconstruct_workspace_size", "rlu_reconstruct_error",
-            "rlu_reconstruct_error_static")
+            "rlu_reconstruct_error_static", "rlu_server_create", "rlu_server_submit",
+            "rlu_server_poll", "rlu_server_wait_all", "rlu_server_stats", "rlu_server_destroy")
+
+RLU_REQ_QUEUED, RLU_REQ_RUNNING, RLU_REQ_DONE, RLU_REQ_FAILED = 0, 1, 2, 3
 
 
 class RluError(RuntimeError):
     pass
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("lda", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("l", ctypes.c_int32), ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32),
+                ("P", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("L", ctypes.c_void_p),
+                ("ldl", ctypes.c_int64), ("U", ctypes.c_void_p), ("ldu", ctypes.c_int64),
+                ("info", ctypes.c_void_p)]
 
 
 class _StageOutputs(ctypes.Structure):
@@ -87,6 +100,18 @@ def load_library(require_cuda: bool = True) -> ctypes.CDLL:
     lib.rlu_reconstruct_error_static.restype = i32
     lib.rlu_reconstruct_error_static.argtypes = [vp, i32, i64, i64, i64, i32, vp, vp, vp, i64,
                                                  vp, i64, i32, vp, vp, i32, vp]
+    lib.rlu_server_create.restype = i32
+    lib.rlu_server_create.argtypes = [sz, i32, ctypes.POINTER(vp)]
+    lib.rlu_server_submit.restype = i32
+    lib.rlu_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(i64)]
+    lib.rlu_server_poll.restype = i32
+    lib.rlu_server_poll.argtypes = [vp, i64] + [ctypes.POINTER(i32)] * 2 + [ctypes.POINTER(i64)] * 3
+    lib.rlu_server_wait_all.restype = i32
+    lib.rlu_server_wait_all.argtypes = [vp]
+    lib.rlu_server_stats.restype = i32
+    lib.rlu_server_stats.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.rlu_server_destroy.restype = i32
+    lib.rlu_server_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -254,3 +279,82 @@ def reconstruct_error_static(A: torch.Tensor, P: torch.Tensor, Q: torch.Tensor,
         _dev_ptr(out), spec_ptr, power_iters, _stream_ptr(stream)),
         "rlu_reconstruct_error_static")
     return out[0], (out[1] if power_iters > 0 else None)
+
+
+class Server:
+    """The serving loop of include/rlu_server.h: requests of mixed sizes and precisions are
+    admitted as slots and workspace memory (a fixed device budget) free up, and run
+    concurrently on their own streams. A and the outputs stay resident on the device; this
+    wrapper allocates the outputs of each request (P, Q, L, U, info) with torch at submission
+    and keeps references until the request is done."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 8):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self.lib.rlu_server_create(budget_bytes, max_inflight, ctypes.byref(h)),
+               "rlu_server_create")
+        self.h = h
+        self.live: dict[int, dict] = {}
+
+    def submit(self, A: torch.Tensor, k: int, l: int, seed: int, prec: int | str,
+               m: int | None = None, n: int | None = None) -> int:
+        """Queue a factorization of the top-left m x n block of the row-major CUDA tensor A
+        (all of A by default); returns the request id."""
+        prec = PREC_BY_NAME[prec] if isinstance(prec, str) else int(prec)
+        m = A.shape[0] if m is None else m
+        n = A.shape[1] if n is None else n
+        if A.stride(1) != 1 or A.device.type != "cuda" or m > A.shape[0] or n > A.shape[1]:
+            raise RluError("A must be a row-major CUDA tensor holding the m x n block")
+        dt = _TORCH_OF_PREC[prec]
+        out = {"P": torch.empty(m, dtype=torch.int32, device="cuda"),
+               "Q": torch.empty(n, dtype=torch.int32, device="cuda"),
+               "L": _colmajor(m, k, dt), "U": torch.empty((k, n), dtype=dt, device="cuda"),
+               "info": torch.empty(4, dtype=torch.int32, device="cuda"), "A": A}
+        # the outputs were allocated on torch's current stream; the request runs on a slot
+        # stream of the server, so make the allocations visible before it can start
+        torch.cuda.current_stream().synchronize()
+        r = _Request(_dev_ptr(A), _DT_OF_TORCH[A.dtype], m, n, A.stride(0), k, l, seed, prec,
+                     _dev_ptr(out["P"]), _dev_ptr(out["Q"]), _dev_ptr(out["L"]),
+                     out["L"].stride(1), _dev_ptr(out["U"]), out["U"].stride(0),
+                     _dev_ptr(out["info"]))
+        rid = ctypes.c_int64()
+        _check(self.lib.rlu_server_submit(self.h, ctypes.byref(r), ctypes.byref(rid)),
+               "rlu_server_submit")
+        self.live[rid.value] = out
+        return rid.value
+
+    def poll(self, rid: int) -> dict:
+        st, status = ctypes.c_int32(), ctypes.c_int32()
+        t = [ctypes.c_int64() for _ in range(3)]
+        _check(self.lib.rlu_server_poll(self.h, rid, ctypes.byref(st), ctypes.byref(status),
+                                        *[ctypes.byref(x) for x in t]), "rlu_server_poll")
+        return {"state": st.value, "status": status.value, "t_submit": t[0].value,
+                "t_start": t[1].value, "t_done": t[2].value}
+
+    def result(self, rid: int) -> dict:
+        """The output tensors of a request (valid once poll() reports it done)."""
+        return self.live[rid]
+
+    def release(self, rid: int) -> None:
+        """Drop this wrapper's references to a finished request's outputs."""
+        self.live.pop(rid, None)
+
+    def wait_all(self) -> None:
+        _check(self.lib.rlu_server_wait_all(self.h), "rlu_server_wait_all")
+
+    def stats(self) -> dict:
+        a = (ctypes.c_int64 * 6)()
+        _check(self.lib.rlu_server_stats(self.h, a), "rlu_server_stats")
+        return {"submitted": a[0], "done": a[1], "failed": a[2], "peak_arena_bytes": a[3],
+                "peak_running": a[4], "bypassed_admissions": a[5]}
+
+    def close(self) -> None:
+        if self.h:
+            _check(self.lib.rlu_server_destroy(self.h), "rlu_server_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,5 +1,5 @@
 """C ABI checks that need no GPU: librlu.so builds, loads, exports every entry point that
-include/rlu.h declares, and rejects bad arguments on the host before any device work."""
+include/*.h declares, and rejects bad arguments on the host before any device work."""
 import ctypes
 import os
 import re
@@ -19,9 +19,13 @@ def lib():
 
 
 def _declared_functions():
-    text = open(os.path.join(ROOT, "include", "rlu.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(rlu_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names.update(re.findall(r"\b(rlu_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_binding_exports():
@@ -82,3 +86,17 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(rlu, "LIB_PATH", "/nonexistent/librlu.so")
     with pytest.raises(rlu.RluError):
         rlu.load_library(require_cuda=False)
+
+
+def test_server_rejects_bad_arguments_on_host(lib):
+    h = ctypes.c_void_p()
+    assert lib.rlu_server_create(0, 4, ctypes.byref(h)) == rlu.RLU_EINVAL        # no budget
+    assert lib.rlu_server_create(1 << 20, 0, ctypes.byref(h)) == rlu.RLU_EINVAL  # no slots
+    assert lib.rlu_server_create(1 << 20, 65, ctypes.byref(h)) == rlu.RLU_EINVAL
+    assert lib.rlu_server_create(1 << 20, 4, None) == rlu.RLU_EINVAL
+    rid = ctypes.c_int64()
+    assert lib.rlu_server_submit(None, None, ctypes.byref(rid)) == rlu.RLU_EINVAL
+    assert lib.rlu_server_poll(None, 0, None, None, None, None, None) == rlu.RLU_EINVAL
+    assert lib.rlu_server_wait_all(None) == rlu.RLU_EINVAL
+    assert lib.rlu_server_stats(None, None) == rlu.RLU_EINVAL
+    assert lib.rlu_server_destroy(None) == rlu.RLU_EINVAL

@@ -19,6 +19,8 @@ pytestmark = pytest.mark.gpu
     (1000, 777, 20, 37),      # lda not a multiple of 4: SIMT fallback for Y
     (300, 5000, 8, 16),       # long K: split-K partials
     (4096, 2048, 200, 210),   # the bench's l
+    (2048, 1800, 256, 266),   # l > 256: two N tiles of the tensor-core products
+    (3000, 2500, 300, 310),   # k > 256: N tiles in the Gram and C products, FP64 LDL^T
 ])
 def test_mixed_projection_and_error(m, n, k, l):
     sigma = synth.spectrum("inv_square", min(m, n))
