@@ -44,18 +44,32 @@ typedef enum {
 
 typedef enum { RLU_F64 = 0, RLU_F32 = 1, RLU_BF16 = 2 } rlu_dtype;
 
-/* Arithmetic of the whole path.
+/* Arithmetic of the whole path. In every precision the pseudo-inverse product of step 5
+ * solves the normal equations M B = C with M = L~^T L~ reduced in FP64 and factored as
+ * L D L^T (FP64 for RLU_PREC_F64 and for k > 256; FP32 otherwise), followed by blocked
+ * triangular solves in the path's type.
  *   RLU_PREC_F64: A, G, Y, B, L, U in FP64, FP64 arithmetic everywhere. A must be RLU_F64.
- *   RLU_PREC_F32: "plain FP32". A, G, Y, B, L, U in FP32; FP32 SIMT GEMMs and LUs; the
- *                 k x k Gram matrix is reduced in FP64 and factored (Cholesky) in FP64.
+ *   RLU_PREC_F32: "plain FP32". A, G, Y, B, L, U in FP32; FP32 SIMT GEMMs and LUs.
  *                 A must be RLU_F32.
- *   RLU_PREC_MIXED: as RLU_PREC_F32, but the projection Y = A G (step 2) runs on the tensor
- *                 cores with TF32 inputs and FP32 accumulation (the random range finder
- *                 tolerates the rounding of A and G to TF32). A must be RLU_F32. The
- *                 tensor-core projection reads A with TMA, which needs 16-byte aligned
- *                 rows (A aligned, lda a multiple of 4); otherwise step 2 runs on the
- *                 FP32 SIMT GEMM. */
-typedef enum { RLU_PREC_F64 = 0, RLU_PREC_F32 = 1, RLU_PREC_MIXED = 2 } rlu_precision;
+ *   RLU_PREC_MIXED: as RLU_PREC_F32, but the three large products run on the tensor cores
+ *                 from exact TF32 splits, FP32-accurate: Y = A G as hi(A) G + lo(A) G (G is
+ *                 rounded to TF32, which only changes the Gaussian test matrix), the Gram
+ *                 matrix and C = L~^T A with three products each. A must be RLU_F32. The
+ *                 tensor-core products read A with TMA, which needs 16-byte aligned rows
+ *                 (A aligned, lda a multiple of 4); otherwise they run on the FP32 SIMT
+ *                 GEMM.
+ *   RLU_PREC_BF16: the precision form for A stored in BF16 (A must be RLU_BF16, 16-byte
+ *                 aligned, lda a multiple of 8, else RLU_EINVAL). G is generated in BF16 and
+ *                 Y = A G runs on the BF16 tensor cores with FP32 accumulation; C = L~^T A
+ *                 takes L~ in three BF16 parts (hi + mid + lo, FP32 accurate) against the
+ *                 exact BF16 A; Y, L~, the Gram matrix (TF32 splits as in RLU_PREC_MIXED), the
+ *                 LUs, L and U are FP32 (L and U are returned in FP32). */
+typedef enum {
+  RLU_PREC_F64 = 0,
+  RLU_PREC_F32 = 1,
+  RLU_PREC_MIXED = 2,
+  RLU_PREC_BF16 = 3
+} rlu_precision;
 
 /* Device-resident status written by rlu_factor (the caller reads it after the stream
  * completes). */

@@ -111,7 +111,7 @@ struct Plan {
   size_t off_G = 0, off_Y = 0, off_Lt = 0, off_Lp = 0, off_M = 0, off_dinv = 0, off_LT = 0,
          off_LR = 0, off_W = 0, off_WT = 0,
          off_C = 0, off_T = 0, off_B = 0, off_Lb = 0, off_part = 0, off_Lhi = 0, off_Llo = 0,
-         off_pos = 0, off_ps = 0, total = 0;
+         off_pos = 0, off_ps = 0, off_Bh = 0, off_Bm = 0, off_Bl = 0, total = 0;
 };
 
 static size_t carve(size_t& cur, size_t bytes) {
@@ -125,8 +125,8 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   if (prec == RLU_PREC_F64) {
     p.dt = RLU_F64;
     p.esz = 8;
-  } else if (prec == RLU_PREC_F32 || prec == RLU_PREC_MIXED) {
-    p.dt = RLU_F32;
+  } else if (prec == RLU_PREC_F32 || prec == RLU_PREC_MIXED || prec == RLU_PREC_BF16) {
+    p.dt = RLU_F32;  // the path's type: Y, L~, the LUs, L and U (A may be BF16)
     p.esz = 4;
   } else {
     return false;
@@ -143,13 +143,15 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   if (prec == RLU_PREC_MIXED) {  // tensor-core products: 128-row tiles, split-K fills the SMs
     p.split_y = umma3_splits(m, n, l);
   }
+  if (prec == RLU_PREC_BF16) p.split_y = umma_bf16_splits(m, n, l, 256);
   p.split_g = split_for(k, k, m, bm, bn);
   if (p.dt == RLU_F32 && p.split_g < 2) p.split_g = 2;  // FP32 partials, FP64 reduction
   p.split_c = split_for(k, n, m, bm, bn);
-  if (prec == RLU_PREC_MIXED) {
+  if (prec == RLU_PREC_MIXED || prec == RLU_PREC_BF16) {
     p.split_g = umma3_splits(k, m, k);
     p.split_c = umma3_splits(n, m, k);
   }
+  if (prec == RLU_PREC_BF16) p.split_c = umma_bf16_splits(n, m, k, 128);
   size_t part = 0;
   auto upd = [&](size_t b) { part = b > part ? b : part; };
   if (p.split_y > 1) upd((size_t)p.split_y * m * l * p.esz);
@@ -174,16 +176,21 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   p.off_part = carve(cur, part);
   p.off_pos = carve(cur, (size_t)(m > n ? m : n) * sizeof(int32_t));  // LU position state
   p.off_ps = carve(cur, (size_t)l * sizeof(int32_t));
-  if (prec == RLU_PREC_MIXED) {
+  if (prec == RLU_PREC_MIXED || prec == RLU_PREC_BF16) {
     p.off_Lhi = carve(cur, (size_t)p.ldl * k * e);
     p.off_Llo = carve(cur, (size_t)p.ldl * k * e);
+  }
+  if (prec == RLU_PREC_BF16) {  // L~ in three BF16 parts for the products with BF16 A
+    p.off_Bh = carve(cur, (size_t)p.ldl * k * 2);
+    p.off_Bm = carve(cur, (size_t)p.ldl * k * 2);
+    p.off_Bl = carve(cur, (size_t)p.ldl * k * 2);
   }
   p.total = cur;
   return true;
 }
 
 template <typename T>
-static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, int32_t* P,
+static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t seed, int32_t* P,
                         int32_t* Q, T* L, int64_t ldl_out, T* U, int64_t ldu, rlu_info* info,
                         char* ws, const rlu_stage_outputs* st, cudaStream_t s) {
   T* G = reinterpret_cast<T*>(ws + p.off_G);
@@ -203,6 +210,8 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
   T* Bb = reinterpret_cast<T*>(ws + p.off_B);
   T* Lb = reinterpret_cast<T*>(ws + p.off_Lb);
   void* part = ws + p.off_part;
+  const T* A = static_cast<const T*>(Av);  // FP32/FP64 storage (BF16: only Av is read)
+  const bool bf16 = p.prec == RLU_PREC_BF16;
   const int64_t m = p.m, n = p.n;
   const int k = p.k, l = p.l;
 
@@ -210,14 +219,36 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
   if (info) RLU_TRY(info_init(info, s));
   // step 1
   RLU_TRY(tm.rec(0, false, s));
-  RLU_TRY(launch_gaussian(seed, 0, n, l, p.dt, G, p.ldg, s));
+  RLU_TRY(launch_gaussian(seed, 0, n, l, bf16 ? RLU_BF16 : p.dt, G, p.ldg, s));
   RLU_TRY(tm.rec(0, true, s));
-  if (st && st->G) RLU_TRY(copy_cm<T>(G, p.ldg, static_cast<T*>(st->G), n, n, l, s));
+  if (st && st->G) {
+    if (bf16)
+      RLU_TRY(copy_cm<__nv_bfloat16>(reinterpret_cast<const __nv_bfloat16*>(G), p.ldg,
+                                     static_cast<__nv_bfloat16*>(st->G), n, n, l, s));
+    else
+      RLU_TRY(copy_cm<T>(G, p.ldg, static_cast<T*>(st->G), n, n, l, s));
+  }
   // step 2: Y (m x l, col-major) = A (row-major) * G (col-major)
   RLU_TRY(tm.rec(1, false, s));
   // the tensor-core projection reads A with TMA: rows must start on 16-byte boundaries
   const bool tma_ok = ((uintptr_t)A & 15u) == 0 && (lda * (int64_t)sizeof(T)) % 16 == 0;
-  if (p.prec == RLU_PREC_MIXED && tma_ok) {
+  if (bf16) {  // BF16 A and G, FP32 accumulation (validated: A rows 16-byte aligned)
+    UmmaBf16Op op{};
+    op.A = Av;
+    op.lda = lda;
+    op.B0 = G;
+    op.ldb = p.ldg;
+    op.M = m;
+    op.N = l;
+    op.K = n;
+    op.out = reinterpret_cast<float*>(Y);
+    op.ldo = p.ldy;
+    op.out_colmajor = true;
+    op.splits = p.split_y;
+    op.partial = reinterpret_cast<float*>(part);
+    op.status = info ? &info->status : nullptr;
+    RLU_TRY(umma_bf16_gemm(UB_MODE_Y, op, s));
+  } else if (p.prec == RLU_PREC_MIXED && tma_ok) {
     Umma3Op op{};
     op.A0 = reinterpret_cast<const float*>(A);
     op.lda = lda;
@@ -256,7 +287,13 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
   RLU_TRY(tm.rec(3, false, s));
   T* Lhi = p.off_Lhi ? reinterpret_cast<T*>(ws + p.off_Lhi) : nullptr;
   T* Llo = p.off_Llo ? reinterpret_cast<T*>(ws + p.off_Llo) : nullptr;
-  RLU_TRY(build_ly<T>(Y, p.ldy, m, k, P, Lt, Lp, p.ldl, s, Lhi, Llo));
+  Bf16Parts bp{};
+  if (bf16) {
+    bp.hi = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Bh);
+    bp.mid = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Bm);
+    bp.lo = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Bl);
+  }
+  RLU_TRY(build_ly<T>(Y, p.ldy, m, k, P, Lt, Lp, p.ldl, s, Lhi, Llo, bp));
   RLU_TRY(tm.rec(3, true, s));
   if (st && st->Ly) RLU_TRY(copy_cm<T>(Lp, p.ldl, static_cast<T*>(st->Ly), m, m, k, s));
   // step 5: Gram M = L~^T L~ in FP64
@@ -297,7 +334,25 @@ static int32_t factor_t(const Plan& p, const T* A, int64_t lda, uint64_t seed, i
     RLU_CUDA_TRY(cudaEventRecord(ss->join, ss->side));
     // C = L~^T A (k x n, row-major)
     RLU_TRY(tm.rec(6, false, s));
-    if (Lhi && tma_ok) {  // C^T = A^T L~ on the tensor cores, 3 TF32 products
+    if (bf16) {  // C^T = A^T L~ with BF16 A and L~ in three BF16 parts
+      UmmaBf16Op op{};
+      op.A = Av;
+      op.lda = lda;
+      op.B0 = bp.hi;
+      op.B1 = bp.mid;
+      op.B2 = bp.lo;
+      op.ldb = p.ldl;
+      op.M = n;
+      op.N = k;
+      op.K = m;
+      op.out = reinterpret_cast<float*>(Cb);
+      op.ldo = p.ldb;
+      op.out_colmajor = true;
+      op.splits = p.split_c;
+      op.partial = reinterpret_cast<float*>(part);
+      op.status = info ? &info->status : nullptr;
+      RLU_TRY(umma_bf16_gemm(UB_MODE_C3, op, s));
+    } else if (Lhi && tma_ok) {  // C^T = A^T L~ on the tensor cores, 3 TF32 products
       Umma3Op op{};
       op.A0 = reinterpret_cast<const float*>(A);
       op.lda = lda;
@@ -362,7 +417,13 @@ int32_t validate(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda
   if (prec == RLU_PREC_F64 && dtype != RLU_F64) return RLU_EUNSUPPORTED;
   if ((prec == RLU_PREC_F32 || prec == RLU_PREC_MIXED) && dtype != RLU_F32)
     return RLU_EUNSUPPORTED;
-  if (prec != RLU_PREC_F64 && prec != RLU_PREC_F32 && prec != RLU_PREC_MIXED)
+  if (prec == RLU_PREC_BF16) {
+    if (dtype != RLU_BF16) return RLU_EUNSUPPORTED;
+    // the BF16 products read A with TMA: rows on 16-byte boundaries
+    if (((uintptr_t)A & 15u) != 0 || lda % 8 != 0) return RLU_EINVAL;
+  }
+  if (prec != RLU_PREC_F64 && prec != RLU_PREC_F32 && prec != RLU_PREC_MIXED &&
+      prec != RLU_PREC_BF16)
     return RLU_EUNSUPPORTED;
   return RLU_OK;
 }
@@ -410,10 +471,10 @@ extern "C" int32_t rlu_factor_stages(const void* A, int32_t dtype, int64_t m, in
   if (((uintptr_t)workspace & 255u) != 0) return RLU_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   if (p.dt == RLU_F64)
-    return factor_t<double>(p, (const double*)A, lda, seed, P, Q, (double*)L, ldl, (double*)U,
-                            ldu, info, (char*)workspace, stages, s);
-  return factor_t<float>(p, (const float*)A, lda, seed, P, Q, (float*)L, ldl, (float*)U, ldu,
-                         info, (char*)workspace, stages, s);
+    return factor_t<double>(p, A, lda, seed, P, Q, (double*)L, ldl, (double*)U, ldu, info,
+                            (char*)workspace, stages, s);
+  return factor_t<float>(p, A, lda, seed, P, Q, (float*)L, ldl, (float*)U, ldu, info,
+                         (char*)workspace, stages, s);
 }
 
 extern "C" int32_t rlu_factor(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,

@@ -3,7 +3,8 @@
 //  * build_ly (steps 4-5): from the swap-free factored Y and its position map, L_y in pivot
 //    row order (Lp, for step 7) and L~ = P^T L_y in original row order (Lt, so that
 //    L_y^T P A = L~^T A without permuting A); optionally L~ split exactly into a TF32 part
-//    and an FP32 remainder for the tensor-core products of step 5.
+//    and an FP32 remainder, and into three BF16 parts, for the tensor-core products of
+//    step 5.
 //  * ldl_factor (step 5, remark after Algorithm 1): M = L_y^T L_y = L D L^T (the Cholesky
 //    factor is D^{1/2} L^T), plus the inverses of L's 32 x 32 diagonal blocks: in FP32 on
 //    one CTA for the single-precision paths (k <= 256), else in FP64 on a thread-block
@@ -27,11 +28,24 @@ __device__ __forceinline__ void tf32_split(float x, float* hi, float* lo, int64_
 }
 __device__ __forceinline__ void tf32_split(double, double*, double*, int64_t) {}
 
+// x = hi + mid + lo with each part a BF16 (8 significant bits): hi = bf16(x), the
+// remainders x - hi and (x - hi) - mid are exact in FP32, so hi + mid + lo carries 24 bits.
+__device__ __forceinline__ void bf16_split3(float x, __nv_bfloat16* h, __nv_bfloat16* mi,
+                                            __nv_bfloat16* lo, int64_t at) {
+  const __nv_bfloat16 a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  const __nv_bfloat16 b = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(b);
+  h[at] = a;
+  mi[at] = b;
+  lo[at] = __float2bfloat16_rn(r2);
+}
+
 template <typename T>
 __global__ void k_build_ly(const T* __restrict__ Y, int64_t ldy, int64_t m, int k,
                            const int32_t* __restrict__ perm, T* __restrict__ Lt,
                            T* __restrict__ Lp, int64_t ldl, T* __restrict__ Lhi,
-                           T* __restrict__ Llo) {
+                           T* __restrict__ Llo, Bf16Parts bp) {
   const int c = blockIdx.y;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -40,23 +54,24 @@ __global__ void k_build_ly(const T* __restrict__ Y, int64_t ldy, int64_t m, int 
     if (Lp) Lp[(int64_t)c * ldl + p] = v;
     if (Lt) Lt[(int64_t)c * ldl + r] = v;
     if (Lhi) tf32_split(v, Lhi, Llo, (int64_t)c * ldl + r);
+    if (bp.hi) bf16_split3((float)v, bp.hi, bp.mid, bp.lo, (int64_t)c * ldl + r);
   }
 }
 
 template <typename T>
 int32_t build_ly(const T* Y, int64_t ldy, int64_t m, int k, const int32_t* perm, T* Lt, T* Lp,
-                 int64_t ldl, cudaStream_t s, T* Lhi, T* Llo) {
+                 int64_t ldl, cudaStream_t s, T* Lhi, T* Llo, Bf16Parts bp) {
   const int threads = 256;
   int64_t bx = ceil_div(m, threads);
   if (bx > 4096) bx = 4096;
   k_build_ly<T><<<dim3((unsigned)bx, (unsigned)k), threads, 0, s>>>(Y, ldy, m, k, perm, Lt, Lp,
-                                                                   ldl, Lhi, Llo);
+                                                                   ldl, Lhi, Llo, bp);
   return last_launch_status();
 }
 template int32_t build_ly<float>(const float*, int64_t, int64_t, int, const int32_t*, float*,
-                                 float*, int64_t, cudaStream_t, float*, float*);
+                                 float*, int64_t, cudaStream_t, float*, float*, Bf16Parts);
 template int32_t build_ly<double>(const double*, int64_t, int64_t, int, const int32_t*, double*,
-                                  double*, int64_t, cudaStream_t, double*, double*);
+                                  double*, int64_t, cudaStream_t, double*, double*, Bf16Parts);
 
 // LDL^T factorization M = L D L^T (FP64, L unit lower) on one thread-block cluster; the
 // Cholesky factor is R = D^{1/2} L^T. M (k x k, row-major, global) is read once; block
@@ -756,6 +771,8 @@ template int32_t copy_cm<float>(const float*, int64_t, float*, int64_t, int64_t,
                                 cudaStream_t);
 template int32_t copy_cm<double>(const double*, int64_t, double*, int64_t, int64_t, int64_t,
                                  cudaStream_t);
+template int32_t copy_cm<__nv_bfloat16>(const __nv_bfloat16*, int64_t, __nv_bfloat16*, int64_t,
+                                        int64_t, int64_t, cudaStream_t);
 
 __global__ void k_info_init(rlu_info* info) {
   info->status = RLU_OK;

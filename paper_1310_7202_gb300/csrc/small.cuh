@@ -5,9 +5,17 @@
 
 namespace rlu {
 
+// Three BF16 parts (hi + mid + lo) of L~, same layout as L~ (ld ldl); all null when unused.
+struct Bf16Parts {
+  __nv_bfloat16* hi = nullptr;
+  __nv_bfloat16* mid = nullptr;
+  __nv_bfloat16* lo = nullptr;
+};
+
 template <typename T>
 int32_t build_ly(const T* Y, int64_t ldy, int64_t m, int k, const int32_t* perm, T* Lt, T* Lp,
-                 int64_t ldl, cudaStream_t s, T* Lhi = nullptr, T* Llo = nullptr);
+                 int64_t ldl, cudaStream_t s, T* Lhi = nullptr, T* Llo = nullptr,
+                 Bf16Parts bp = Bf16Parts{});
 
 // Outputs of the LDL^T factorization M = L D L^T that the triangular solves read, in the
 // path's type and zero-padded to kp = 32 * ceil(k / 32) (identity on the padded diagonal):

@@ -68,6 +68,29 @@ struct Umma3Op {
 };
 
 int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s);
+
+// BF16 products (see umma_bf16.cu), same output conventions as Umma3Op.
+// Y : A (M x K row-major BF16, lda), B0 = G^T (N x K row-major BF16, ldb), one product.
+// C3: A stored K x M row-major BF16 (lda); B0/B1/B2 = hi/mid/lo BF16 parts (N x K, ldb).
+enum { UB_MODE_Y = 0, UB_MODE_C3 = 1 };
+struct UmmaBf16Op {
+  const void* A;
+  int64_t lda;
+  const void* B0;
+  const void* B1;
+  const void* B2;
+  int64_t ldb;
+  int64_t M, N, K;
+  float* out;
+  int64_t ldo;
+  bool out_colmajor;
+  int splits;
+  float* partial;
+  int32_t* status;
+};
+int32_t umma_bf16_gemm(int mode, const UmmaBf16Op& op, cudaStream_t s);
+// split-K factor that fills the SMs for an M x N output (N tiles of bn columns)
+int umma_bf16_splits(int64_t M, int64_t K, int64_t N, int bn);
 int umma3_splits(int64_t M, int64_t K, int64_t N);
 
 // Fixed-order sum of row-major FP32 partial slices into out (row- or column-major).

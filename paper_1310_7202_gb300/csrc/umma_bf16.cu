@@ -1,0 +1,384 @@
+// BF16 tensor-core GEMMs on tcgen05/TMEM (sm_103a) for the precision form of Algorithm 1
+// (A stored in BF16): D (M x N, FP32 accumulation in TMEM) = A (M x K) * B (N x K)^T with
+// kind::f16 MMAs on BF16 operands.
+//
+//   UB_MODE_Y   Y = A G (step 2): A row-major (K = n contiguous), G column-major (K
+//               contiguous); both arrive by TMA in 128-byte-swizzled K-major tiles. One
+//               product: the range finder only needs Y's column space, so BF16 A and G with
+//               FP32 accumulation suffice.
+//   UB_MODE_C3  C^T = A^T L~ (step 5): the A tile arrives n-contiguous and is transposed on
+//               chip into a K-major tile (A is exact in BF16, nothing to split); L~ comes as
+//               three BF16 parts hi + mid + lo (8 significant bits each, FP32 accurate), so
+//               three products A L_hi + A L_mid + A L_lo accumulate in FP32.
+//
+// Warp roles as in the TF32 kernels: warp 0 TMA producer over a ring of slots, warp 1 TMEM
+// allocation and MMA issue, warps 2..5 epilogue, warps 6..9 the transposing converter
+// (UB_MODE_C3). Every wait is bounded (~1 s) and records an error instead of hanging.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace rlu {
+
+static constexpr int UB_BM = 128;
+static constexpr int UB_BK = 64;  // BF16 elements: one 128-byte swizzle row
+static constexpr int UB_THREADS = 320;
+static constexpr int UB_MAXST = 4;
+
+struct UbSmem {
+  uint64_t full[UB_MAXST];
+  uint64_t conv[UB_MAXST];
+  uint64_t empty[UB_MAXST];
+  uint64_t accum;
+  uint32_t tmem_base;
+  int32_t err;
+};
+
+namespace ub {
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mb_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+               ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n"
+               ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mb_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity) {
+  if (mb_try(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (!mb_try(bar, parity))
+    if (now_ns() - t0 > 1000000000ull) return false;
+  return true;
+}
+__device__ __forceinline__ void tma2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                      uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// K-major operand in 128-byte-swizzled rows: 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+               ::"r"(bar) : "memory");
+}
+}  // namespace ub
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B BF16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t ub_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+struct UbLayout {
+  uint32_t a0, a2, b0, b1, b2, stage, tx;
+};
+__host__ __device__ inline UbLayout ub_layout(int mode, int BN) {
+  UbLayout L{};
+  const uint32_t at = UB_BM * 128, bt = (uint32_t)BN * 128;
+  if (mode == UB_MODE_Y) {  // a0: A, b0: G
+    L.a0 = 0; L.b0 = at; L.b1 = L.b2 = L.b0; L.a2 = 0; L.stage = at + bt; L.tx = at + bt;
+  } else {                  // a2: raw A (64 x 128, n contiguous), a0: K-major A, b0..b2: L~
+    L.a2 = 0; L.a0 = at; L.b0 = 2 * at; L.b1 = 2 * at + bt; L.b2 = 2 * at + 2 * bt;
+    L.stage = 2 * at + 3 * bt; L.tx = at + 3 * bt;
+  }
+  L.stage = (L.stage + 1023u) & ~1023u;
+  return L;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(UB_THREADS, 1)
+k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB0,
+        const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
+        Umma3Args a) {
+  using namespace ub;
+  extern __shared__ __align__(1024) unsigned char ub_smem[];
+  UbSmem& sh = *reinterpret_cast<UbSmem*>(ub_smem);
+  const uint32_t tiles = (su32(ub_smem) + sizeof(UbSmem) + 1023u) & ~1023u;
+  const UbLayout lay = ub_layout(MODE, a.BN);
+  const int S = a.stages;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * UB_BM;
+  const int kz = blockIdx.y;
+  const int nb0 = blockIdx.z * a.BN;
+  const int k_begin = kz * a.kchunk;
+  const int k_end = min(a.K, k_begin + a.kchunk);
+  const int nk = (k_end - k_begin + UB_BK - 1) / UB_BK;
+  constexpr bool CONV = (MODE == UB_MODE_C3);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mb_init(su32(&sh.full[s]), 1);
+      mb_init(su32(&sh.conv[s]), 128);
+      mb_init(su32(&sh.empty[s]), 1);
+    }
+    mb_init(su32(&sh.accum), 1);
+    sh.err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n"
+                 ::"r"(su32(&sh.tmem_base)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = sh.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ------------------------------------------------------------------
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % S;
+      if (kt >= S && !mb_wait(su32(&sh.empty[s]), (uint32_t)(((kt / S) - 1) & 1))) {
+        sh.err = 1;
+        break;
+      }
+      const uint32_t base = tiles + s * lay.stage;
+      const uint32_t bar = su32(&sh.full[s]);
+      mb_expect_tx(bar, lay.tx);
+      const int kx = k_begin + kt * UB_BK;
+      if (MODE == UB_MODE_Y) {
+        tma2d(base + lay.a0, &mA, kx, m0, bar);
+        tma2d(base + lay.b0, &mB0, kx, nb0, bar);
+      } else {
+        tma2d(base + lay.a2, &mA, m0, kx, bar);  // raw A: x = n (128 wide), y = m (64)
+        tma2d(base + lay.b0, &mB0, kx, nb0, bar);
+        tma2d(base + lay.b1, &mB1, kx, nb0, bar);
+        tma2d(base + lay.b2, &mB2, kx, nb0, bar);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: 4 MMAs of K = 16 per 64-wide slot ---------------------------------
+    const uint32_t idesc = ub_idesc(UB_BM, a.BN);
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % S;
+      const uint32_t par = (uint32_t)((kt / S) & 1);
+      if (!mb_wait(su32(CONV ? &sh.conv[s] : &sh.full[s]), par)) {
+        sh.err = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t base = tiles + s * lay.stage;
+#pragma unroll
+      for (int kk = 0; kk < UB_BK / 16; ++kk) {
+        const uint32_t off = kk * 32;
+        const uint64_t da = desc_sw128(base + lay.a0 + off);
+        mma_bf16(tmem, da, desc_sw128(base + lay.b0 + off), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+        if (MODE == UB_MODE_C3) {
+          mma_bf16(tmem, da, desc_sw128(base + lay.b1 + off), idesc, 1u);
+          mma_bf16(tmem, da, desc_sw128(base + lay.b2 + off), idesc, 1u);
+        }
+      }
+      commit(su32(&sh.empty[s]));
+    }
+    commit(su32(&sh.accum));
+  } else if (warp >= 2 && warp < 6) {
+    // ---- epilogue ------------------------------------------------------------------------
+    const bool ok = mb_wait(su32(&sh.accum), 0u);
+    if (!ok) sh.err = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int quarter = warp & 3;
+    const int row = m0 + quarter * 32 + lane;
+    float* __restrict__ out = a.out + (size_t)kz * a.split_stride;
+    for (int c0 = 0; c0 < a.BN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+          "%28, %29, %30, %31}, [%32];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (ok && row < a.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = nb0 + c0 + j;
+          if (c0 + j < a.BN && col < a.N) {
+            const float f = __uint_as_float(v[j]);
+            if (a.out_colmajor)
+              out[(size_t)col * a.ldo + row] = f;
+            else
+              out[(size_t)row * a.ldo + col] = f;
+          }
+        }
+      }
+    }
+  } else if (CONV && warp >= 6) {
+    // ---- converter: thread r builds K-major row r (128 bytes = 8 chunks of 8 BF16) of the
+    // A tile from column r of the raw 64 x 128 tile; chunk c goes to position c ^ (r & 7)
+    const int r = threadIdx.x - 192;  // 0..127
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % S;
+      if (!mb_wait(su32(&sh.full[s]), (uint32_t)((kt / S) & 1))) {
+        sh.err = 1;
+        break;
+      }
+      const uint32_t base = tiles + s * lay.stage;
+      const uint16_t* raw =
+          reinterpret_cast<const uint16_t*>(ub_smem + (base + lay.a2 - su32(ub_smem)));
+      unsigned char* dst = ub_smem + (base + lay.a0 - su32(ub_smem)) + r * 128;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          w[j] = (uint32_t)raw[(8 * c + 2 * j) * UB_BM + r] |
+                 ((uint32_t)raw[(8 * c + 2 * j + 1) * UB_BM + r] << 16);
+        *reinterpret_cast<uint4*>(dst + 16 * (c ^ (r & 7))) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mb_arrive(su32(&sh.conv[s]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
+  }
+  if (threadIdx.x == 0 && sh.err && a.status) atomicExch(a.status, RLU_ETIMEOUT);
+}
+
+// ---------------------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 ub_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// BF16 row-major (rows x cols, ld elements) tensor map with a box of box_x x box_y.
+static int32_t map2d_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
+                          int64_t ld, int box_x, int box_y, bool swizzle) {
+  auto enc = ub_encode_fn();
+  if (!enc) return RLU_ECUDA;
+  if (((uintptr_t)base & 15u) != 0 || (ld * 2) % 16 != 0) return RLU_EINVAL;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RLU_OK : RLU_ECUDA;
+}
+
+template <int MODE>
+static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
+  if (op.M <= 0 || op.N <= 0 || op.K <= 0) return RLU_EINVAL;
+  // N tiles: up to 256 columns for Y; 128 for C3, whose slot holds three B tiles
+  const int bnmax = MODE == UB_MODE_Y ? 256 : 128;
+  const int BN = op.N > bnmax ? bnmax : (int)round_up(op.N, 16);
+  const int ntiles = (int)ceil_div(op.N, BN);
+  const UbLayout lay = ub_layout(MODE, BN);
+  int dev = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  int optin = 0;
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int ctrl = 2048;
+  int stages = (int)((optin - ctrl) / (int)lay.stage);
+  if (stages > UB_MAXST) stages = UB_MAXST;
+  if (stages < 2) return RLU_EUNSUPPORTED;
+  const size_t smem = (size_t)ctrl + (size_t)stages * lay.stage;
+  CUtensorMap mA{}, b0{}, b1{}, b2{};
+  if (MODE == UB_MODE_Y) {
+    RLU_TRY(map2d_bf16(&mA, op.A, op.M, op.K, op.lda, UB_BK, UB_BM, true));
+    RLU_TRY(map2d_bf16(&b0, op.B0, op.N, op.K, op.ldb, UB_BK, BN, true));
+    b1 = b2 = b0;
+  } else {
+    // A stored row-major K x M (rows = K index, M contiguous): box 128 (M) x 64 (K)
+    RLU_TRY(map2d_bf16(&mA, op.A, op.K, op.M, op.lda, UB_BM, UB_BK, false));
+    RLU_TRY(map2d_bf16(&b0, op.B0, op.N, op.K, op.ldb, UB_BK, BN, true));
+    RLU_TRY(map2d_bf16(&b1, op.B1, op.N, op.K, op.ldb, UB_BK, BN, true));
+    RLU_TRY(map2d_bf16(&b2, op.B2, op.N, op.K, op.ldb, UB_BK, BN, true));
+  }
+  int splits = op.splits < 1 ? 1 : op.splits;
+  const int kchunk = (int)round_up(ceil_div(op.K, splits), UB_BK);
+  splits = (int)ceil_div(op.K, kchunk);
+  Umma3Args a{};
+  a.M = (int)op.M;
+  a.N = (int)op.N;
+  a.K = (int)op.K;
+  a.BN = BN;
+  a.kchunk = kchunk;
+  a.stages = stages;
+  a.status = op.status;
+  if (splits == 1 && op.out) {
+    a.out = op.out;
+    a.ldo = op.ldo;
+    a.out_colmajor = op.out_colmajor;
+  } else {
+    if (!op.partial) return RLU_ENOMEM;
+    a.out = op.partial;
+    a.ldo = op.N;
+    a.out_colmajor = false;
+    a.split_stride = (size_t)op.M * op.N;
+  }
+  auto kern = k_ummab<MODE>;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)ceil_div(op.M, UB_BM), (unsigned)splits, (unsigned)ntiles);
+  kern<<<grid, UB_THREADS, smem, s>>>(mA, b0, b1, b2, a);
+  RLU_TRY(last_launch_status());
+  if (a.out == op.partial && op.out)
+    return splitk_reduce_f32(op.partial, splits, op.M, op.N, op.out, op.ldo, !op.out_colmajor, s);
+  return RLU_OK;
+}
+
+int32_t umma_bf16_gemm(int mode, const UmmaBf16Op& op, cudaStream_t s) {
+  if (mode == UB_MODE_Y) return launch_ub<UB_MODE_Y>(op, s);
+  if (mode == UB_MODE_C3) return launch_ub<UB_MODE_C3>(op, s);
+  return RLU_EINVAL;
+}
+
+int umma_bf16_splits(int64_t M, int64_t K, int64_t N, int bn) {
+  const int64_t tiles = ceil_div(M, UB_BM) * ceil_div(N, bn);
+  int64_t s = (int64_t)sm_count() / (tiles > 0 ? tiles : 1);
+  const int64_t kmax = K / 512 > 1 ? K / 512 : 1;
+  return (int)(s < 1 ? 1 : (s > kmax ? kmax : s));
+}
+
+}  // namespace rlu

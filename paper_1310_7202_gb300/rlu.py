@@ -18,12 +18,13 @@ LIB_PATH = os.path.join(_PKG, "librlu.so")
 
 RLU_OK, RLU_EINVAL, RLU_ENOMEM, RLU_EUNSUPPORTED, RLU_ECUDA = 0, 1, 2, 3, 4
 RLU_F64, RLU_F32, RLU_BF16 = 0, 1, 2
-RLU_PREC_F64, RLU_PREC_F32, RLU_PREC_MIXED = 0, 1, 2
+RLU_PREC_F64, RLU_PREC_F32, RLU_PREC_MIXED, RLU_PREC_BF16 = 0, 1, 2, 3
 
-PREC_BY_NAME = {"f64": RLU_PREC_F64, "f32": RLU_PREC_F32, "mixed": RLU_PREC_MIXED}
+PREC_BY_NAME = {"f64": RLU_PREC_F64, "f32": RLU_PREC_F32, "mixed": RLU_PREC_MIXED,
+                "bf16": RLU_PREC_BF16}
 _DT_OF_TORCH = {torch.float64: RLU_F64, torch.float32: RLU_F32, torch.bfloat16: RLU_BF16}
 _TORCH_OF_PREC = {RLU_PREC_F64: torch.float64, RLU_PREC_F32: torch.float32,
-                  RLU_PREC_MIXED: torch.float32}
+                  RLU_PREC_MIXED: torch.float32, RLU_PREC_BF16: torch.float32}
 
 # Every symbol include/*.h declares.
 EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian",
@@ -211,7 +212,8 @@ class Factorizer:
     def stage_buffers(self) -> dict:
         """Column-/row-major tensors laid out as rlu_stage_outputs expects."""
         m, n, k, l, dt = self.m, self.n, self.k, self.l, self.dtype
-        return {"G": _colmajor(n, l, dt), "Y": _colmajor(m, l, dt), "Ly": _colmajor(m, k, dt),
+        gdt = torch.bfloat16 if self.prec == RLU_PREC_BF16 else dt  # G in the BF16 form
+        return {"G": _colmajor(n, l, gdt), "Y": _colmajor(m, l, dt), "Ly": _colmajor(m, k, dt),
                 "B": torch.empty((k, n), dtype=dt, device="cuda")}
 
 
@@ -220,7 +222,8 @@ def factor(A: torch.Tensor, k: int, l: int, seed: int, prec: int | str | None = 
     """One randomized LU of A (CUDA tensor, row-major). Returns P, Q, L, U, info (device
     tensors) and, with ``stages=True``, the intermediates G, Y, Ly, B."""
     if prec is None:
-        prec = RLU_PREC_F64 if A.dtype == torch.float64 else RLU_PREC_F32
+        prec = {torch.float64: RLU_PREC_F64, torch.bfloat16: RLU_PREC_BF16}.get(A.dtype,
+                                                                               RLU_PREC_F32)
     f = Factorizer(A.shape[0], A.shape[1], k, l, prec)
     st = f.stage_buffers() if stages else None
     P, Q, L, U, info = f(A, seed, stages=st)
