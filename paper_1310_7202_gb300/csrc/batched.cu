@@ -1,0 +1,312 @@
+// Batched form (include/rlu_batch.h): the steps of Algorithm 1 for many independent problems
+// of uneven sizes, each step one launch over the whole batch (per-problem argument records
+// in device memory, entry z = problem z), so the launch count does not grow with the batch
+// and the sequence can be captured in a CUDA graph.
+//
+//   info init, step 1 G (batched Philox/Box-Muller), step 2 Y = A G (batched SIMT GEMM),
+//   step 3 LU(Y) (one thread-block cluster per problem, launches grouped by cluster size),
+//   step 4 L_y and L~, step 5 Gram (FP32 products stored in FP64) -> LDL^T (one CTA per
+//   problem) and C = L~^T A -> blocked triangular solves, step 6 LU(B^T) (clusters), steps
+//   7-8 L_b, U gathers and L = L_y L_b.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "batched.cuh"
+#include "gemm_simt.cuh"
+#include "panel_lu.cuh"
+#include "../../include/rlu_batch.h"
+
+namespace rlu {
+
+namespace {
+
+constexpr int kMaxL = 76;   // one register panel per LU (FP32)
+constexpr int kMaxK = 256;  // one-CTA LDL^T
+constexpr int64_t kMaxRows = 16 * 512;
+
+size_t carve(size_t& cur, size_t bytes) {
+  const size_t at = cur;
+  cur += (size_t)round_up((int64_t)std::max<size_t>(bytes, 1), 256);
+  return at;
+}
+
+struct ProblemLayout {
+  int64_t ldg, ldy, ldl, ldb;
+  int kp;
+  size_t G, Y, Lt, Lp, Mg, dinv, LT, LR, W, WT, C, B, Lb, pos, ps;
+};
+
+struct Tables {
+  size_t info, gauss, gemm_y, lu_y, build, gemm_g, ldl, gemm_c, trsm, lu_b, gather, gemm_l;
+};
+
+bool valid_problem(const rlu_problem& p) {
+  if (!p.A || !p.P || !p.Q || !p.L || !p.U) return false;
+  if (p.m < 1 || p.n < 1 || p.k < 1 || p.k > p.l || p.l > p.m || p.l > p.n) return false;
+  if (p.l > kMaxL || p.k > kMaxK || p.m > kMaxRows || p.n > kMaxRows) return false;
+  if (p.lda < p.n || p.ldl < p.m || p.ldu < p.n) return false;
+  return true;
+}
+
+// Layout of everything: the argument tables first, then each problem's buffers.
+size_t plan_layout(const rlu_problem* probs, int count, Tables& t,
+                   std::vector<ProblemLayout>* lay) {
+  size_t cur = 0;
+  const size_t c = (size_t)count;
+  t.info = carve(cur, c * sizeof(rlu_info*));
+  t.gauss = carve(cur, c * sizeof(GaussJob));
+  t.gemm_y = carve(cur, c * sizeof(GemmArgs));
+  t.lu_y = carve(cur, c * sizeof(LuArgs));
+  t.build = carve(cur, c * sizeof(BuildJob));
+  t.gemm_g = carve(cur, c * sizeof(GemmArgs));
+  t.ldl = carve(cur, c * sizeof(Ldl32Job));
+  t.gemm_c = carve(cur, c * sizeof(GemmArgs));
+  t.trsm = carve(cur, c * sizeof(TrsmJob));
+  t.lu_b = carve(cur, c * sizeof(LuArgs));
+  t.gather = carve(cur, c * sizeof(GatherJob));
+  t.gemm_l = carve(cur, c * sizeof(GemmArgs));
+  for (int i = 0; i < count; ++i) {
+    const rlu_problem& p = probs[i];
+    ProblemLayout L{};
+    L.ldg = round_up(p.n, 4);
+    L.ldy = round_up(p.m, 4);
+    L.ldl = round_up(p.m, 4);
+    L.ldb = round_up(p.n, 4);
+    L.kp = (int)round_up(p.k, 32);
+    const size_t kp = (size_t)L.kp;
+    L.G = carve(cur, (size_t)L.ldg * p.l * 4);
+    L.Y = carve(cur, (size_t)L.ldy * p.l * 4);
+    L.Lt = carve(cur, (size_t)L.ldl * p.k * 4);
+    L.Lp = carve(cur, (size_t)L.ldl * p.k * 4);
+    L.Mg = carve(cur, (size_t)p.k * p.k * 8);
+    L.dinv = carve(cur, (size_t)p.k * 8);
+    L.LT = carve(cur, kp * kp * 4);
+    L.LR = carve(cur, kp * kp * 4);
+    L.W = carve(cur, kp * 32 * 4);
+    L.WT = carve(cur, kp * 32 * 4);
+    L.C = carve(cur, (size_t)p.k * L.ldb * 4);
+    L.B = carve(cur, (size_t)p.k * L.ldb * 4);
+    L.Lb = carve(cur, (size_t)p.k * p.k * 4);
+    L.pos = carve(cur, (size_t)std::max(p.m, p.n) * 4);
+    L.ps = carve(cur, (size_t)p.l * 4);
+    if (lay) lay->push_back(L);
+  }
+  return cur;
+}
+
+__global__ void k_info_init_batched(rlu_info* const* __restrict__ infos, int count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    rlu_info* p = infos[i];
+    if (p) {
+      p->status = RLU_OK;
+      p->first_zero_pivot_y = -1;
+      p->first_zero_pivot_b = -1;
+      p->nonfinite = 0;
+    }
+  }
+}
+
+}  // namespace
+}  // namespace rlu
+
+struct rlu_batch {
+  char* ws = nullptr;
+  int count = 0;
+  int32_t prec = RLU_PREC_F32;
+  rlu::Tables t{};
+  int64_t max_m = 0, max_n = 0;
+  int max_k = 0, max_l = 0, max_kp = 0;
+  int first_y[17] = {}, count_y[17] = {}, first_b[17] = {}, count_b[17] = {};
+  int launches = 0;
+};
+
+extern "C" size_t rlu_batch_workspace_size(const rlu_problem* problems, int32_t count,
+                                           int32_t prec) {
+  using namespace rlu;
+  if (!problems || count < 1 || count > 65535 || prec != RLU_PREC_F32) return 0;
+  for (int i = 0; i < count; ++i)
+    if (!valid_problem(problems[i])) return 0;
+  Tables t{};
+  return plan_layout(problems, count, t, nullptr);
+}
+
+extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, int32_t prec,
+                                    void* workspace, size_t ws_bytes, rlu_batch** out) {
+  using namespace rlu;
+  if (!out || !problems || count < 1 || count > 65535) return RLU_EINVAL;
+  *out = nullptr;
+  if (prec != RLU_PREC_F32) return RLU_EUNSUPPORTED;
+  for (int i = 0; i < count; ++i)
+    if (!valid_problem(problems[i])) return RLU_EINVAL;
+  if (workspace == nullptr || ((uintptr_t)workspace & 255u) != 0) return RLU_EINVAL;
+  Tables t{};
+  std::vector<ProblemLayout> lay;
+  const size_t need = plan_layout(problems, count, t, &lay);
+  if (ws_bytes < need) return RLU_ENOMEM;
+  char* ws = static_cast<char*>(workspace);
+  rlu_batch* b = new rlu_batch();
+  b->ws = ws;
+  b->count = count;
+  b->prec = prec;
+  b->t = t;
+
+  const size_t c = (size_t)count;
+  std::vector<rlu_info*> infos(c);
+  std::vector<GaussJob> gauss(c);
+  std::vector<GemmArgs> gy(c), gg(c), gc(c), gl(c);
+  std::vector<LuArgs> luy_all(c), lub_all(c);
+  std::vector<BuildJob> build(c);
+  std::vector<Ldl32Job> ldl(c);
+  std::vector<TrsmJob> trsm(c);
+  std::vector<GatherJob> gather(c);
+  std::vector<int> gy_of(c), gb_of(c);
+  for (int i = 0; i < count; ++i) {
+    const rlu_problem& p = problems[i];
+    const ProblemLayout& L = lay[(size_t)i];
+    float* G = reinterpret_cast<float*>(ws + L.G);
+    float* Y = reinterpret_cast<float*>(ws + L.Y);
+    float* Lt = reinterpret_cast<float*>(ws + L.Lt);
+    float* Lp = reinterpret_cast<float*>(ws + L.Lp);
+    double* Mg = reinterpret_cast<double*>(ws + L.Mg);
+    float* Cb = reinterpret_cast<float*>(ws + L.C);
+    float* Bb = reinterpret_cast<float*>(ws + L.B);
+    float* Lb = reinterpret_cast<float*>(ws + L.Lb);
+    int32_t* pos = reinterpret_cast<int32_t*>(ws + L.pos);
+    int32_t* ps = reinterpret_cast<int32_t*>(ws + L.ps);
+    LdlOut<float> o{};
+    o.LT = reinterpret_cast<float*>(ws + L.LT);
+    o.LR = reinterpret_cast<float*>(ws + L.LR);
+    o.W = reinterpret_cast<float*>(ws + L.W);
+    o.WT = reinterpret_cast<float*>(ws + L.WT);
+    o.dinv = reinterpret_cast<double*>(ws + L.dinv);
+    o.k = p.k;
+    o.kp = L.kp;
+    infos[(size_t)i] = p.info;
+    gauss[(size_t)i] = GaussJob{p.seed, p.n, p.l, G, L.ldg};
+    GemmArgs a{};
+    a.split_stride = 0;
+    a.alpha_neg = false;
+    // step 2: Y (m x l, column-major) = A (row-major) G (column-major)
+    a.A = p.A; a.lda = p.lda; a.B = G; a.ldb = L.ldg; a.C = Y; a.ldc = L.ldy;
+    a.M = p.m; a.N = p.l; a.K = p.n; a.kchunk = p.n;
+    gy[(size_t)i] = a;
+    // step 5: Gram M (k x k, FP64) = L~^T L~ ; C (k x n, row-major) = L~^T A
+    a.A = Lt; a.lda = L.ldl; a.B = Lt; a.ldb = L.ldl; a.C = Mg; a.ldc = p.k;
+    a.M = p.k; a.N = p.k; a.K = p.m; a.kchunk = p.m;
+    gg[(size_t)i] = a;
+    a.A = Lt; a.lda = L.ldl; a.B = p.A; a.ldb = p.lda; a.C = Cb; a.ldc = L.ldb;
+    a.M = p.k; a.N = p.n; a.K = p.m; a.kchunk = p.m;
+    gc[(size_t)i] = a;
+    // step 7: L (m x k, column-major) = L_y (pivot order) L_b
+    a.A = Lp; a.lda = L.ldl; a.B = Lb; a.ldb = p.k; a.C = p.L; a.ldc = p.ldl;
+    a.M = p.m; a.N = p.k; a.K = p.k; a.kchunk = p.k;
+    gl[(size_t)i] = a;
+    LuArgs u{};
+    u.X = Y; u.ldx = L.ldy; u.R = (int)p.m; u.C = p.l; u.perm = p.P;
+    u.zero_step = p.info ? &p.info->first_zero_pivot_y : nullptr;
+    u.nonfinite = p.info ? &p.info->nonfinite : nullptr;
+    u.status = p.info ? &p.info->status : nullptr;
+    u.posg = pos; u.psg = ps; u.p0 = 0; u.pw = p.l; u.rpc = 512; u.nb = kMaxL;
+    luy_all[(size_t)i] = u;
+    u.X = Bb; u.ldx = L.ldb; u.R = (int)p.n; u.C = p.k; u.perm = p.Q;
+    u.zero_step = p.info ? &p.info->first_zero_pivot_b : nullptr;
+    u.pw = p.k;
+    lub_all[(size_t)i] = u;
+    gy_of[(size_t)i] = (int)ceil_div(p.m, 512);
+    gb_of[(size_t)i] = (int)ceil_div(p.n, 512);
+    build[(size_t)i] = BuildJob{Y, L.ldy, p.m, p.k, p.P, Lt, Lp, L.ldl};
+    ldl[(size_t)i] = Ldl32Job{Mg, p.k, o, p.info ? &p.info->status : nullptr};
+    trsm[(size_t)i] = TrsmJob{o, Cb, L.ldb, p.n, Bb, L.ldb};
+    gather[(size_t)i] = GatherJob{Bb, L.ldb, p.Q, p.k, p.n, Lb, static_cast<float*>(p.U), p.ldu};
+    b->max_m = std::max(b->max_m, p.m);
+    b->max_n = std::max(b->max_n, p.n);
+    b->max_k = std::max(b->max_k, p.k);
+    b->max_l = std::max(b->max_l, p.l);
+    b->max_kp = std::max(b->max_kp, L.kp);
+  }
+  // LU records grouped by cluster size
+  auto group = [&](const std::vector<LuArgs>& all, const std::vector<int>& gof, int* first,
+                   int* cnt, std::vector<LuArgs>& sorted) {
+    for (int g = 0; g <= 16; ++g) cnt[g] = 0;
+    for (int v : gof) ++cnt[v];
+    int acc = 0;
+    for (int g = 0; g <= 16; ++g) {
+      first[g] = acc;
+      acc += cnt[g];
+    }
+    std::vector<int> fill(first, first + 17);
+    sorted.resize(all.size());
+    for (size_t i = 0; i < all.size(); ++i) sorted[(size_t)fill[gof[i]]++] = all[i];
+  };
+  std::vector<LuArgs> luy, lub;
+  group(luy_all, gy_of, b->first_y, b->count_y, luy);
+  group(lub_all, gb_of, b->first_b, b->count_b, lub);
+
+  auto up = [&](size_t off, const void* src, size_t bytes) -> int32_t {
+    RLU_CUDA_TRY(cudaMemcpy(ws + off, src, bytes, cudaMemcpyHostToDevice));
+    return RLU_OK;
+  };
+  int32_t st = RLU_OK;
+  if (st == RLU_OK) st = up(t.info, infos.data(), c * sizeof(rlu_info*));
+  if (st == RLU_OK) st = up(t.gauss, gauss.data(), c * sizeof(GaussJob));
+  if (st == RLU_OK) st = up(t.gemm_y, gy.data(), c * sizeof(GemmArgs));
+  if (st == RLU_OK) st = up(t.lu_y, luy.data(), c * sizeof(LuArgs));
+  if (st == RLU_OK) st = up(t.build, build.data(), c * sizeof(BuildJob));
+  if (st == RLU_OK) st = up(t.gemm_g, gg.data(), c * sizeof(GemmArgs));
+  if (st == RLU_OK) st = up(t.ldl, ldl.data(), c * sizeof(Ldl32Job));
+  if (st == RLU_OK) st = up(t.gemm_c, gc.data(), c * sizeof(GemmArgs));
+  if (st == RLU_OK) st = up(t.trsm, trsm.data(), c * sizeof(TrsmJob));
+  if (st == RLU_OK) st = up(t.lu_b, lub.data(), c * sizeof(LuArgs));
+  if (st == RLU_OK) st = up(t.gather, gather.data(), c * sizeof(GatherJob));
+  if (st == RLU_OK) st = up(t.gemm_l, gl.data(), c * sizeof(GemmArgs));
+  if (st != RLU_OK) {
+    delete b;
+    return st;
+  }
+  int groups = 0;
+  for (int g = 1; g <= 16; ++g) groups += (b->count_y[g] > 0) + (b->count_b[g] > 0);
+  b->launches = 10 + groups;
+  *out = b;
+  return RLU_OK;
+}
+
+extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
+  using namespace rlu;
+  if (!b) return RLU_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = b->ws;
+  const Tables& t = b->t;
+  const int c = b->count;
+  k_info_init_batched<<<(unsigned)ceil_div(c, 256), 256, 0, s>>>(
+      reinterpret_cast<rlu_info* const*>(ws + t.info), c);
+  RLU_TRY(last_launch_status());
+  RLU_TRY(launch_gaussian_batched(reinterpret_cast<const GaussJob*>(ws + t.gauss), c, s));
+  RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_y), c,
+                                           b->max_m, b->max_l, true, true, false, s)));
+  RLU_TRY(launch_lu_reg_batched(false, reinterpret_cast<const LuArgs*>(ws + t.lu_y), b->first_y,
+                                b->count_y, s));
+  RLU_TRY(build_ly_batched(reinterpret_cast<const BuildJob*>(ws + t.build), c, b->max_m,
+                           b->max_k, s));
+  RLU_TRY((gemm_simt_batched<float, double>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_g), c,
+                                            b->max_k, b->max_k, true, true, true, s)));
+  RLU_TRY(ldl32_batched(reinterpret_cast<const Ldl32Job*>(ws + t.ldl), c, b->max_k, s));
+  RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_c), c,
+                                           b->max_k, b->max_n, true, false, true, s)));
+  RLU_TRY(trsm_batched(reinterpret_cast<const TrsmJob*>(ws + t.trsm), c, b->max_kp, b->max_n, s));
+  RLU_TRY(launch_lu_reg_batched(true, reinterpret_cast<const LuArgs*>(ws + t.lu_b), b->first_b,
+                                b->count_b, s));
+  RLU_TRY(gather_batched(reinterpret_cast<const GatherJob*>(ws + t.gather), c, b->max_k,
+                         b->max_n, s));
+  RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_l), c,
+                                           b->max_m, b->max_k, false, true, false, s)));
+  return RLU_OK;
+}
+
+extern "C" int32_t rlu_batch_launches(const rlu_batch* b) { return b ? b->launches : 0; }
+
+extern "C" int32_t rlu_batch_destroy(rlu_batch* b) {
+  if (!b) return RLU_EINVAL;
+  delete b;
+  return RLU_OK;
+}

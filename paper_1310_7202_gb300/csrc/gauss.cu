@@ -13,6 +13,7 @@
 // FP64 transform per pair would cost ~90 FP64 instructions, which GB300 runs at a small
 // fraction of its FP32 rate).
 #include "common.cuh"
+#include "batched.cuh"
 
 namespace rlu {
 
@@ -239,6 +240,34 @@ __global__ void k_gauss32(uint64_t seed, uint32_t stream_id, int64_t n, int64_t 
       if (e < total) store_g<OutT>(G, ldg, n, e, z[t]);
     }
   }
+}
+
+// Batched FP32 G: problem blockIdx.y of the table, its own seed and sizes.
+__global__ void k_gauss32_batched(const GaussJob* __restrict__ jobs, SeriesCoefs C) {
+  const GaussJob j = jobs[blockIdx.y];
+  const uint32_t k0 = (uint32_t)j.seed, k1 = (uint32_t)(j.seed >> 32);
+  const int64_t total = j.n * j.l, nc = (total + 3) / 4;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 w = philox10(make_uint4((uint32_t)c, (uint32_t)((uint64_t)c >> 32), 0u, 0u), k0,
+                             k1);
+    float z[4];
+    box_muller32(w.x, w.y, C, z[0], z[1]);
+    box_muller32(w.z, w.w, C, z[2], z[3]);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int64_t e = 4 * c + t;
+      if (e < total) j.G[(e / j.n) * j.ldg + (e % j.n)] = z[t];
+    }
+  }
+}
+
+int32_t launch_gaussian_batched(const GaussJob* jobs_dev, int count, cudaStream_t s) {
+  if (count <= 0) return RLU_OK;
+  if (count > 65535) return RLU_EINVAL;
+  static const SeriesCoefs C = make_coefs();
+  k_gauss32_batched<<<dim3(8, (unsigned)count), 256, 0, s>>>(jobs_dev, C);
+  return last_launch_status();
 }
 
 static int grid_for(int64_t work, int threads) {

@@ -27,8 +27,10 @@ template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; };
 template <> struct Vec<double> { using type = double2; };
 
-template <typename T, bool AK, bool BKM, bool CR>
-__global__ void __launch_bounds__(256) k_gemm_simt(GemmArgs p) {
+// One BM x BN output tile (bx, by) of K range slice bz; the output element type OutT may be
+// wider than T (the batched Gram matrix is stored in FP64 for the LDL^T).
+template <typename T, typename OutT, bool AK, bool BKM, bool CR>
+__device__ __forceinline__ void gemm_tile(const GemmArgs& p, int bx, int by, int bz) {
   using Cfg = GemmCfg<T>;
   constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, V = Cfg::V;
   constexpr int NT = Cfg::TX * Cfg::TY;
@@ -43,8 +45,8 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmArgs p) {
   const T* __restrict__ Bm = static_cast<const T*>(p.B);
   const int tid = threadIdx.x;
   const int tx = tid % Cfg::TX, ty = tid / Cfg::TX;
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
-  const int64_t kbeg = (int64_t)blockIdx.z * p.kchunk;
+  const int64_t m0 = (int64_t)by * BM, n0 = (int64_t)bx * BN;
+  const int64_t kbeg = (int64_t)bz * p.kchunk;
   const int64_t kend = (kbeg + p.kchunk < p.K) ? kbeg + p.kchunk : p.K;
 
   T acc[2 * V][2 * V];
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmArgs p) {
     buf ^= 1;
   }
 
-  T* __restrict__ Cm = static_cast<T*>(p.C) + (int64_t)blockIdx.z * p.split_stride;
+  OutT* __restrict__ Cm = static_cast<OutT*>(p.C) + (int64_t)bz * p.split_stride;
 #pragma unroll
   for (int i = 0; i < 2 * V; ++i) {
     const int64_t gm = m0 + (i < V ? ty * V + i : BM / 2 + ty * V + (i - V));
@@ -128,13 +130,28 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmArgs p) {
     for (int j = 0; j < 2 * V; ++j) {
       const int64_t gn = n0 + (j < V ? tx * V + j : BN / 2 + tx * V + (j - V));
       if (gn >= p.N) continue;
-      const T v = p.alpha_neg ? -acc[i][j] : acc[i][j];
+      const OutT v = (OutT)(p.alpha_neg ? -acc[i][j] : acc[i][j]);
       if (CR)
         Cm[gm * p.ldc + gn] = v;
       else
         Cm[gn * p.ldc + gm] = v;
     }
   }
+}
+
+template <typename T, bool AK, bool BKM, bool CR>
+__global__ void __launch_bounds__(256) k_gemm_simt(GemmArgs p) {
+  gemm_tile<T, T, AK, BKM, CR>(p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched form: problem blockIdx.z of the table, whole K range (no split); CTAs past the
+// problem's own tile counts return at once.
+template <typename T, typename OutT, bool AK, bool BKM, bool CR>
+__global__ void __launch_bounds__(256) k_gemm_simt_batched(const GemmArgs* __restrict__ table) {
+  using Cfg = GemmCfg<T>;
+  const GemmArgs p = table[blockIdx.z];
+  if ((int64_t)blockIdx.y * Cfg::BM >= p.M || (int64_t)blockIdx.x * Cfg::BN >= p.N) return;
+  gemm_tile<T, OutT, AK, BKM, CR>(p, blockIdx.x, blockIdx.y, 0);
 }
 
 // out(i, j) = sum_z part[z][i][j], z ascending; accumulation and output in OutT.
@@ -173,6 +190,35 @@ static void launch_variant(const GemmArgs& a, bool AK, bool BKM, bool CR, dim3 g
   RLU_GEMM_CASE(false, false, false)
 #undef RLU_GEMM_CASE
 }
+
+template <typename T, typename OutT>
+int32_t gemm_simt_batched(const GemmArgs* table_dev, int count, int64_t max_m, int64_t max_n,
+                          bool a_kmajor, bool b_kmajor, bool c_rowmajor, cudaStream_t s) {
+  using Cfg = GemmCfg<T>;
+  if (count <= 0) return RLU_OK;
+  if (count > 65535) return RLU_EINVAL;
+  const dim3 grid((unsigned)ceil_div(max_n, Cfg::BN), (unsigned)ceil_div(max_m, Cfg::BM),
+                  (unsigned)count);
+#define RLU_GEMM_BCASE(x, y, z)                                                        \
+  if (a_kmajor == x && b_kmajor == y && c_rowmajor == z) {                             \
+    k_gemm_simt_batched<T, OutT, x, y, z><<<grid, 256, 0, s>>>(table_dev);             \
+    return last_launch_status();                                                       \
+  }
+  RLU_GEMM_BCASE(true, true, true)
+  RLU_GEMM_BCASE(true, true, false)
+  RLU_GEMM_BCASE(true, false, true)
+  RLU_GEMM_BCASE(true, false, false)
+  RLU_GEMM_BCASE(false, true, true)
+  RLU_GEMM_BCASE(false, true, false)
+  RLU_GEMM_BCASE(false, false, true)
+  RLU_GEMM_BCASE(false, false, false)
+#undef RLU_GEMM_BCASE
+  return RLU_EINVAL;
+}
+template int32_t gemm_simt_batched<float, float>(const GemmArgs*, int, int64_t, int64_t, bool,
+                                                 bool, bool, cudaStream_t);
+template int32_t gemm_simt_batched<float, double>(const GemmArgs*, int, int64_t, int64_t, bool,
+                                                  bool, bool, cudaStream_t);
 
 template <typename T>
 size_t gemm_partial_bytes(int64_t M, int64_t N, int splits) {

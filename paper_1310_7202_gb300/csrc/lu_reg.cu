@@ -165,7 +165,7 @@ struct LrShared {
 };
 
 template <typename T, bool CROUT, int RT, int NB, int NT>
-__global__ void __launch_bounds__(NT, 1) k_lu_reg(LuArgs a) {
+__device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
   constexpr int NW = NT / 32;
   cg::cluster_group cl = cg::this_cluster();
   const int ncta = (int)cl.num_blocks();
@@ -474,6 +474,18 @@ __global__ void __launch_bounds__(NT, 1) k_lu_reg(LuArgs a) {
   cl.sync();
 }
 
+template <typename T, bool CROUT, int RT, int NB, int NT>
+__global__ void __launch_bounds__(NT, 1) k_lu_reg(LuArgs a) {
+  lu_reg_body<T, CROUT, RT, NB, NT>(a);
+}
+
+// Batched form: cluster c of the launch factors problem table[c] (one panel: pw = C).
+template <typename T, bool CROUT, int RT, int NB, int NT>
+__global__ void __launch_bounds__(NT, 1) k_lu_reg_batched(const LuArgs* __restrict__ table) {
+  const int csize = (int)cg::this_cluster().num_blocks();
+  lu_reg_body<T, CROUT, RT, NB, NT>(table[blockIdx.x / csize]);
+}
+
 // Rank-w update of the trailing columns [c_begin, C) of every row whose position is at
 // least p0 + w: X[r][c] -= sum_s X[r][p0+s] * U12[s][c], U12 = the panel's pivot rows
 // (already solved by the panel launch). One thread per row, 32 columns per CTA.
@@ -597,6 +609,42 @@ int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s
   *launched = false;
   if (dtype == RLU_F64) return crout ? launch_reg_t<double, true>(a, s, launched) : launch_reg_t<double, false>(a, s, launched);
   if (dtype == RLU_F32) return crout ? launch_reg_t<float, true>(a, s, launched) : launch_reg_t<float, false>(a, s, launched);
+  return RLU_OK;
+}
+
+// Batched LUs of problems that fit one register panel (C <= NB - 1 = 76 FP32 columns, R <=
+// 16 x 512 rows): the table on the device is grouped by cluster size (ceil(R / 512) CTAs);
+// group g starts at table entry first[g] and holds count[g] problems.
+int32_t launch_lu_reg_batched(bool crout, const LuArgs* table_dev, const int* first,
+                              const int* count, cudaStream_t s) {
+  using T = float;
+  constexpr int NB = 77, NT = 512;
+  int dev = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  int optin = 0;
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t bytes = lr_smem_bytes<T, NB, NT>(NT, 0);
+  if (bytes > (size_t)optin) return RLU_EUNSUPPORTED;
+  for (int g = 1; g <= 16; ++g) {
+    if (count[g] == 0) continue;
+    auto kern = crout ? k_lu_reg_batched<T, true, 1, NB, NT> : k_lu_reg_batched<T, false, 1, NB, NT>;
+    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = g;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(g * count[g]));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, table_dev + first[g]));
+    RLU_TRY(last_launch_status());
+  }
   return RLU_OK;
 }
 

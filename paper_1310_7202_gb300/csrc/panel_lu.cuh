@@ -28,4 +28,11 @@ int32_t launch_cluster_lu(int32_t dtype, bool crout, const LuArgs& a, cudaStream
 // Register-resident variant (lu_reg.cu); *launched is false when the shape does not fit it.
 int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s, bool* launched);
 
+// Batched FP32 LUs of single-panel problems (C <= 76, R <= 8192), one cluster each; the
+// device table is grouped by cluster size g = ceil(R / 512) (entries first[g] ..
+// first[g] + count[g] - 1; first and count are host arrays of 17 entries). Each entry
+// carries rpc = 512, p0 = 0, pw = C and its own position state (posg, psg).
+int32_t launch_lu_reg_batched(bool crout, const LuArgs* table_dev, const int* first,
+                              const int* count, cudaStream_t s);
+
 }  // namespace rlu

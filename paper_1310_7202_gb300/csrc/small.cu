@@ -14,10 +14,13 @@
 //    B^T with the column permutation Q.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include <utility>
 
 #include "common.cuh"
 #include "small.cuh"
+#include "batched.cuh"
 
 namespace rlu {
 
@@ -297,8 +300,8 @@ __device__ __forceinline__ void ldl_cols(float (&a)[LB], int lane, float* d_out,
   (ldl_col<ts>(a, lane, d_out, bad), ...);
 }
 
-__global__ void __launch_bounds__(L32_NT, 1) k_ldl32(const double* __restrict__ M, int k,
-                                                    LdlOut<float> o, int32_t* __restrict__ status) {
+__device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
+                                           const LdlOut<float>& o, int32_t* __restrict__ status) {
   extern __shared__ __align__(16) float l32_smem[];
   const int nb = (k + LB - 1) / LB;
   const int nblk = nb * (nb + 1) / 2;
@@ -438,6 +441,17 @@ __global__ void __launch_bounds__(L32_NT, 1) k_ldl32(const double* __restrict__ 
   if (tid == 0 && s_bad && status) *status = RLU_EINVAL;
 }
 
+__global__ void __launch_bounds__(L32_NT, 1) k_ldl32(const double* __restrict__ M, int k,
+                                                    LdlOut<float> o, int32_t* __restrict__ status) {
+  ldl32_body(M, k, o, status);
+}
+
+// Batched form: problem blockIdx.x of the table.
+__global__ void __launch_bounds__(L32_NT, 1) k_ldl32_batched(const Ldl32Job* __restrict__ jobs) {
+  const Ldl32Job& j = jobs[blockIdx.x];
+  ldl32_body(j.M, j.k, j.o, j.status);
+}
+
 static size_t ldl32_smem_bytes(int k) {
   const int nb = (k + LB - 1) / LB;
   return sizeof(float) * ((size_t)(nb * (nb + 1) / 2 + 2 * nb) * LB * LBP + (size_t)nb * LB);
@@ -549,9 +563,8 @@ __device__ __forceinline__ const T* trsm_block_src(const LdlOut<T>& o, int nb, i
 }
 
 template <typename T, int TC>
-__global__ void __launch_bounds__(TB / 2 * TC / 4) k_trsm_ldl(LdlOut<T> o, const T* __restrict__ C,
-                                                             int64_t ldc, int64_t n,
-                                                             T* __restrict__ B, int64_t ldb) {
+__device__ __forceinline__ void trsm_body(const LdlOut<T>& o, const T* __restrict__ C, int64_t ldc,
+                                          int64_t n, T* __restrict__ B, int64_t ldb, int bx) {
   // two thread groups split the 32 rows of each staged block (the reduction index) in
   // halves; their partial sums meet in the diagonal step, where every thread owns 2 x 4
   constexpr int NG = TB / 4 * TC / 4;  // threads of one group
@@ -565,7 +578,7 @@ __global__ void __launch_bounds__(TB / 2 * TC / 4) k_trsm_ldl(LdlOut<T> o, const
   T* Ws = Ls + (size_t)TSTAGES * TB * LSP;  // [2][TB][TC] the groups' partial sums
   const int tid = threadIdx.x;
   const int g = tid / NG, gt = tid % NG;
-  const int64_t c0 = (int64_t)blockIdx.x * TC;
+  const int64_t c0 = (int64_t)bx * TC;
   const int nseq = nb * (nb + 1);
   auto issue = [&](int sidx) {
     if (sidx < nseq) {
@@ -670,6 +683,20 @@ __global__ void __launch_bounds__(TB / 2 * TC / 4) k_trsm_ldl(LdlOut<T> o, const
     const int i = e / TC, c = e % TC;
     if (c0 + c < n) B[(int64_t)i * ldb + c0 + c] = Xs[e];
   }
+}
+
+template <typename T, int TC>
+__global__ void __launch_bounds__(TB / 2 * TC / 4) k_trsm_ldl(LdlOut<T> o, const T* __restrict__ C,
+                                                             int64_t ldc, int64_t n,
+                                                             T* __restrict__ B, int64_t ldb) {
+  trsm_body<T, TC>(o, C, ldc, n, B, ldb, blockIdx.x);
+}
+
+// Batched form: problem blockIdx.y, column block blockIdx.x (CTAs past its n return).
+__global__ void __launch_bounds__(TB / 2 * 64 / 4) k_trsm_batched(const TrsmJob* __restrict__ jobs) {
+  const TrsmJob& j = jobs[blockIdx.y];
+  if ((int64_t)blockIdx.x * 64 >= j.n) return;
+  trsm_body<float, 64>(j.o, j.C, j.ldc, j.n, j.B, j.ldb, blockIdx.x);
 }
 
 template <typename T>
@@ -783,6 +810,74 @@ __global__ void k_info_init(rlu_info* info) {
 
 int32_t info_init(rlu_info* info, cudaStream_t s) {
   k_info_init<<<1, 1, 0, s>>>(info);
+  return last_launch_status();
+}
+
+// ---- batched launchers --------------------------------------------------------------------
+__global__ void k_build_ly_batched(const BuildJob* __restrict__ jobs) {
+  const BuildJob j = jobs[blockIdx.z];
+  const int c = blockIdx.y;
+  if (c >= j.k) return;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < j.m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = j.perm[p];
+    const float v = (c < p) ? j.Y[(int64_t)c * j.ldy + r] : (c == p ? 1.f : 0.f);
+    j.Lp[(int64_t)c * j.ldl + p] = v;
+    j.Lt[(int64_t)c * j.ldl + r] = v;
+  }
+}
+
+int32_t build_ly_batched(const BuildJob* jobs_dev, int count, int64_t max_m, int max_k,
+                         cudaStream_t s) {
+  if (count <= 0) return RLU_OK;
+  const unsigned bx = (unsigned)std::min<int64_t>(ceil_div(max_m, 256), 8);
+  k_build_ly_batched<<<dim3(bx, (unsigned)max_k, (unsigned)count), 256, 0, s>>>(jobs_dev);
+  return last_launch_status();
+}
+
+int32_t ldl32_batched(const Ldl32Job* jobs_dev, int count, int max_k, cudaStream_t s) {
+  if (count <= 0) return RLU_OK;
+  if (max_k > L32_MAXB * LB) return RLU_EUNSUPPORTED;
+  const size_t bytes = ldl32_smem_bytes(max_k);
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_ldl32_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes));
+  k_ldl32_batched<<<(unsigned)count, L32_NT, bytes, s>>>(jobs_dev);
+  return last_launch_status();
+}
+
+int32_t trsm_batched(const TrsmJob* jobs_dev, int count, int max_kp, int64_t max_n,
+                     cudaStream_t s) {
+  if (count <= 0) return RLU_OK;
+  const size_t bytes = trsm_smem_bytes<float>(max_kp, 64);
+  int dev = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  int optin = 0;
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (bytes > (size_t)optin) return RLU_EUNSUPPORTED;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_trsm_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes));
+  k_trsm_batched<<<dim3((unsigned)ceil_div(max_n, 64), (unsigned)count), TB / 2 * 64 / 4, bytes,
+                   s>>>(jobs_dev);
+  return last_launch_status();
+}
+
+__global__ void k_gather_batched(const GatherJob* __restrict__ jobs) {
+  const GatherJob j = jobs[blockIdx.z];
+  const int i = blockIdx.y;  // row of U / column of L_b
+  if (i >= j.k) return;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < j.n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    j.U[(int64_t)i * j.ldu + c] = c >= i ? j.B[(int64_t)i * j.ldb + j.Q[c]] : 0.f;
+  // L_b column i: rows r > i from B's row r at the pivot column Q[i]
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < j.k; r += gridDim.x * blockDim.x)
+    j.Lb[(int64_t)i * j.k + r] = r > i ? j.B[(int64_t)r * j.ldb + j.Q[i]] : (r == i ? 1.f : 0.f);
+}
+
+int32_t gather_batched(const GatherJob* jobs_dev, int count, int max_k, int64_t max_n,
+                       cudaStream_t s) {
+  if (count <= 0) return RLU_OK;
+  const unsigned bx = (unsigned)std::min<int64_t>(ceil_div(max_n, 256), 8);
+  k_gather_batched<<<dim3(bx, (unsigned)max_k, (unsigned)count), 256, 0, s>>>(jobs_dev);
   return last_launch_status();
 }
 

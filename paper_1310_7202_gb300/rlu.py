@@ -1,5 +1,5 @@
-"""Python binding of the C ABI in include/rlu.h and include/rlu_server.h (ctypes; argument
-marshalling only).
+"""Python binding of the C ABI in include/rlu.h, include/rlu_server.h and include/rlu_batch.h
+(ctypes; argument marshalling only).
 
 Every computation runs in librlu.so's CUDA kernels. PyTorch only provides device memory
 (the tensors passed in and the outputs allocated here) and the current CUDA stream.
@@ -31,7 +31,9 @@ EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian"
             "rlu_workspace_size", "rlu_factor", "rlu_factor_stages", "rlu_timed_step_name",
             "rlu_launch_count", "rlu_reconstruct_workspace_size", "rlu_reconstruct_error",
             "rlu_reconstruct_error_static", "rlu_server_create", "rlu_server_submit",
-            "rlu_server_poll", "rlu_server_wait_all", "rlu_server_stats", "rlu_server_destroy")
+            "rlu_server_poll", "rlu_server_wait_all", "rlu_server_stats", "rlu_server_destroy",
+            "rlu_batch_workspace_size", "rlu_batch_create", "rlu_factor_batched",
+            "rlu_batch_launches", "rlu_batch_destroy")
 
 RLU_REQ_QUEUED, RLU_REQ_RUNNING, RLU_REQ_DONE, RLU_REQ_FAILED = 0, 1, 2, 3
 
@@ -47,6 +49,14 @@ class _Request(ctypes.Structure):
                 ("P", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("L", ctypes.c_void_p),
                 ("ldl", ctypes.c_int64), ("U", ctypes.c_void_p), ("ldu", ctypes.c_int64),
                 ("info", ctypes.c_void_p)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("P", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("L", ctypes.c_void_p), ("ldl", ctypes.c_int64), ("U", ctypes.c_void_p),
+                ("ldu", ctypes.c_int64), ("info", ctypes.c_void_p)]
 
 
 class _StageOutputs(ctypes.Structure):
@@ -113,6 +123,17 @@ def load_library(require_cuda: bool = True) -> ctypes.CDLL:
     lib.rlu_server_stats.argtypes = [vp, ctypes.POINTER(i64)]
     lib.rlu_server_destroy.restype = i32
     lib.rlu_server_destroy.argtypes = [vp]
+    lib.rlu_batch_workspace_size.restype = sz
+    lib.rlu_batch_workspace_size.argtypes = [ctypes.POINTER(_Problem), i32, i32]
+    lib.rlu_batch_create.restype = i32
+    lib.rlu_batch_create.argtypes = [ctypes.POINTER(_Problem), i32, i32, vp, sz,
+                                     ctypes.POINTER(vp)]
+    lib.rlu_factor_batched.restype = i32
+    lib.rlu_factor_batched.argtypes = [vp, vp]
+    lib.rlu_batch_launches.restype = i32
+    lib.rlu_batch_launches.argtypes = [vp]
+    lib.rlu_batch_destroy.restype = i32
+    lib.rlu_batch_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -354,6 +375,61 @@ class Server:
     def close(self) -> None:
         if self.h:
             _check(self.lib.rlu_server_destroy(self.h), "rlu_server_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """The batched form of include/rlu_batch.h: one plan for many problems of uneven sizes
+    (dicts with A, a row-major FP32 CUDA tensor, and k, l, seed); run() enqueues the whole
+    batch (a fixed number of launches), which can be captured in a CUDA graph."""
+
+    def __init__(self, problems: list[dict], prec: int | str = RLU_PREC_F32):
+        self.lib = load_library()
+        self.prec = PREC_BY_NAME[prec] if isinstance(prec, str) else int(prec)
+        self.outs = []
+        arr = (_Problem * len(problems))()
+        for i, p in enumerate(problems):
+            A = p["A"]
+            m, n = A.shape
+            k, l = p["k"], p["l"]
+            if A.dtype != torch.float32 or A.stride(1) != 1 or A.device.type != "cuda":
+                raise RluError("batched problems take row-major FP32 CUDA tensors")
+            o = {"P": torch.empty(m, dtype=torch.int32, device="cuda"),
+                 "Q": torch.empty(n, dtype=torch.int32, device="cuda"),
+                 "L": _colmajor(m, k, torch.float32),
+                 "U": torch.empty((k, n), dtype=torch.float32, device="cuda"),
+                 "info": torch.empty(4, dtype=torch.int32, device="cuda")}
+            self.outs.append(o)
+            arr[i] = _Problem(_dev_ptr(A), m, n, A.stride(0), k, l, p["seed"], _dev_ptr(o["P"]),
+                              _dev_ptr(o["Q"]), _dev_ptr(o["L"]), o["L"].stride(1),
+                              _dev_ptr(o["U"]), o["U"].stride(0), _dev_ptr(o["info"]))
+        self._problems = problems  # keep the inputs alive
+        ws = self.lib.rlu_batch_workspace_size(arr, len(problems), self.prec)
+        if ws == 0:
+            raise RluError("a problem does not fit the batched form (see rlu_batch.h)")
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        h = ctypes.c_void_p()
+        _check(self.lib.rlu_batch_create(arr, len(problems), self.prec,
+                                         _dev_ptr(self.workspace), ws, ctypes.byref(h)),
+               "rlu_batch_create")
+        self.h = h
+
+    def run(self, stream=None) -> None:
+        _check(self.lib.rlu_factor_batched(self.h, _stream_ptr(stream)), "rlu_factor_batched")
+
+    def launches(self) -> int:
+        return int(self.lib.rlu_batch_launches(self.h))
+
+    def close(self) -> None:
+        if self.h:
+            _check(self.lib.rlu_batch_destroy(self.h), "rlu_batch_destroy")
             self.h = None
 
     def __del__(self):

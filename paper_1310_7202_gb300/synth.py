@@ -105,4 +105,24 @@ WORKLOADS = {
                       seed_u=21, seed_v=22, seed_g=2),
     "bf16_32768x16384": dict(m=32768, n=16384, k=512, l=532, spectrum="geometric_099",
                              dtype="bf16", seed_u=31, seed_v=32, seed_g=3),
+    # batched form: 4096 problems, sizes from batch_shapes, sigma_i = exp(-i/k), FP32
+    "batch4096": dict(kind="batch", count=4096, spectrum="exp_k", dtype="f32", seed_shapes=4,
+                      seed_u=41, seed_g=5000),
 }
+
+
+def batch_shapes(count: int, seed: int, max_m: int = 2048, max_n: int = 1024):
+    """Problem sizes of the batched workload: m log-uniform in [64, max_m], n log-uniform in
+    [64, max_n] and at most m, k uniform in {8..64}, l = k + 10; k is drawn again while
+    l > n (the sizes must satisfy k <= l <= min(m, n))."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(np.exp(rng.uniform(np.log(64), np.log(max_m))))
+        n = min(int(np.exp(rng.uniform(np.log(64), np.log(max_n)))), m)
+        while True:
+            k = int(rng.integers(8, 65))
+            if k + 10 <= n:
+                break
+        out.append((m, n, k, k + 10))
+    return out

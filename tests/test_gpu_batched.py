@@ -1,0 +1,80 @@
+"""Batched form (include/rlu_batch.h): many uneven FP32 problems per launch sequence. Each
+problem is checked against the FP64 oracle (same FP32 Gaussian, tolerance 1.1x the oracle's
+||PAQ - LU||_F plus 1e-4 ||A||_2) and against the single-problem path; a CUDA-graph replay
+of the batch reproduces the direct launch bit for bit. GPU only."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1310_7202_gb300 import rlu, synth
+from tests.gpu_helpers import leading_agreement
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def batch():
+    shapes = synth.batch_shapes(40, seed=3, max_m=768, max_n=512)
+    probs, mats = [], []
+    for i, (m, n, k, l) in enumerate(shapes):
+        sigma = np.exp(-np.arange(1, min(m, n) + 1) / k)
+        A = synth.prescribed_matrix(m, n, sigma, 100 + i, 200 + i, dtype=np.float32)
+        mats.append((A, sigma))
+        probs.append({"A": torch.from_numpy(A).cuda(), "k": k, "l": l, "seed": 1000 + i})
+    b = rlu.Batch(probs, "f32")
+    b.run()
+    torch.cuda.synchronize()
+    res = [{key: v.clone() for key, v in o.items()} for o in b.outs]
+    return shapes, mats, probs, b, res
+
+
+def test_batched_against_oracle(batch):
+    shapes, mats, probs, b, res = batch
+    for (m, n, k, l), (A, sigma), p, r in zip(shapes, mats, probs, res):
+        G = O.gaussian_f32(p["seed"], 0, n, l).astype(np.float64)
+        o = O.rlu_factor(A.astype(np.float64), k, l, seed=p["seed"], G=G)
+        fro_o, _ = O.reconstruct_error(A, o["P"], o["Q"], o["L"], o["U"], spectral=False)
+        P, Q, L, U = (r[x].cpu().numpy() for x in ("P", "Q", "L", "U"))
+        fro_g, _ = O.reconstruct_error(A, P, Q, L, U, spectral=False)
+        assert fro_g <= 1.1 * fro_o + 1e-4 * sigma[0], (m, n, k, fro_g, fro_o)
+        assert sorted(P.tolist()) == list(range(m)) and sorted(Q.tolist()) == list(range(n))
+        assert leading_agreement(P, o["P"], l) >= min(5, l), (m, n, k)
+        assert r["info"].tolist()[:3] == [0, -1, -1]
+
+
+def test_batched_matches_single_problem_path(batch):
+    shapes, mats, probs, b, res = batch
+    for (m, n, k, l), (A, sigma), p, r in zip(shapes, mats, probs, res):
+        s = rlu.factor(p["A"], k, l, p["seed"], "f32")
+        fro_s, _ = rlu.reconstruct_error(p["A"], s["P"], s["Q"], s["L"], s["U"])
+        fro_b, _ = rlu.reconstruct_error(p["A"], r["P"], r["Q"], r["L"], r["U"])
+        assert abs(fro_b.item() - fro_s.item()) <= 0.05 * fro_s.item() + 1e-6, (m, n, k)
+
+
+def test_graph_replay_reproduces_batch(batch):
+    shapes, mats, probs, b, res = batch
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run()  # warm-up outside the capture (kernel attributes are set here)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        b.run()
+    for o in b.outs:
+        for t in o.values():
+            t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(b.outs, res):
+        for key in ("P", "Q", "L", "U", "info"):
+            assert torch.equal(o[key], r[key]), key
+    assert b.launches() <= 10 + 2 * 16
+
+
+def test_batched_rejects_problems_outside_the_form():
+    A = torch.zeros(300, 200, device="cuda")
+    with pytest.raises(rlu.RluError):
+        rlu.Batch([{"A": A, "k": 80, "l": 90, "seed": 1}])   # l > 76: two LU panels
