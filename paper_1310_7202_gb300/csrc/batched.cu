@@ -3,10 +3,12 @@
 // in device memory, entry z = problem z), so the launch count does not grow with the batch
 // and the sequence can be captured in a CUDA graph.
 //
-//   info init, step 1 G (batched Philox/Box-Muller), step 2 Y = A G (batched SIMT GEMM),
+//   info init, step 1 G (batched Philox/Box-Muller), step 2 Y = A G (batched SIMT GEMM, or
+//   the tcgen05 TF32-split GEMM with per-problem tensor maps for RLU_PREC_MIXED),
 //   step 3 LU(Y) (one thread-block cluster per problem, launches grouped by cluster size),
 //   step 4 L_y and L~, step 5 Gram (FP32 products stored in FP64) -> LDL^T (one CTA per
-//   problem) and C = L~^T A -> blocked triangular solves, step 6 LU(B^T) (clusters), steps
+//   problem) and C = L~^T A (SIMT, or tcgen05 for RLU_PREC_MIXED) -> blocked triangular
+//   solves, step 6 LU(B^T) (clusters), steps
 //   7-8 L_b, U gathers and L = L_y L_b.
 #include <algorithm>
 #include <vector>
@@ -15,6 +17,7 @@
 #include "batched.cuh"
 #include "gemm_simt.cuh"
 #include "panel_lu.cuh"
+#include "umma.cuh"
 #include "../../include/rlu_batch.h"
 
 namespace rlu {
@@ -34,15 +37,18 @@ size_t carve(size_t& cur, size_t bytes) {
 struct ProblemLayout {
   int64_t ldg, ldy, ldl, ldb;
   int kp;
-  size_t G, Y, Lt, Lp, Mg, dinv, LT, LR, W, WT, C, B, Lb, pos, ps;
+  size_t G, Y, Lt, Lp, Mg, dinv, LT, LR, W, WT, C, B, Lb, pos, ps, Lhi, Llo;
 };
 
 struct Tables {
-  size_t info, gauss, gemm_y, lu_y, build, gemm_g, ldl, gemm_c, trsm, lu_b, gather, gemm_l;
+  size_t info, gauss, gemm_y, lu_y, build, gemm_g, ldl, gemm_c, trsm, lu_b, gather, gemm_l,
+      u3y, u3c;
 };
 
-bool valid_problem(const rlu_problem& p) {
+bool valid_problem(const rlu_problem& p, int32_t prec) {
   if (!p.A || !p.P || !p.Q || !p.L || !p.U) return false;
+  // the tensor-core products read A with TMA: rows on 16-byte boundaries
+  if (prec == RLU_PREC_MIXED && (((uintptr_t)p.A & 15u) != 0 || p.lda % 4 != 0)) return false;
   if (p.m < 1 || p.n < 1 || p.k < 1 || p.k > p.l || p.l > p.m || p.l > p.n) return false;
   if (p.l > kMaxL || p.k > kMaxK || p.m > kMaxRows || p.n > kMaxRows) return false;
   if (p.lda < p.n || p.ldl < p.m || p.ldu < p.n) return false;
@@ -50,7 +56,7 @@ bool valid_problem(const rlu_problem& p) {
 }
 
 // Layout of everything: the argument tables first, then each problem's buffers.
-size_t plan_layout(const rlu_problem* probs, int count, Tables& t,
+size_t plan_layout(const rlu_problem* probs, int count, int32_t prec, Tables& t,
                    std::vector<ProblemLayout>* lay) {
   size_t cur = 0;
   const size_t c = (size_t)count;
@@ -66,6 +72,11 @@ size_t plan_layout(const rlu_problem* probs, int count, Tables& t,
   t.lu_b = carve(cur, c * sizeof(LuArgs));
   t.gather = carve(cur, c * sizeof(GatherJob));
   t.gemm_l = carve(cur, c * sizeof(GemmArgs));
+  t.u3y = t.u3c = 0;
+  if (prec == RLU_PREC_MIXED) {
+    t.u3y = carve(cur, c * sizeof(U3Job));
+    t.u3c = carve(cur, c * sizeof(U3Job));
+  }
   for (int i = 0; i < count; ++i) {
     const rlu_problem& p = probs[i];
     ProblemLayout L{};
@@ -90,6 +101,11 @@ size_t plan_layout(const rlu_problem* probs, int count, Tables& t,
     L.Lb = carve(cur, (size_t)p.k * p.k * 4);
     L.pos = carve(cur, (size_t)std::max(p.m, p.n) * 4);
     L.ps = carve(cur, (size_t)p.l * 4);
+    L.Lhi = L.Llo = 0;
+    if (prec == RLU_PREC_MIXED) {
+      L.Lhi = carve(cur, (size_t)L.ldl * p.k * 4);
+      L.Llo = carve(cur, (size_t)L.ldl * p.k * 4);
+    }
     if (lay) lay->push_back(L);
   }
   return cur;
@@ -119,16 +135,18 @@ struct rlu_batch {
   int max_k = 0, max_l = 0, max_kp = 0;
   int first_y[17] = {}, count_y[17] = {}, first_b[17] = {}, count_b[17] = {};
   int launches = 0;
+  int u3_stages = 0, u3_stage_bytes = 0;  // tensor-core ring of the mixed precision
 };
 
 extern "C" size_t rlu_batch_workspace_size(const rlu_problem* problems, int32_t count,
                                            int32_t prec) {
   using namespace rlu;
-  if (!problems || count < 1 || count > 65535 || prec != RLU_PREC_F32) return 0;
+  if (!problems || count < 1 || count > 65535) return 0;
+  if (prec != RLU_PREC_F32 && prec != RLU_PREC_MIXED) return 0;
   for (int i = 0; i < count; ++i)
-    if (!valid_problem(problems[i])) return 0;
+    if (!valid_problem(problems[i], prec)) return 0;
   Tables t{};
-  return plan_layout(problems, count, t, nullptr);
+  return plan_layout(problems, count, prec, t, nullptr);
 }
 
 extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, int32_t prec,
@@ -136,13 +154,13 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   using namespace rlu;
   if (!out || !problems || count < 1 || count > 65535) return RLU_EINVAL;
   *out = nullptr;
-  if (prec != RLU_PREC_F32) return RLU_EUNSUPPORTED;
+  if (prec != RLU_PREC_F32 && prec != RLU_PREC_MIXED) return RLU_EUNSUPPORTED;
   for (int i = 0; i < count; ++i)
-    if (!valid_problem(problems[i])) return RLU_EINVAL;
+    if (!valid_problem(problems[i], prec)) return RLU_EINVAL;
   if (workspace == nullptr || ((uintptr_t)workspace & 255u) != 0) return RLU_EINVAL;
   Tables t{};
   std::vector<ProblemLayout> lay;
-  const size_t need = plan_layout(problems, count, t, &lay);
+  const size_t need = plan_layout(problems, count, prec, t, &lay);
   if (ws_bytes < need) return RLU_ENOMEM;
   char* ws = static_cast<char*>(workspace);
   rlu_batch* b = new rlu_batch();
@@ -161,6 +179,9 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   std::vector<TrsmJob> trsm(c);
   std::vector<GatherJob> gather(c);
   std::vector<int> gy_of(c), gb_of(c);
+  const bool mixed = prec == RLU_PREC_MIXED;
+  std::vector<U3Job> u3y(mixed ? c : 0), u3c(mixed ? c : 0);
+  int max_stage = 0;
   for (int i = 0; i < count; ++i) {
     const rlu_problem& p = problems[i];
     const ProblemLayout& L = lay[(size_t)i];
@@ -215,7 +236,45 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
     lub_all[(size_t)i] = u;
     gy_of[(size_t)i] = (int)ceil_div(p.m, 512);
     gb_of[(size_t)i] = (int)ceil_div(p.n, 512);
-    build[(size_t)i] = BuildJob{Y, L.ldy, p.m, p.k, p.P, Lt, Lp, L.ldl};
+    float* Lhi = mixed ? reinterpret_cast<float*>(ws + L.Lhi) : nullptr;
+    float* Llo = mixed ? reinterpret_cast<float*>(ws + L.Llo) : nullptr;
+    build[(size_t)i] = BuildJob{Y, L.ldy, p.m, p.k, p.P, Lt, Lp, L.ldl, Lhi, Llo};
+    if (mixed) {  // tensor-core records of Y = A G and C^T = A^T L~
+      Umma3Op op{};
+      op.A0 = static_cast<const float*>(p.A);
+      op.lda = p.lda;
+      op.B0 = G;
+      op.ldb = L.ldg;
+      op.M = p.m;
+      op.N = p.l;
+      op.K = p.n;
+      op.out = Y;
+      op.ldo = L.ldy;
+      op.out_colmajor = true;
+      op.status = p.info ? &p.info->status : nullptr;
+      int sb = 0;
+      int32_t st = umma3_make_job(U3_MODE_Y2, op, &u3y[(size_t)i], &sb);
+      max_stage = std::max(max_stage, sb);
+      op = Umma3Op{};
+      op.A0 = static_cast<const float*>(p.A);
+      op.lda = p.lda;
+      op.B0 = Lhi;
+      op.B1 = Llo;
+      op.ldb = L.ldl;
+      op.M = p.n;
+      op.N = p.k;
+      op.K = p.m;
+      op.out = Cb;
+      op.ldo = L.ldb;
+      op.out_colmajor = true;
+      op.status = p.info ? &p.info->status : nullptr;
+      if (st == RLU_OK) st = umma3_make_job(U3_MODE_C3, op, &u3c[(size_t)i], &sb);
+      max_stage = std::max(max_stage, sb);
+      if (st != RLU_OK) {
+        delete b;
+        return st;
+      }
+    }
     ldl[(size_t)i] = Ldl32Job{Mg, p.k, o, p.info ? &p.info->status : nullptr};
     trsm[(size_t)i] = TrsmJob{o, Cb, L.ldb, p.n, Bb, L.ldb};
     gather[(size_t)i] = GatherJob{Bb, L.ldb, p.Q, p.k, p.n, Lb, static_cast<float*>(p.U), p.ldu};
@@ -260,6 +319,16 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   if (st == RLU_OK) st = up(t.lu_b, lub.data(), c * sizeof(LuArgs));
   if (st == RLU_OK) st = up(t.gather, gather.data(), c * sizeof(GatherJob));
   if (st == RLU_OK) st = up(t.gemm_l, gl.data(), c * sizeof(GemmArgs));
+  if (mixed && st == RLU_OK) {
+    const int stages = umma3_stages_for(max_stage);
+    if (stages < 2) st = RLU_EUNSUPPORTED;
+    for (auto& j : u3y) j.a.stages = stages;
+    for (auto& j : u3c) j.a.stages = stages;
+    b->u3_stages = stages;
+    b->u3_stage_bytes = max_stage;
+    if (st == RLU_OK) st = up(t.u3y, u3y.data(), c * sizeof(U3Job));
+    if (st == RLU_OK) st = up(t.u3c, u3c.data(), c * sizeof(U3Job));
+  }
   if (st != RLU_OK) {
     delete b;
     return st;
@@ -282,8 +351,12 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
       reinterpret_cast<rlu_info* const*>(ws + t.info), c);
   RLU_TRY(last_launch_status());
   RLU_TRY(launch_gaussian_batched(reinterpret_cast<const GaussJob*>(ws + t.gauss), c, s));
-  RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_y), c,
-                                           b->max_m, b->max_l, true, true, false, s)));
+  if (b->prec == RLU_PREC_MIXED)
+    RLU_TRY(umma3_batched(U3_MODE_Y2, reinterpret_cast<const U3Job*>(ws + t.u3y), c,
+                          (int)b->max_m, b->u3_stages, b->u3_stage_bytes, s));
+  else
+    RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_y),
+                                             c, b->max_m, b->max_l, true, true, false, s)));
   RLU_TRY(launch_lu_reg_batched(false, reinterpret_cast<const LuArgs*>(ws + t.lu_y), b->first_y,
                                 b->count_y, s));
   RLU_TRY(build_ly_batched(reinterpret_cast<const BuildJob*>(ws + t.build), c, b->max_m,
@@ -291,8 +364,12 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
   RLU_TRY((gemm_simt_batched<float, double>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_g), c,
                                             b->max_k, b->max_k, true, true, true, s)));
   RLU_TRY(ldl32_batched(reinterpret_cast<const Ldl32Job*>(ws + t.ldl), c, b->max_k, s));
-  RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_c), c,
-                                           b->max_k, b->max_n, true, false, true, s)));
+  if (b->prec == RLU_PREC_MIXED)
+    RLU_TRY(umma3_batched(U3_MODE_C3, reinterpret_cast<const U3Job*>(ws + t.u3c), c,
+                          (int)b->max_n, b->u3_stages, b->u3_stage_bytes, s));
+  else
+    RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_c),
+                                             c, b->max_k, b->max_n, true, false, true, s)));
   RLU_TRY(trsm_batched(reinterpret_cast<const TrsmJob*>(ws + t.trsm), c, b->max_kp, b->max_n, s));
   RLU_TRY(launch_lu_reg_batched(true, reinterpret_cast<const LuArgs*>(ws + t.lu_b), b->first_b,
                                 b->count_b, s));

@@ -14,7 +14,8 @@ struct GaussJob {  // step 1: G (n x l, column-major, ld ldg) from the problem's
   int64_t ldg;
 };
 
-struct BuildJob {  // step 4: L_y (pivot order, Lp) and L~ = P^T L_y (Lt), both m x k, ld ldl
+struct BuildJob {  // step 4: L_y (pivot order, Lp) and L~ = P^T L_y (Lt), both m x k, ld ldl;
+                   // with Lhi non-null also L~'s exact TF32 split (Lhi + Llo)
   const float* Y;
   int64_t ldy, m;
   int k;
@@ -22,6 +23,8 @@ struct BuildJob {  // step 4: L_y (pivot order, Lp) and L~ = P^T L_y (Lt), both 
   float* Lt;
   float* Lp;
   int64_t ldl;
+  float* Lhi;
+  float* Llo;
 };
 
 struct Ldl32Job {  // step 5: M (k x k FP64) = L D L^T on one CTA

@@ -824,6 +824,7 @@ __global__ void k_build_ly_batched(const BuildJob* __restrict__ jobs) {
     const float v = (c < p) ? j.Y[(int64_t)c * j.ldy + r] : (c == p ? 1.f : 0.f);
     j.Lp[(int64_t)c * j.ldl + p] = v;
     j.Lt[(int64_t)c * j.ldl + r] = v;
+    if (j.Lhi) tf32_split(v, j.Lhi, j.Llo, (int64_t)c * j.ldl + r);
   }
 }
 

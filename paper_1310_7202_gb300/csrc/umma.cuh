@@ -1,6 +1,8 @@
 // Interface of the tcgen05 TF32 GEMM (see umma.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace rlu {
@@ -68,6 +70,20 @@ struct Umma3Op {
 };
 
 int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s);
+
+// Batched form (Y2 and C3 only, N <= 256, whole K per CTA): one record per problem with its
+// tensor maps (A0, A1, B0, B1) and arguments, in device memory, 64-byte aligned.
+struct U3Job {
+  CUtensorMap map[4];
+  Umma3Args a;
+};
+// Fills job (host memory) for op; *stage_bytes = its shared-memory slot size.
+int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes);
+// Ring slots that fit for the largest slot size; writes every record's stages field.
+int32_t umma3_stages_for(int stage_bytes);
+// One launch for count records: grid (ceil(max_m / 128), count).
+int32_t umma3_batched(int mode, const U3Job* jobs_dev, int count, int max_m, int stages,
+                      int max_stage_bytes, cudaStream_t s);
 
 // BF16 products (see umma_bf16.cu), same output conventions as Umma3Op.
 // Y : A (M x K row-major BF16, lda), B0 = G^T (N x K row-major BF16, ldb), one product.

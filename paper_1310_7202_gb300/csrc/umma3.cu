@@ -121,11 +121,12 @@ __host__ __device__ inline U3Layout u3_layout(int mode, int BN) {
   return L;
 }
 
+// One 128-row tile (mt) of N tile nt over K slice kz; the tensor maps are read by address
+// (kernel parameters or, for the batched form, records in global memory).
 template <int MODE>
-__global__ void __launch_bounds__(U3_THREADS, 1)
-k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-        const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
-        Umma3Args a) {
+__device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtensorMap& mA1,
+                                           const CUtensorMap& mB0, const CUtensorMap& mB1,
+                                           const Umma3Args& a, int mt, int kz, int nt) {
   using namespace u3;
   extern __shared__ __align__(1024) unsigned char u3_smem[];
   U3Smem& sh = *reinterpret_cast<U3Smem*>(u3_smem);
@@ -133,9 +134,8 @@ k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtenso
   const U3Layout lay = u3_layout(MODE, a.BN);
   const int S = a.stages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * U3_BM;
-  const int kz = blockIdx.y;
-  const int nb0 = blockIdx.z * a.BN;  // first column of this CTA's N tile
+  const int m0 = mt * U3_BM;
+  const int nb0 = nt * a.BN;  // first column of this CTA's N tile
   const int k_begin = kz * a.kchunk;
   const int k_end = min(a.K, k_begin + a.kchunk);
   const int nk = (k_end - k_begin + U3_BK - 1) / U3_BK;
@@ -311,6 +311,23 @@ k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtenso
   if (threadIdx.x == 0 && sh.err && a.status) atomicExch(a.status, RLU_ETIMEOUT);
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(U3_THREADS, 1)
+k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+        const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+        Umma3Args a) {
+  umma3_tile<MODE>(mA0, mA1, mB0, mB1, a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched form: problem blockIdx.y (one N tile, no split), 128-row tile blockIdx.x; CTAs past
+// the problem's rows return before any allocation.
+template <int MODE>
+__global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_batched(const U3Job* __restrict__ jobs) {
+  const U3Job& j = jobs[blockIdx.y];
+  if ((int)blockIdx.x * U3_BM >= j.a.M) return;
+  umma3_tile<MODE>(j.map[0], j.map[1], j.map[2], j.map[3], j.a, blockIdx.x, 0, 0);
+}
+
 // ---------------------------------------------------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -405,6 +422,75 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
   if (a.out == op.partial && op.out)
     return splitk_reduce_f32(op.partial, splits, op.M, op.N, op.out, op.ldo, !op.out_colmajor, s);
   return RLU_OK;
+}
+
+// Fills one problem's record of the batched form (whole K, one N tile: N <= 256).
+template <int MODE>
+static int32_t make_job(const Umma3Op& op, U3Job* job, int* stage_bytes) {
+  if (op.M <= 0 || op.N <= 0 || op.N > 256 || op.K <= 0 || !op.out) return RLU_EINVAL;
+  const int BN = (int)round_up(op.N, 16);
+  const U3Layout lay = u3_layout(MODE, BN);
+  if (MODE == U3_MODE_Y2) {
+    RLU_TRY(map2d(&job->map[0], op.A0, op.M, op.K, op.lda, U3_BK, U3_BM, true));
+    RLU_TRY(map2d(&job->map[2], op.B0, op.N, op.K, op.ldb, U3_BK, BN, true));
+    job->map[1] = job->map[0];
+    job->map[3] = job->map[2];
+  } else if (MODE == U3_MODE_C3) {
+    RLU_TRY(map2d(&job->map[0], op.A0, op.K, op.M, op.lda, U3_BM, U3_BK, false));
+    RLU_TRY(map2d(&job->map[2], op.B0, op.N, op.K, op.ldb, U3_BK, BN, true));
+    RLU_TRY(map2d(&job->map[3], op.B1, op.N, op.K, op.ldb, U3_BK, BN, true));
+    job->map[1] = job->map[0];
+  } else {
+    return RLU_EINVAL;
+  }
+  Umma3Args& a = job->a;
+  a = Umma3Args{};
+  a.M = (int)op.M;
+  a.N = (int)op.N;
+  a.K = (int)op.K;
+  a.BN = BN;
+  a.kchunk = (int)round_up(op.K, U3_BK);
+  a.out = op.out;
+  a.ldo = op.ldo;
+  a.out_colmajor = op.out_colmajor;
+  a.status = op.status;
+  *stage_bytes = (int)lay.stage;
+  return RLU_OK;
+}
+
+int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes) {
+  if (mode == U3_MODE_Y2) return make_job<U3_MODE_Y2>(op, job, stage_bytes);
+  if (mode == U3_MODE_C3) return make_job<U3_MODE_C3>(op, job, stage_bytes);
+  return RLU_EINVAL;
+}
+
+int32_t umma3_stages_for(int stage_bytes) {
+  int dev = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  int optin = 0;
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int stages = (optin - 2048) / stage_bytes;
+  return stages > U3_MAXST ? U3_MAXST : stages;
+}
+
+int32_t umma3_batched(int mode, const U3Job* jobs_dev, int count, int max_m, int stages,
+                      int max_stage_bytes, cudaStream_t s) {
+  if (count <= 0) return RLU_OK;
+  if (count > 65535 || stages < 2) return RLU_EINVAL;
+  const size_t smem = 2048 + (size_t)stages * max_stage_bytes;
+  const dim3 grid((unsigned)ceil_div(max_m, U3_BM), (unsigned)count);
+  if (mode == U3_MODE_Y2) {
+    RLU_CUDA_TRY(cudaFuncSetAttribute(k_umma3_batched<U3_MODE_Y2>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_umma3_batched<U3_MODE_Y2><<<grid, U3_THREADS, smem, s>>>(jobs_dev);
+  } else if (mode == U3_MODE_C3) {
+    RLU_CUDA_TRY(cudaFuncSetAttribute(k_umma3_batched<U3_MODE_C3>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_umma3_batched<U3_MODE_C3><<<grid, U3_THREADS, smem, s>>>(jobs_dev);
+  } else {
+    return RLU_EINVAL;
+  }
+  return last_launch_status();
 }
 
 int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s) {

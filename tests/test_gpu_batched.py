@@ -1,7 +1,8 @@
-"""Batched form (include/rlu_batch.h): many uneven FP32 problems per launch sequence. Each
-problem is checked against the FP64 oracle (same FP32 Gaussian, tolerance 1.1x the oracle's
-||PAQ - LU||_F plus 1e-4 ||A||_2) and against the single-problem path; a CUDA-graph replay
-of the batch reproduces the direct launch bit for bit. GPU only."""
+"""Batched form (include/rlu_batch.h): many uneven FP32 problems per launch sequence, plain
+FP32 and mixed (tensor-core products). Each problem is checked against the FP64 oracle (same
+FP32 Gaussian, tolerance 1.1x the oracle's ||PAQ - LU||_F plus 1e-4 ||A||_2) and against the
+single-problem path; a CUDA-graph replay of the batch reproduces the direct launch bit for
+bit. GPU only."""
 import numpy as np
 import pytest
 import torch
@@ -13,16 +14,25 @@ from tests.gpu_helpers import leading_agreement
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def batch():
+def _padded(A: np.ndarray) -> torch.Tensor:
+    """A on the device with rows padded to a multiple of 4 floats (16-byte aligned rows, as
+    the tensor-core products of the mixed precision read them)."""
+    m, n = A.shape
+    buf = torch.zeros(m, (n + 3) // 4 * 4, device="cuda")
+    buf[:, :n] = torch.from_numpy(A).cuda()
+    return buf[:, :n]
+
+
+@pytest.fixture(scope="module", params=["f32", "mixed"])
+def batch(request):
     shapes = synth.batch_shapes(40, seed=3, max_m=768, max_n=512)
     probs, mats = [], []
     for i, (m, n, k, l) in enumerate(shapes):
         sigma = np.exp(-np.arange(1, min(m, n) + 1) / k)
         A = synth.prescribed_matrix(m, n, sigma, 100 + i, 200 + i, dtype=np.float32)
         mats.append((A, sigma))
-        probs.append({"A": torch.from_numpy(A).cuda(), "k": k, "l": l, "seed": 1000 + i})
-    b = rlu.Batch(probs, "f32")
+        probs.append({"A": _padded(A), "k": k, "l": l, "seed": 1000 + i})
+    b = rlu.Batch(probs, request.param)
     b.run()
     torch.cuda.synchronize()
     res = [{key: v.clone() for key, v in o.items()} for o in b.outs]
@@ -46,7 +56,7 @@ def test_batched_against_oracle(batch):
 def test_batched_matches_single_problem_path(batch):
     shapes, mats, probs, b, res = batch
     for (m, n, k, l), (A, sigma), p, r in zip(shapes, mats, probs, res):
-        s = rlu.factor(p["A"], k, l, p["seed"], "f32")
+        s = rlu.factor(p["A"], k, l, p["seed"], b.prec)
         fro_s, _ = rlu.reconstruct_error(p["A"], s["P"], s["Q"], s["L"], s["U"])
         fro_b, _ = rlu.reconstruct_error(p["A"], r["P"], r["Q"], r["L"], r["U"])
         assert abs(fro_b.item() - fro_s.item()) <= 0.05 * fro_s.item() + 1e-6, (m, n, k)
@@ -78,3 +88,6 @@ def test_batched_rejects_problems_outside_the_form():
     A = torch.zeros(300, 200, device="cuda")
     with pytest.raises(rlu.RluError):
         rlu.Batch([{"A": A, "k": 80, "l": 90, "seed": 1}])   # l > 76: two LU panels
+    with pytest.raises(rlu.RluError):                          # rows not 16-byte aligned
+        rlu.Batch([{"A": torch.zeros(300, 203, device="cuda")[:, :201], "k": 8, "l": 18,
+                    "seed": 1}], "mixed")
