@@ -1,4 +1,4 @@
-// Interface of the tcgen05 TF32 GEMM (see umma.cu).
+// Interfaces of the tcgen05 GEMMs (see umma3.cu and umma_bf16.cu).
 #pragma once
 
 #include <cuda.h>
@@ -6,36 +6,6 @@
 #include "common.cuh"
 
 namespace rlu {
-
-// Kernel arguments (by value).
-struct UmmaArgs {
-  float* out;
-  int64_t ldo;
-  size_t split_stride;
-  int M, N, K, BN, kchunk;
-  bool out_colmajor;
-  int32_t* status;
-};
-
-// D (M x N) = A (M x K, row-major, lda) * B (N x K, row-major, ldb)^T, TF32 multiplies.
-// N <= 256. out: column-major (ldo >= M) or row-major (ldo >= N). splits > 1 writes
-// row-major partial slices (splits * M * N floats) reduced in a fixed order.
-struct UmmaOp {
-  const float* A;
-  int64_t lda;
-  const float* B;
-  int64_t ldb;
-  int64_t M, N, K;
-  float* out;
-  int64_t ldo;
-  bool out_colmajor;
-  int splits;
-  float* partial;
-  int32_t* status;
-};
-
-int32_t umma_tf32_gemm(const UmmaOp& op, cudaStream_t s);
-size_t umma_smem_bytes(int BN);
 
 // FP32-accurate tensor-core products from exact TF32 splits (see umma3.cu).
 enum { U3_MODE_Y2 = 0, U3_MODE_C3 = 1, U3_MODE_G3 = 2 };
