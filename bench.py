@@ -559,8 +559,12 @@ def run_batched(args):
     K, W = args.steps, args.warmup
     stream = torch.cuda.Stream()
     out = {}
+    from paper_1310_7202_gb300 import autotune
     for prec in (["mixed", "f32"] if args.prec is None else [args.prec]):
-        b = rlu.Batch(probs, prec)
+        t_tune = time.perf_counter()
+        tuned = autotune.tune(probs, prec, reps=3, use_cache=False)
+        t_tune = time.perf_counter() - t_tune
+        b = rlu.Batch(probs, prec, tuned["options"])
         with torch.cuda.stream(stream):
             b.run()
         torch.cuda.synchronize()
@@ -585,7 +589,10 @@ def run_batched(args):
         infos = torch.stack([o["info"] for o in b.outs]).cpu()
         out[prec] = {"ms": ms, "mean_ms": statistics.mean(times), "clocks": clocks.summary(),
                      "launches_per_batch": b.launches(), "ok": bool((infos[:, 0] == 0).all()),
-                     "b": b}
+                     "autotune": {"options": tuned["options"], "default_ms": tuned["default_ms"],
+                                  "tuned_ms": tuned["ms"], "trials": len(tuned["trials"]),
+                                  "seconds": round(t_tune, 1)}}
+        del b, g
     prec = next(iter(out))
     r = out[prec]
     count = len(probs)
@@ -614,6 +621,7 @@ def run_batched(args):
                      "note": "algorithmic bytes: A read twice, G, Y, C, B and L written/read "
                              "once per problem"},
         "all_info_ok": r["ok"], "setup_s": round(setup_s, 1),
+        "autotune": {p: v["autotune"] for p, v in out.items()},
         "plain_fp32": ({"value": count / (out["f32"]["ms"] / 1e3), "unit": "LU/s",
                         "ms_per_step": out["f32"]["ms"],
                         "speedup": out["f32"]["ms"] / r["ms"], "speedup_of": prec}

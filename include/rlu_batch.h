@@ -43,14 +43,29 @@ typedef struct {
   rlu_info* info;
 } rlu_problem;
 
+/* Kernel choices of a batch (the autotuner's knobs; zero-initialised = defaults).
+ *   gemm_tile_y, gemm_tile_c, gemm_tile_l: SIMT output tile of the products Y = A G,
+ *     C = L~^T A and L = L_y L_b: 0 = 128 x 128, 1 = 64 x 64 (Y and C use the tensor cores
+ *     under RLU_PREC_MIXED; their knobs are then ignored).
+ *   lu_rows_per_cta: rows of an LU held by one CTA of a problem's cluster: 0 or 512 (512
+ *     threads), 256 (256 threads, twice the CTAs per problem; m and n <= 4096). */
+typedef struct {
+  int32_t gemm_tile_y;
+  int32_t gemm_tile_c;
+  int32_t gemm_tile_l;
+  int32_t lu_rows_per_cta;
+} rlu_batch_options;
+
 /* Workspace bytes for the batch (0 if a problem is invalid for the batched form). */
 size_t rlu_batch_workspace_size(const rlu_problem* problems, int32_t count, int32_t prec);
 
 /* Plans the batch in the caller's workspace (256-byte aligned, at least
  * rlu_batch_workspace_size bytes) and uploads the argument records (synchronous copies).
- * RLU_EINVAL for an invalid problem or argument, RLU_ENOMEM for a small workspace. */
+ * options may be NULL (defaults). RLU_EINVAL for an invalid problem, option or argument
+ * (including a problem too tall for lu_rows_per_cta), RLU_ENOMEM for a small workspace. */
 int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, int32_t prec,
-                         void* workspace, size_t ws_bytes, rlu_batch** out);
+                         const rlu_batch_options* options, void* workspace, size_t ws_bytes,
+                         rlu_batch** out);
 
 /* Enqueues the whole batch on stream (a cudaStream_t, NULL for the legacy stream). */
 int32_t rlu_factor_batched(rlu_batch* batch, void* stream);

@@ -136,6 +136,7 @@ struct rlu_batch {
   int first_y[17] = {}, count_y[17] = {}, first_b[17] = {}, count_b[17] = {};
   int launches = 0;
   int u3_stages = 0, u3_stage_bytes = 0;  // tensor-core ring of the mixed precision
+  rlu_batch_options opt{};
 };
 
 extern "C" size_t rlu_batch_workspace_size(const rlu_problem* problems, int32_t count,
@@ -150,10 +151,20 @@ extern "C" size_t rlu_batch_workspace_size(const rlu_problem* problems, int32_t 
 }
 
 extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, int32_t prec,
-                                    void* workspace, size_t ws_bytes, rlu_batch** out) {
+                                    const rlu_batch_options* options, void* workspace,
+                                    size_t ws_bytes, rlu_batch** out) {
   using namespace rlu;
   if (!out || !problems || count < 1 || count > 65535) return RLU_EINVAL;
   *out = nullptr;
+  rlu_batch_options opt{};
+  if (options) opt = *options;
+  if (opt.lu_rows_per_cta == 0) opt.lu_rows_per_cta = 512;
+  if (opt.lu_rows_per_cta != 512 && opt.lu_rows_per_cta != 256) return RLU_EINVAL;
+  for (int t : {opt.gemm_tile_y, opt.gemm_tile_c, opt.gemm_tile_l})
+    if (t != 0 && t != 1) return RLU_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (std::max(problems[i].m, problems[i].n) > 16 * (int64_t)opt.lu_rows_per_cta)
+      return RLU_EINVAL;
   if (prec != RLU_PREC_F32 && prec != RLU_PREC_MIXED) return RLU_EUNSUPPORTED;
   for (int i = 0; i < count; ++i)
     if (!valid_problem(problems[i], prec)) return RLU_EINVAL;
@@ -168,6 +179,7 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   b->count = count;
   b->prec = prec;
   b->t = t;
+  b->opt = opt;
 
   const size_t c = (size_t)count;
   std::vector<rlu_info*> infos(c);
@@ -228,14 +240,14 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
     u.zero_step = p.info ? &p.info->first_zero_pivot_y : nullptr;
     u.nonfinite = p.info ? &p.info->nonfinite : nullptr;
     u.status = p.info ? &p.info->status : nullptr;
-    u.posg = pos; u.psg = ps; u.p0 = 0; u.pw = p.l; u.rpc = 512; u.nb = kMaxL;
+    u.posg = pos; u.psg = ps; u.p0 = 0; u.pw = p.l; u.rpc = opt.lu_rows_per_cta; u.nb = kMaxL;
     luy_all[(size_t)i] = u;
     u.X = Bb; u.ldx = L.ldb; u.R = (int)p.n; u.C = p.k; u.perm = p.Q;
     u.zero_step = p.info ? &p.info->first_zero_pivot_b : nullptr;
     u.pw = p.k;
     lub_all[(size_t)i] = u;
-    gy_of[(size_t)i] = (int)ceil_div(p.m, 512);
-    gb_of[(size_t)i] = (int)ceil_div(p.n, 512);
+    gy_of[(size_t)i] = (int)ceil_div(p.m, opt.lu_rows_per_cta);
+    gb_of[(size_t)i] = (int)ceil_div(p.n, opt.lu_rows_per_cta);
     float* Lhi = mixed ? reinterpret_cast<float*>(ws + L.Lhi) : nullptr;
     float* Llo = mixed ? reinterpret_cast<float*>(ws + L.Llo) : nullptr;
     build[(size_t)i] = BuildJob{Y, L.ldy, p.m, p.k, p.P, Lt, Lp, L.ldl, Lhi, Llo};
@@ -356,8 +368,10 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
                           (int)b->max_m, b->u3_stages, b->u3_stage_bytes, s));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_y),
-                                             c, b->max_m, b->max_l, true, true, false, s)));
-  RLU_TRY(launch_lu_reg_batched(false, reinterpret_cast<const LuArgs*>(ws + t.lu_y), b->first_y,
+                                             c, b->max_m, b->max_l, true, true, false, s,
+                                             b->opt.gemm_tile_y)));
+  RLU_TRY(launch_lu_reg_batched(false, b->opt.lu_rows_per_cta,
+                                reinterpret_cast<const LuArgs*>(ws + t.lu_y), b->first_y,
                                 b->count_y, s));
   RLU_TRY(build_ly_batched(reinterpret_cast<const BuildJob*>(ws + t.build), c, b->max_m,
                            b->max_k, s));
@@ -369,14 +383,17 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
                           (int)b->max_n, b->u3_stages, b->u3_stage_bytes, s));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_c),
-                                             c, b->max_k, b->max_n, true, false, true, s)));
+                                             c, b->max_k, b->max_n, true, false, true, s,
+                                             b->opt.gemm_tile_c)));
   RLU_TRY(trsm_batched(reinterpret_cast<const TrsmJob*>(ws + t.trsm), c, b->max_kp, b->max_n, s));
-  RLU_TRY(launch_lu_reg_batched(true, reinterpret_cast<const LuArgs*>(ws + t.lu_b), b->first_b,
+  RLU_TRY(launch_lu_reg_batched(true, b->opt.lu_rows_per_cta,
+                                reinterpret_cast<const LuArgs*>(ws + t.lu_b), b->first_b,
                                 b->count_b, s));
   RLU_TRY(gather_batched(reinterpret_cast<const GatherJob*>(ws + t.gather), c, b->max_k,
                          b->max_n, s));
   RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_l), c,
-                                           b->max_m, b->max_k, false, true, false, s)));
+                                           b->max_m, b->max_k, false, true, false, s,
+                                           b->opt.gemm_tile_l)));
   return RLU_OK;
 }
 

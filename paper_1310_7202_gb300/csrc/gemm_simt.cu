@@ -22,21 +22,26 @@ template <> struct GemmCfg<float> {
 template <> struct GemmCfg<double> {
   static constexpr int BM = 64, BN = 64, BK = 16, V = 2, TX = 16, TY = 16;
 };
+// the smaller FP32 tile of the batched products (chosen per step by the autotuner)
+struct GemmCfgF64x64 {
+  static constexpr int BM = 64, BN = 64, BK = 16, V = 2, TX = 16, TY = 16;
+};
 
-template <typename T> struct Vec;
-template <> struct Vec<float> { using type = float4; };
-template <> struct Vec<double> { using type = double2; };
+// V consecutive elements of T as one vector load
+template <typename T, int V> struct Vec;
+template <> struct Vec<float, 4> { using type = float4; };
+template <> struct Vec<float, 2> { using type = float2; };
+template <> struct Vec<double, 2> { using type = double2; };
 
 // One BM x BN output tile (bx, by) of K range slice bz; the output element type OutT may be
 // wider than T (the batched Gram matrix is stored in FP64 for the LDL^T).
-template <typename T, typename OutT, bool AK, bool BKM, bool CR>
+template <typename T, typename OutT, bool AK, bool BKM, bool CR, typename Cfg = GemmCfg<T>>
 __device__ __forceinline__ void gemm_tile(const GemmArgs& p, int bx, int by, int bz) {
-  using Cfg = GemmCfg<T>;
   constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, V = Cfg::V;
   constexpr int NT = Cfg::TX * Cfg::TY;
   constexpr int PAD = V;
   constexpr int A_LD = BM * BK / NT, B_LD = BN * BK / NT;
-  using VT = typename Vec<T>::type;
+  using VT = typename Vec<T, V>::type;
 
   __shared__ __align__(16) T As[2][BK][BM + PAD];
   __shared__ __align__(16) T Bs[2][BK][BN + PAD];
@@ -146,12 +151,11 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmArgs p) {
 
 // Batched form: problem blockIdx.z of the table, whole K range (no split); CTAs past the
 // problem's own tile counts return at once.
-template <typename T, typename OutT, bool AK, bool BKM, bool CR>
+template <typename T, typename OutT, bool AK, bool BKM, bool CR, typename Cfg>
 __global__ void __launch_bounds__(256) k_gemm_simt_batched(const GemmArgs* __restrict__ table) {
-  using Cfg = GemmCfg<T>;
   const GemmArgs p = table[blockIdx.z];
   if ((int64_t)blockIdx.y * Cfg::BM >= p.M || (int64_t)blockIdx.x * Cfg::BN >= p.N) return;
-  gemm_tile<T, OutT, AK, BKM, CR>(p, blockIdx.x, blockIdx.y, 0);
+  gemm_tile<T, OutT, AK, BKM, CR, Cfg>(p, blockIdx.x, blockIdx.y, 0);
 }
 
 // out(i, j) = sum_z part[z][i][j], z ascending; accumulation and output in OutT.
@@ -191,17 +195,15 @@ static void launch_variant(const GemmArgs& a, bool AK, bool BKM, bool CR, dim3 g
 #undef RLU_GEMM_CASE
 }
 
-template <typename T, typename OutT>
-int32_t gemm_simt_batched(const GemmArgs* table_dev, int count, int64_t max_m, int64_t max_n,
-                          bool a_kmajor, bool b_kmajor, bool c_rowmajor, cudaStream_t s) {
-  using Cfg = GemmCfg<T>;
-  if (count <= 0) return RLU_OK;
-  if (count > 65535) return RLU_EINVAL;
+template <typename T, typename OutT, typename Cfg>
+static int32_t gemm_batched_cfg(const GemmArgs* table_dev, int count, int64_t max_m,
+                                int64_t max_n, bool a_kmajor, bool b_kmajor, bool c_rowmajor,
+                                cudaStream_t s) {
   const dim3 grid((unsigned)ceil_div(max_n, Cfg::BN), (unsigned)ceil_div(max_m, Cfg::BM),
                   (unsigned)count);
 #define RLU_GEMM_BCASE(x, y, z)                                                        \
   if (a_kmajor == x && b_kmajor == y && c_rowmajor == z) {                             \
-    k_gemm_simt_batched<T, OutT, x, y, z><<<grid, 256, 0, s>>>(table_dev);             \
+    k_gemm_simt_batched<T, OutT, x, y, z, Cfg><<<grid, 256, 0, s>>>(table_dev);        \
     return last_launch_status();                                                       \
   }
   RLU_GEMM_BCASE(true, true, true)
@@ -215,10 +217,23 @@ int32_t gemm_simt_batched(const GemmArgs* table_dev, int count, int64_t max_m, i
 #undef RLU_GEMM_BCASE
   return RLU_EINVAL;
 }
+
+template <typename T, typename OutT>
+int32_t gemm_simt_batched(const GemmArgs* table_dev, int count, int64_t max_m, int64_t max_n,
+                          bool a_kmajor, bool b_kmajor, bool c_rowmajor, cudaStream_t s,
+                          int tile) {
+  if (count <= 0) return RLU_OK;
+  if (count > 65535) return RLU_EINVAL;
+  if (tile == 1)
+    return gemm_batched_cfg<T, OutT, GemmCfgF64x64>(table_dev, count, max_m, max_n, a_kmajor,
+                                                    b_kmajor, c_rowmajor, s);
+  return gemm_batched_cfg<T, OutT, GemmCfg<T>>(table_dev, count, max_m, max_n, a_kmajor,
+                                               b_kmajor, c_rowmajor, s);
+}
 template int32_t gemm_simt_batched<float, float>(const GemmArgs*, int, int64_t, int64_t, bool,
-                                                 bool, bool, cudaStream_t);
+                                                 bool, bool, cudaStream_t, int);
 template int32_t gemm_simt_batched<float, double>(const GemmArgs*, int, int64_t, int64_t, bool,
-                                                  bool, bool, cudaStream_t);
+                                                  bool, bool, cudaStream_t, int);
 
 template <typename T>
 size_t gemm_partial_bytes(int64_t M, int64_t N, int splits) {

@@ -51,10 +51,12 @@ size_t gemm_partial_bytes(int64_t M, int64_t N, int splits);
 
 // Batched products: table_dev[z] (device array of count GemmArgs with kchunk = K and
 // split_stride = 0) is problem z; layouts as for GemmOp, the same for every problem;
-// max_m / max_n bound the problems' M and N (grid size).
+// max_m / max_n bound the problems' M and N (grid size). tile 0: 128 x 128 output tiles
+// (FP32), 1: 64 x 64.
 template <typename T, typename OutT>
 int32_t gemm_simt_batched(const GemmArgs* table_dev, int count, int64_t max_m, int64_t max_n,
-                          bool a_kmajor, bool b_kmajor, bool c_rowmajor, cudaStream_t s);
+                          bool a_kmajor, bool b_kmajor, bool c_rowmajor, cudaStream_t s,
+                          int tile = 0);
 
 int gemm_tile_m(int32_t dtype);
 int gemm_tile_n(int32_t dtype);

@@ -613,12 +613,15 @@ int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s
 }
 
 // Batched LUs of problems that fit one register panel (C <= NB - 1 = 76 FP32 columns, R <=
-// 16 x 512 rows): the table on the device is grouped by cluster size (ceil(R / 512) CTAs);
-// group g starts at table entry first[g] and holds count[g] problems.
-int32_t launch_lu_reg_batched(bool crout, const LuArgs* table_dev, const int* first,
-                              const int* count, cudaStream_t s) {
+// 16 x rows_per_cta): the table on the device is grouped by cluster size (ceil(R /
+// rows_per_cta) CTAs); group g starts at table entry first[g] and holds count[g] problems.
+// rows_per_cta is 512 (512-thread CTAs) or 256 (256-thread CTAs, twice as many CTAs per
+// problem).
+template <int NT>
+static int32_t lu_batched_nt(bool crout, const LuArgs* table_dev, const int* first,
+                             const int* count, cudaStream_t s) {
   using T = float;
-  constexpr int NB = 77, NT = 512;
+  constexpr int NB = 77;
   int dev = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
   int optin = 0;
@@ -646,6 +649,13 @@ int32_t launch_lu_reg_batched(bool crout, const LuArgs* table_dev, const int* fi
     RLU_TRY(last_launch_status());
   }
   return RLU_OK;
+}
+
+int32_t launch_lu_reg_batched(bool crout, int rows_per_cta, const LuArgs* table_dev,
+                              const int* first, const int* count, cudaStream_t s) {
+  if (rows_per_cta == 256) return lu_batched_nt<256>(crout, table_dev, first, count, s);
+  if (rows_per_cta == 512) return lu_batched_nt<512>(crout, table_dev, first, count, s);
+  return RLU_EINVAL;
 }
 
 }  // namespace rlu

@@ -28,11 +28,12 @@ int32_t launch_cluster_lu(int32_t dtype, bool crout, const LuArgs& a, cudaStream
 // Register-resident variant (lu_reg.cu); *launched is false when the shape does not fit it.
 int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s, bool* launched);
 
-// Batched FP32 LUs of single-panel problems (C <= 76, R <= 8192), one cluster each; the
-// device table is grouped by cluster size g = ceil(R / 512) (entries first[g] ..
-// first[g] + count[g] - 1; first and count are host arrays of 17 entries). Each entry
-// carries rpc = 512, p0 = 0, pw = C and its own position state (posg, psg).
-int32_t launch_lu_reg_batched(bool crout, const LuArgs* table_dev, const int* first,
-                              const int* count, cudaStream_t s);
+// Batched FP32 LUs of single-panel problems (C <= 76, R <= 16 x rows_per_cta), one cluster
+// each; the device table is grouped by cluster size g = ceil(R / rows_per_cta) (entries
+// first[g] .. first[g] + count[g] - 1; first and count are host arrays of 17 entries). Each
+// entry carries rpc = rows_per_cta (512 or 256), p0 = 0, pw = C and its own position state
+// (posg, psg).
+int32_t launch_lu_reg_batched(bool crout, int rows_per_cta, const LuArgs* table_dev,
+                              const int* first, const int* count, cudaStream_t s);
 
 }  // namespace rlu

@@ -59,6 +59,11 @@ class _Problem(ctypes.Structure):
                 ("ldu", ctypes.c_int64), ("info", ctypes.c_void_p)]
 
 
+class _BatchOptions(ctypes.Structure):
+    _fields_ = [("gemm_tile_y", ctypes.c_int32), ("gemm_tile_c", ctypes.c_int32),
+                ("gemm_tile_l", ctypes.c_int32), ("lu_rows_per_cta", ctypes.c_int32)]
+
+
 class _StageOutputs(ctypes.Structure):
     _fields_ = [("G", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("Ly", ctypes.c_void_p),
                 ("B", ctypes.c_void_p), ("events", ctypes.POINTER(ctypes.c_void_p)),
@@ -126,8 +131,8 @@ def load_library(require_cuda: bool = True) -> ctypes.CDLL:
     lib.rlu_batch_workspace_size.restype = sz
     lib.rlu_batch_workspace_size.argtypes = [ctypes.POINTER(_Problem), i32, i32]
     lib.rlu_batch_create.restype = i32
-    lib.rlu_batch_create.argtypes = [ctypes.POINTER(_Problem), i32, i32, vp, sz,
-                                     ctypes.POINTER(vp)]
+    lib.rlu_batch_create.argtypes = [ctypes.POINTER(_Problem), i32, i32,
+                                     ctypes.POINTER(_BatchOptions), vp, sz, ctypes.POINTER(vp)]
     lib.rlu_factor_batched.restype = i32
     lib.rlu_factor_batched.argtypes = [vp, vp]
     lib.rlu_batch_launches.restype = i32
@@ -389,9 +394,13 @@ class Batch:
     (dicts with A, a row-major FP32 CUDA tensor, and k, l, seed); run() enqueues the whole
     batch (a fixed number of launches), which can be captured in a CUDA graph."""
 
-    def __init__(self, problems: list[dict], prec: int | str = RLU_PREC_F32):
+    def __init__(self, problems: list[dict], prec: int | str = RLU_PREC_F32,
+                 options: dict | None = None):
+        """options: the kernel choices of include/rlu_batch.h (gemm_tile_y, gemm_tile_c,
+        gemm_tile_l, lu_rows_per_cta); missing keys take the defaults."""
         self.lib = load_library()
         self.prec = PREC_BY_NAME[prec] if isinstance(prec, str) else int(prec)
+        self.options = dict(options or {})
         self.outs = []
         arr = (_Problem * len(problems))()
         for i, p in enumerate(problems):
@@ -416,7 +425,8 @@ class Batch:
         self.workspace = torch.empty(ws, dtype=torch.uint8, device="cuda")
         torch.cuda.synchronize()
         h = ctypes.c_void_p()
-        _check(self.lib.rlu_batch_create(arr, len(problems), self.prec,
+        opt = _BatchOptions(**{k: int(v) for k, v in self.options.items()})
+        _check(self.lib.rlu_batch_create(arr, len(problems), self.prec, ctypes.byref(opt),
                                          _dev_ptr(self.workspace), ws, ctypes.byref(h)),
                "rlu_batch_create")
         self.h = h

@@ -91,3 +91,43 @@ def test_batched_rejects_problems_outside_the_form():
     with pytest.raises(rlu.RluError):                          # rows not 16-byte aligned
         rlu.Batch([{"A": torch.zeros(300, 203, device="cuda")[:, :201], "k": 8, "l": 18,
                     "seed": 1}], "mixed")
+
+
+@pytest.mark.parametrize("options", [{"lu_rows_per_cta": 256},
+                                     {"gemm_tile_y": 1, "gemm_tile_c": 1, "gemm_tile_l": 1}])
+def test_batched_kernel_choices_keep_results(options):
+    """The autotuner's alternatives (256-row LU CTAs, 64 x 64 SIMT tiles) factor the same
+    problems within the same tolerance."""
+    shapes = synth.batch_shapes(12, seed=9, max_m=1100, max_n=600)
+    probs, mats = [], []
+    for i, (m, n, k, l) in enumerate(shapes):
+        sigma = np.exp(-np.arange(1, min(m, n) + 1) / k)
+        A = synth.prescribed_matrix(m, n, sigma, 300 + i, 400 + i, dtype=np.float32)
+        mats.append((A, sigma))
+        probs.append({"A": _padded(A), "k": k, "l": l, "seed": 70 + i})
+    b = rlu.Batch(probs, "f32", options)
+    b.run()
+    torch.cuda.synchronize()
+    for (m, n, k, l), (A, sigma), p, o in zip(shapes, mats, probs, b.outs):
+        G = O.gaussian_f32(p["seed"], 0, n, l).astype(np.float64)
+        orc = O.rlu_factor(A.astype(np.float64), k, l, seed=p["seed"], G=G)
+        fro_o, _ = O.reconstruct_error(A, orc["P"], orc["Q"], orc["L"], orc["U"],
+                                       spectral=False)
+        fro_g, _ = O.reconstruct_error(A, *(o[x].cpu().numpy() for x in ("P", "Q", "L", "U")),
+                                       spectral=False)
+        assert fro_g <= 1.1 * fro_o + 1e-4 * sigma[0], (m, n, k, options)
+
+
+def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
+    from paper_1310_7202_gb300 import autotune
+    monkeypatch.setenv("RLU_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
+    shapes = synth.batch_shapes(16, seed=11, max_m=600, max_n=400)
+    probs = [{"A": torch.randn(m, (n + 3) // 4 * 4, device="cuda")[:, :n], "k": k, "l": l,
+              "seed": i} for i, (m, n, k, l) in enumerate(shapes)]
+    r = autotune.tune(probs, "f32", reps=2)
+    assert not r["cached"] and r["ms"] <= r["default_ms"]
+    for knob, v in r["options"].items():
+        assert v in autotune.KNOBS[knob]
+    assert len(r["trials"]) >= 4
+    again = autotune.tune(probs, "f32", reps=2)
+    assert again["cached"] and again["options"] == r["options"]
