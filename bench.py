@@ -173,10 +173,11 @@ STAGE_SOURCE = {"gaussian": "gauss.cu", "gemm_Y": "gemm_simt.cu", "lu_Y": "lu_re
                 "gather_Lb_U": "small.cu", "gemm_L": "gemm_simt.cu"}
 # the mixed path runs its three large products on the tensor cores
 MIXED_SOURCE = {"gemm_Y": "umma3.cu", "gram": "umma3.cu", "gemm_C": "umma3.cu"}
+BF16_SOURCE = {"gemm_Y": "umma_bf16.cu", "gram": "umma3.cu", "gemm_C": "umma_bf16.cu"}
 
 
 def source_sha(stage: str, prec: str = "f32") -> str:
-    src = MIXED_SOURCE.get(stage) if prec == "mixed" else None
+    src = {"mixed": MIXED_SOURCE, "bf16": BF16_SOURCE}.get(prec, {}).get(stage)
     p = os.path.join(ROOT, "paper_1310_7202_gb300", "csrc", src or STAGE_SOURCE[stage])
     with open(p, "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()[:12]
@@ -444,7 +445,7 @@ def run_ours(args):
         roof = {"kernel": dom, "bound": "hbm", "achieved": byts / (dom_ms / 1e3) / 1e9,
                 "peak": peak, "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs"}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
-    tr = dram_traffic(dom, args.workload, args.prec)
+    tr = dram_traffic(dom, args.workload, prec)
     roof["traffic"] = tr
     roof["algorithmic_per_launch"] = flops if roof["unit"] == "TFLOP/s" else byts
     roof["launch_ms"] = dom_ms

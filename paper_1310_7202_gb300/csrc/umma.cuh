@@ -15,6 +15,7 @@ struct Umma3Args {
   int64_t ldo;
   size_t split_stride;
   int M, N, K, BN, kchunk, stages;
+  int ntiles;  // N tiles; grid x = row tiles x N tiles, the N tile varying fastest
   bool out_colmajor;
   int32_t* status;
 };

@@ -316,7 +316,10 @@ __global__ void __launch_bounds__(U3_THREADS, 1)
 k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
         const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
         Umma3Args a) {
-  umma3_tile<MODE>(mA0, mA1, mB0, mB1, a, blockIdx.x, blockIdx.y, blockIdx.z);
+  // grid x = N tile fastest, then 128-row tile: the CTAs that share an A tile run together
+  // and A is fetched from DRAM once, the other N tiles hitting L2
+  const int nt = (int)blockIdx.x % a.ntiles, mt = (int)blockIdx.x / a.ntiles;
+  umma3_tile<MODE>(mA0, mA1, mB0, mB1, a, mt, blockIdx.y, nt);
 }
 
 // Batched form: problem blockIdx.y (one N tile, no split), 128-row tile blockIdx.x; CTAs past
@@ -402,6 +405,7 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
   a.BN = BN;
   a.kchunk = kchunk;
   a.stages = stages;
+  a.ntiles = ntiles;
   a.status = op.status;
   if (splits == 1 && op.out) {
     a.out = op.out;
@@ -416,7 +420,8 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
   }
   auto kern = k_umma3<MODE>;
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)ceil_div(op.M, U3_BM), (unsigned)splits, (unsigned)ntiles);
+  // x: (row tile, N tile) with the N tile fastest
+  dim3 grid((unsigned)(ceil_div(op.M, U3_BM) * ntiles), (unsigned)splits);
   kern<<<grid, U3_THREADS, smem, s>>>(m0, m1, n0, n1, a);
   RLU_TRY(last_launch_status());
   if (a.out == op.partial && op.out)
@@ -450,6 +455,7 @@ static int32_t make_job(const Umma3Op& op, U3Job* job, int* stage_bytes) {
   a.K = (int)op.K;
   a.BN = BN;
   a.kchunk = (int)round_up(op.K, U3_BK);
+  a.ntiles = 1;
   a.out = op.out;
   a.ldo = op.ldo;
   a.out_colmajor = op.out_colmajor;

@@ -129,9 +129,11 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
   const UbLayout lay = ub_layout(MODE, a.BN);
   const int S = a.stages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * UB_BM;
+  // grid x = (row tile, N tile), N tile fastest: the CTAs sharing an A tile run together and
+  // A is fetched from DRAM once, the other N tiles hitting L2
+  const int m0 = ((int)blockIdx.x / a.ntiles) * UB_BM;
   const int kz = blockIdx.y;
-  const int nb0 = blockIdx.z * a.BN;
+  const int nb0 = ((int)blockIdx.x % a.ntiles) * a.BN;
   const int k_begin = kz * a.kchunk;
   const int k_end = min(a.K, k_begin + a.kchunk);
   const int nk = (k_end - k_begin + UB_BK - 1) / UB_BK;
@@ -346,6 +348,7 @@ static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
   a.BN = BN;
   a.kchunk = kchunk;
   a.stages = stages;
+  a.ntiles = ntiles;
   a.status = op.status;
   if (splits == 1 && op.out) {
     a.out = op.out;
@@ -360,7 +363,7 @@ static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
   }
   auto kern = k_ummab<MODE>;
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)ceil_div(op.M, UB_BM), (unsigned)splits, (unsigned)ntiles);
+  dim3 grid((unsigned)(ceil_div(op.M, UB_BM) * ntiles), (unsigned)splits);
   kern<<<grid, UB_THREADS, smem, s>>>(mA, b0, b1, b2, a);
   RLU_TRY(last_launch_status());
   if (a.out == op.partial && op.out)
