@@ -266,35 +266,44 @@ def serve_requests(lam: float, secs: float, rng: np.random.Generator):
 
 def serve_run(lams, secs: float, seed: int = 7):
     """The serving form: requests arrive by a Poisson process and are submitted to the
-    server at their arrival times; latency = arrival -> completion (host clock)."""
+    server at their arrival times; latency = arrival -> completion (host clock). Half the
+    requests are FP32-accuracy (mixed path, FP32 A), half BF16-accuracy (BF16 A, the
+    precision form), drawn at random."""
     from paper_1310_7202_gb300 import rlu
 
-    pool = {}
+    pool, pool_bf = {}, {}
     for sz in SERVE_POOL:   # resident inputs, generated before any timing
         sigma = synth.spectrum("inv_1p5", sz)
         pool[sz] = synth.prescribed_matrix_torch(sz, sz, sigma, 31 + sz, 32 + sz, torch.float32)
+        pool_bf[sz] = pool[sz].to(torch.bfloat16)
     torch.cuda.synchronize()
     rng = np.random.default_rng(seed)
     res = {}
     srv = rlu.Server(budget_bytes=24 << 30, max_inflight=16)
     try:
-        # warm-up: one request per pool size
+        # warm-up: one request per pool size and class
         for sz in SERVE_POOL:
             srv.submit(pool[sz], 16, 26, 1, "mixed", m=sz, n=sz)
+            srv.submit(pool_bf[sz], 16, 26, 1, "bf16", m=sz, n=sz)
         srv.wait_all()
         for lam in lams:
             reqs = serve_requests(lam, secs, rng)
-            ids, t_arr = [], []
+            classes = rng.random(len(reqs)) < 0.5
+            ids, t_arr, cls = [], [], []
             t0 = time.perf_counter_ns()
             pending = []
-            for (ta, m, n, k, l) in reqs:
+            for (ta, m, n, k, l), bf in zip(reqs, classes):
                 target = t0 + int(ta * 1e9)
                 while time.perf_counter_ns() < target:
                     pass
                 sz = next(s for s in SERVE_POOL if s >= max(m, n))
-                rid = srv.submit(pool[sz], k, l, len(ids) + 1, "mixed", m=m, n=n)
+                if bf:
+                    rid = srv.submit(pool_bf[sz], k, l, len(ids) + 1, "bf16", m=m, n=n)
+                else:
+                    rid = srv.submit(pool[sz], k, l, len(ids) + 1, "mixed", m=m, n=n)
                 ids.append(rid)
                 t_arr.append(target)
+                cls.append("bf16" if bf else "fp32")
                 pending.append(rid)
                 if len(pending) > 64:   # let finished outputs go
                     keep = []
@@ -305,31 +314,58 @@ def serve_run(lams, secs: float, seed: int = 7):
                             keep.append(r)
                     pending = keep
             srv.wait_all()
-            lat, done_t, failed = [], [], 0
+            lat = {"all": [], "fp32": [], "bf16": []}
+            done_t, failed = [], 0
             # perf_counter_ns and the server's steady clock are the same monotonic clock on
             # Linux (CLOCK_MONOTONIC); latencies are differences on it
-            for rid, ta in zip(ids, t_arr):
+            for rid, ta, c in zip(ids, t_arr, cls):
                 st = srv.poll(rid)
                 srv.release(rid)
                 if st["state"] != rlu.RLU_REQ_DONE:
                     failed += 1
                     continue
-                lat.append((st["t_done"] - ta) / 1e6)
+                ms = (st["t_done"] - ta) / 1e6
+                lat["all"].append(ms)
+                lat[c].append(ms)
                 done_t.append(st["t_done"])
             span = (max(done_t) - t0) / 1e9 if done_t else float("nan")
+
+            def pct(v, q):
+                return float(np.percentile(v, q)) if v else None
             res[str(int(lam))] = {
                 "requests": len(ids), "failed": failed,
-                "p50_ms": float(np.percentile(lat, 50)) if lat else None,
-                "p99_ms": float(np.percentile(lat, 99)) if lat else None,
-                "throughput_req_s": len(lat) / span if lat else None}
+                "p50_ms": pct(lat["all"], 50), "p99_ms": pct(lat["all"], 99),
+                "fp32_class": {"p50_ms": pct(lat["fp32"], 50), "p99_ms": pct(lat["fp32"], 99)},
+                "bf16_class": {"p50_ms": pct(lat["bf16"], 50), "p99_ms": pct(lat["bf16"], 99)},
+                "throughput_req_s": len(lat["all"]) / span if lat["all"] else None}
         stats = srv.stats()
     finally:
         srv.close()
-    return {"lambdas": res, "arrival_window_s": secs, "class": "FP32-accuracy (mixed path)",
+    return {"lambdas": res, "arrival_window_s": secs,
+            "classes": "half FP32-accuracy (mixed path, FP32 A), half BF16-accuracy (BF16 A, "
+                       "precision form), drawn at random",
             "max_inflight": 16, "budget_GB": 24, "peak_running": stats["peak_running"],
             "peak_arena_GB": round(stats["peak_arena_bytes"] / 2 ** 30, 2),
+            "bypassed_admissions": stats["bypassed_admissions"],
             "inputs": "top-left m x n blocks of resident prescribed-spectrum matrices "
                       "(sigma_i = i^-1.5) of sizes " + ",".join(map(str, SERVE_POOL))}
+
+
+def run_serve(args):
+    """Serving form alone: the full arrival-rate sweep of the serving workload."""
+    lams = [float(x) for x in args.serve_lambdas.split(",") if x]
+    with ClockSampler(0) as clocks:
+        r = serve_run(lams, args.serve_secs)
+    top = r["lambdas"][str(int(max(lams)))]
+    line = {"metric": METRIC, "value": top["throughput_req_s"], "unit": "req/s", "n_gpus": 1,
+            "steps": len(lams), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "mixed+bf16", "data": "synthetic",
+            "config": {"workload": "serve: Poisson arrivals, m, n log-uniform [256, 16384], k "
+                                   "uniform [16, 256], l = k + 10, sigma_i = i^-1.5",
+                       "lambdas": lams, "window_s": args.serve_secs},
+            "serve": r, "clocks": clocks.summary(), "e2e": None, "cpu_baseline": None,
+            "gpu_launches": None, "roofline": None}
+    print(json.dumps(line))
 
 
 # ---------------------------------------------------------------------------------------
@@ -673,5 +709,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif synth.WORKLOADS[a.workload].get("kind") == "batch":
         run_batched(a)
+    elif synth.WORKLOADS[a.workload].get("kind") == "serve":
+        run_serve(a)
     else:
         run_ours(a)

@@ -108,6 +108,8 @@ WORKLOADS = {
     # batched form: 4096 problems, sizes from batch_shapes, sigma_i = exp(-i/k), FP32
     "batch4096": dict(kind="batch", count=4096, spectrum="exp_k", dtype="f32", seed_shapes=4,
                       seed_u=41, seed_g=5000),
+    # served form: Poisson arrivals (rates and window from the bench's --serve-* flags)
+    "serve": dict(kind="serve", spectrum="inv_1p5", dtype="mixed+bf16"),
 }
 
 
