@@ -16,6 +16,7 @@ struct Umma3Args {
   size_t split_stride;
   int M, N, K, BN, kchunk, stages;
   int ntiles;  // N tiles; grid x = row tiles x N tiles, the N tile varying fastest
+  int bn_last;  // MMA width of the last N tile (BF16 kernels)
   bool out_colmajor;
   int32_t* status;
 };

@@ -6,14 +6,19 @@
 //               contiguous); both arrive by TMA in 128-byte-swizzled K-major tiles. One
 //               product: the range finder only needs Y's column space, so BF16 A and G with
 //               FP32 accumulation suffice.
-//   UB_MODE_C3  C^T = A^T L~ (step 5): the A tile arrives n-contiguous and is transposed on
-//               chip into a K-major tile (A is exact in BF16, nothing to split); L~ comes as
-//               three BF16 parts hi + mid + lo (8 significant bits each, FP32 accurate), so
-//               three products A L_hi + A L_mid + A L_lo accumulate in FP32.
+//   UB_MODE_C3  C^T = A^T L~ (step 5): A is stored m x n row-major, so the operand A^T
+//               (M = n, K = m) is M-major; it arrives by TMA in 128-byte-swizzled boxes of
+//               64 (n) x 64 (m) and the MMA reads it as an MN-major operand (A is exact in
+//               BF16, nothing to split or transpose). L~ comes as three BF16 parts
+//               hi + mid + lo (8 significant bits each, FP32 accurate), so three products
+//               A L_hi + A L_mid + A L_lo accumulate in FP32.
+//
+// N tiles: BN columns each, the last one only as wide as the columns left (rounded up to
+// 16), so that no MMA work is spent on padding.
 //
 // Warp roles as in the TF32 kernels: warp 0 TMA producer over a ring of slots, warp 1 TMEM
-// allocation and MMA issue, warps 2..5 epilogue, warps 6..9 the transposing converter
-// (UB_MODE_C3). Every wait is bounded (~1 s) and records an error instead of hanging.
+// allocation and MMA issue, warps 2..5 epilogue. Every wait is bounded (~1 s) and records an
+// error instead of hanging.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -24,12 +29,11 @@ namespace rlu {
 
 static constexpr int UB_BM = 128;
 static constexpr int UB_BK = 64;  // BF16 elements: one 128-byte swizzle row
-static constexpr int UB_THREADS = 320;
+static constexpr int UB_THREADS = 192;
 static constexpr int UB_MAXST = 4;
 
 struct UbSmem {
   uint64_t full[UB_MAXST];
-  uint64_t conv[UB_MAXST];
   uint64_t empty[UB_MAXST];
   uint64_t accum;
   uint32_t tmem_base;
@@ -82,6 +86,13 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
          ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
+// MN-major operand in 128-byte-swizzled boxes of 64 (MN) x 64 (K): a row of the box holds 64
+// consecutive MN elements of one K index; groups of 8 K rows lie 1024 bytes apart (stride
+// offset) and the next 64 MN elements start one box (8192 bytes) further (leading offset).
+__device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(8192u >> 4) << 16) |
+         ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
                                          uint32_t acc) {
   asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -95,24 +106,25 @@ __device__ __forceinline__ void commit(uint32_t bar) {
 }  // namespace ub
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B BF16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t ub_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// (bits 7-9, 10-12 = 1), A MN-major if a_mn (bit 15), B K-major, N >> 3 at bit 17, M >> 4
+// at bit 24.
+__host__ __device__ constexpr uint32_t ub_idesc(int M, int N, bool a_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 struct UbLayout {
-  uint32_t a0, a2, b0, b1, b2, stage, tx;
+  uint32_t a0, b0, b1, b2, stage, tx;
 };
 __host__ __device__ inline UbLayout ub_layout(int mode, int BN) {
   UbLayout L{};
   const uint32_t at = UB_BM * 128, bt = (uint32_t)BN * 128;
-  if (mode == UB_MODE_Y) {  // a0: A, b0: G
-    L.a0 = 0; L.b0 = at; L.b1 = L.b2 = L.b0; L.a2 = 0; L.stage = at + bt; L.tx = at + bt;
-  } else {                  // a2: raw A (64 x 128, n contiguous), a0: K-major A, b0..b2: L~
-    L.a2 = 0; L.a0 = at; L.b0 = 2 * at; L.b1 = 2 * at + bt; L.b2 = 2 * at + 2 * bt;
-    L.stage = 2 * at + 3 * bt; L.tx = at + 3 * bt;
+  if (mode == UB_MODE_Y) {  // a0: A (K-major), b0: G
+    L.a0 = 0; L.b0 = at; L.b1 = L.b2 = L.b0; L.stage = at + bt;
+  } else {                  // a0: A^T as two MN-major 64 x 64 boxes, b0..b2: L~ parts
+    L.a0 = 0; L.b0 = at; L.b1 = at + bt; L.b2 = at + 2 * bt; L.stage = at + 3 * bt;
   }
+  L.tx = L.stage;
   L.stage = (L.stage + 1023u) & ~1023u;
   return L;
 }
@@ -133,16 +145,16 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
   // A is fetched from DRAM once, the other N tiles hitting L2
   const int m0 = ((int)blockIdx.x / a.ntiles) * UB_BM;
   const int kz = blockIdx.y;
-  const int nb0 = ((int)blockIdx.x % a.ntiles) * a.BN;
+  const int nt = (int)blockIdx.x % a.ntiles;
+  const int nb0 = nt * a.BN;
+  const int bn = nt == a.ntiles - 1 ? a.bn_last : a.BN;  // this tile's MMA width
   const int k_begin = kz * a.kchunk;
   const int k_end = min(a.K, k_begin + a.kchunk);
   const int nk = (k_end - k_begin + UB_BK - 1) / UB_BK;
-  constexpr bool CONV = (MODE == UB_MODE_C3);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mb_init(su32(&sh.full[s]), 1);
-      mb_init(su32(&sh.conv[s]), 128);
       mb_init(su32(&sh.empty[s]), 1);
     }
     mb_init(su32(&sh.accum), 1);
@@ -169,13 +181,17 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
       }
       const uint32_t base = tiles + s * lay.stage;
       const uint32_t bar = su32(&sh.full[s]);
-      mb_expect_tx(bar, lay.tx);
       const int kx = k_begin + kt * UB_BK;
       if (MODE == UB_MODE_Y) {
+        // the last N tile loads only its bn rows of G (map B1 has a box of bn_last rows)
+        const bool narrow = bn < a.BN;
+        mb_expect_tx(bar, narrow ? lay.tx - (uint32_t)(a.BN - bn) * 128u : lay.tx);
         tma2d(base + lay.a0, &mA, kx, m0, bar);
-        tma2d(base + lay.b0, &mB0, kx, nb0, bar);
+        tma2d(base + lay.b0, narrow ? &mB1 : &mB0, kx, nb0, bar);
       } else {
-        tma2d(base + lay.a2, &mA, m0, kx, bar);  // raw A: x = n (128 wide), y = m (64)
+        mb_expect_tx(bar, lay.tx);
+        tma2d(base + lay.a0, &mA, m0, kx, bar);  // A^T: x = n (64 wide), y = m (64)
+        tma2d(base + lay.a0 + 8192u, &mA, m0 + 64, kx, bar);
         tma2d(base + lay.b0, &mB0, kx, nb0, bar);
         tma2d(base + lay.b1, &mB1, kx, nb0, bar);
         tma2d(base + lay.b2, &mB2, kx, nb0, bar);
@@ -183,11 +199,11 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: 4 MMAs of K = 16 per 64-wide slot ---------------------------------
-    const uint32_t idesc = ub_idesc(UB_BM, a.BN);
+    const uint32_t idesc = ub_idesc(UB_BM, bn, MODE == UB_MODE_C3);
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % S;
       const uint32_t par = (uint32_t)((kt / S) & 1);
-      if (!mb_wait(su32(CONV ? &sh.conv[s] : &sh.full[s]), par)) {
+      if (!mb_wait(su32(&sh.full[s]), par)) {
         sh.err = 1;
         break;
       }
@@ -195,8 +211,10 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
       const uint32_t base = tiles + s * lay.stage;
 #pragma unroll
       for (int kk = 0; kk < UB_BK / 16; ++kk) {
-        const uint32_t off = kk * 32;
-        const uint64_t da = desc_sw128(base + lay.a0 + off);
+        const uint32_t off = kk * 32;  // 16 K elements along a K-major row
+        // MN-major A: 16 K rows further (two 8-row groups)
+        const uint64_t da = MODE == UB_MODE_C3 ? desc_mn_sw128(base + lay.a0 + kk * 2048u)
+                                               : desc_sw128(base + lay.a0 + off);
         mma_bf16(tmem, da, desc_sw128(base + lay.b0 + off), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
         if (MODE == UB_MODE_C3) {
           mma_bf16(tmem, da, desc_sw128(base + lay.b1 + off), idesc, 1u);
@@ -214,7 +232,7 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
     const int quarter = warp & 3;
     const int row = m0 + quarter * 32 + lane;
     float* __restrict__ out = a.out + (size_t)kz * a.split_stride;
-    for (int c0 = 0; c0 < a.BN; c0 += 32) {
+    for (int c0 = 0; c0 < bn; c0 += 32) {
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
       asm volatile(
@@ -233,7 +251,7 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = nb0 + c0 + j;
-          if (c0 + j < a.BN && col < a.N) {
+          if (c0 + j < bn && col < a.N) {
             const float f = __uint_as_float(v[j]);
             if (a.out_colmajor)
               out[(size_t)col * a.ldo + row] = f;
@@ -242,32 +260,6 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
           }
         }
       }
-    }
-  } else if (CONV && warp >= 6) {
-    // ---- converter: thread r builds K-major row r (128 bytes = 8 chunks of 8 BF16) of the
-    // A tile from column r of the raw 64 x 128 tile; chunk c goes to position c ^ (r & 7)
-    const int r = threadIdx.x - 192;  // 0..127
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % S;
-      if (!mb_wait(su32(&sh.full[s]), (uint32_t)((kt / S) & 1))) {
-        sh.err = 1;
-        break;
-      }
-      const uint32_t base = tiles + s * lay.stage;
-      const uint16_t* raw =
-          reinterpret_cast<const uint16_t*>(ub_smem + (base + lay.a2 - su32(ub_smem)));
-      unsigned char* dst = ub_smem + (base + lay.a0 - su32(ub_smem)) + r * 128;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        uint32_t w[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          w[j] = (uint32_t)raw[(8 * c + 2 * j) * UB_BM + r] |
-                 ((uint32_t)raw[(8 * c + 2 * j + 1) * UB_BM + r] << 16);
-        *reinterpret_cast<uint4*>(dst + 16 * (c ^ (r & 7))) = make_uint4(w[0], w[1], w[2], w[3]);
-      }
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      mb_arrive(su32(&sh.conv[s]));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -316,6 +308,7 @@ static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
   const int bnmax = MODE == UB_MODE_Y ? 256 : 128;
   const int BN = op.N > bnmax ? bnmax : (int)round_up(op.N, 16);
   const int ntiles = (int)ceil_div(op.N, BN);
+  const int bn_last = (int)round_up(op.N - (int64_t)(ntiles - 1) * BN, 16);
   const UbLayout lay = ub_layout(MODE, BN);
   int dev = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
@@ -330,10 +323,11 @@ static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
   if (MODE == UB_MODE_Y) {
     RLU_TRY(map2d_bf16(&mA, op.A, op.M, op.K, op.lda, UB_BK, UB_BM, true));
     RLU_TRY(map2d_bf16(&b0, op.B0, op.N, op.K, op.ldb, UB_BK, BN, true));
-    b1 = b2 = b0;
+    RLU_TRY(map2d_bf16(&b1, op.B0, op.N, op.K, op.ldb, UB_BK, bn_last, true));
+    b2 = b0;
   } else {
-    // A stored row-major K x M (rows = K index, M contiguous): box 128 (M) x 64 (K)
-    RLU_TRY(map2d_bf16(&mA, op.A, op.K, op.M, op.lda, UB_BM, UB_BK, false));
+    // A stored row-major K x M (rows = K index, M contiguous): swizzled boxes 64 (M) x 64 (K)
+    RLU_TRY(map2d_bf16(&mA, op.A, op.K, op.M, op.lda, 64, UB_BK, true));
     RLU_TRY(map2d_bf16(&b0, op.B0, op.N, op.K, op.ldb, UB_BK, BN, true));
     RLU_TRY(map2d_bf16(&b1, op.B1, op.N, op.K, op.ldb, UB_BK, BN, true));
     RLU_TRY(map2d_bf16(&b2, op.B2, op.N, op.K, op.ldb, UB_BK, BN, true));
@@ -349,6 +343,7 @@ static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
   a.kchunk = kchunk;
   a.stages = stages;
   a.ntiles = ntiles;
+  a.bn_last = bn_last;
   a.status = op.status;
   if (splits == 1 && op.out) {
     a.out = op.out;
