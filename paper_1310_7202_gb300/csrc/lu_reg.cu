@@ -5,7 +5,11 @@
 //
 // One launch factors one panel of up to NB-1 columns; the positions of the rows persist in
 // global memory between launches, and k_lu_trail (all SMs) applies each panel's rank-w
-// update to the remaining columns. Each thread owns RT rows; the panel's part of each row
+// update to the remaining columns. Narrow panels (tall X, several rows per thread) are
+// grouped into blocks of about 64 columns, a right-looking blocked LU: a panel's update
+// reaches only the rest of its block, and each block's pivot rows are solved (k_lu_u12)
+// and its rank-64 update applied to the columns after the block once, so that the
+// trailing columns are read and written once per block rather than once per panel. Each thread owns RT rows; the panel's part of each row
 // lives in registers and shifts by one register per step, so the rank-1 update is
 // register-to-register. The
 // per-step exchange avoids cluster barriers: every CTA reduces its candidates (warp
@@ -413,7 +417,8 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
   // all records of this panel consumed before anyone reuses receive slots / exits; the
   // panel's columns are final in global memory for the whole cluster
   cl.sync();
-  if (p0 + w < C) {
+  const int cu = a.cu > 0 ? a.cu : C;
+  if (p0 + w < cu) {
     // ---- U12 of the pivot rows for the trailing columns (forward substitution) -----------
     for (int e = tid; e < w * w; e += NT) {
       const int t = e / w, s = e % w;
@@ -421,7 +426,7 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
       L11[t * NB + s] = pr >= 0 ? X[(int64_t)(p0 + s) * ldx + pr] : T(0);
     }
     __syncthreads();
-    for (int c = p0 + w + crank * NW + warp; c < C; c += ncta * NW) {
+    for (int c = p0 + w + crank * NW + warp; c < cu; c += ncta * NW) {
       constexpr int NQ = (NB + 31) / 32;
       T u[NQ], fin[NQ];
 #pragma unroll
@@ -529,6 +534,58 @@ __global__ void __launch_bounds__(256) k_lu_trail(T* __restrict__ X, int64_t ldx
     if (q < cw) X[(int64_t)(c0 + q) * ldx + r] = acc[q];
 }
 
+// Pivot rows of a block of W <= 96 columns [o0, o0 + W), for the columns [c_begin, c_end):
+// u = L11^-1 x over the block's pivot rows (forward substitution; L11[t][s] = X[o0 + s] at
+// the row of position o0 + t, unit diagonal for Doolittle; Crout divides by the diagonal).
+// One warp per column; L11 in shared memory.
+template <typename T, bool CROUT>
+__global__ void __launch_bounds__(256) k_lu_u12(T* __restrict__ X, int64_t ldx, int o0, int W,
+                                               int c_begin, int c_end,
+                                               const int32_t* __restrict__ psg) {
+  extern __shared__ __align__(16) unsigned char u12_smem[];
+  T* L11 = reinterpret_cast<T*>(u12_smem);           // [W][W]
+  int* prow = reinterpret_cast<int*>(L11 + W * W);   // [W]
+  for (int t = threadIdx.x; t < W; t += blockDim.x) prow[t] = psg[o0 + t];
+  __syncthreads();
+  for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
+    const int t = e / W, s = e % W;
+    L11[e] = prow[t] >= 0 ? X[(int64_t)(o0 + s) * ldx + prow[t]] : T(0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int c = c_begin + (int)blockIdx.x * (blockDim.x / 32) + (int)(threadIdx.x >> 5);
+  if (c >= c_end) return;
+  constexpr int NQ = 3;  // W <= 96
+  T u[NQ], fin[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int t = lane + 32 * q;
+    u[q] = (t < W && prow[t] >= 0) ? X[(int64_t)c * ldx + prow[t]] : T(0);
+    fin[q] = u[q];
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    for (int s = 32 * q; s < min(W, 32 * q + 32); ++s) {
+      T us = __shfl_sync(0xffffffffu, u[q], s - 32 * q);
+      if (CROUT) {
+        const T pv = L11[s * W + s];
+        if (pv != T(0)) us = us * rcp_piv(pv);
+      }
+      if (lane == s - 32 * q) fin[q] = us;
+#pragma unroll
+      for (int qq = q; qq < NQ; ++qq) {
+        const int t = lane + 32 * qq;
+        if (t > s && t < W) u[qq] = fma(-L11[t * W + s], us, u[qq]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int t = lane + 32 * q;
+    if (t < W && prow[t] >= 0) X[(int64_t)c * ldx + prow[t]] = fin[q];
+  }
+}
+
 template <typename T, int NB, int NT>
 static size_t lr_smem_bytes(int rpc, int C) {
   size_t b = (sizeof(LrShared<T, NB, NT / 32>) + 15) / 16 * 16;
@@ -577,16 +634,38 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
   LuArgs a = in;
   a.rpc = rpc;
   a.nb = NB - 1;
-  for (int p0 = 0; p0 < in.C; p0 += NB - 1) {
-    a.p0 = p0;
-    a.pw = min(NB - 1, in.C - p0);
-    RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
-    RLU_TRY(last_launch_status());
-    *launched = true;
-    if (p0 + a.pw < in.C) {
-      const dim3 grid((unsigned)ceil_div(in.R, 256), (unsigned)ceil_div(in.C - p0 - a.pw, LR_CH));
-      k_lu_trail<T><<<grid, 256, 0, s>>>(static_cast<T*>(in.X), in.ldx, in.R, in.C, p0, a.pw,
-                                         in.posg, in.psg);
+  // blocks of whole panels, about 64 columns (panels of 64 or more columns: one block);
+  // a block's L11 (W x W) must fit k_lu_u12's 48 KB of shared memory and W <= 96
+  const int pw_max = NB - 1;
+  int np = (64 + pw_max / 2) / pw_max;
+  while (np > 1 && (np * pw_max > 96 ||
+                    sizeof(T) * (size_t)(np * pw_max) * (np * pw_max) + 4 * (np * pw_max) > 48 * 1024))
+    --np;
+  const int wo = pw_max >= 64 ? in.C : np * pw_max;
+  T* X = static_cast<T*>(in.X);
+  for (int o0 = 0; o0 < in.C; o0 += wo) {
+    const int o1 = min(in.C, o0 + wo);
+    for (int p0 = o0; p0 < o1; p0 += pw_max) {
+      a.p0 = p0;
+      a.pw = min(pw_max, o1 - p0);
+      a.cu = o1;
+      RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
+      RLU_TRY(last_launch_status());
+      *launched = true;
+      if (p0 + a.pw < o1) {
+        const dim3 grid((unsigned)ceil_div(in.R, 256), (unsigned)ceil_div(o1 - p0 - a.pw, LR_CH));
+        k_lu_trail<T><<<grid, 256, 0, s>>>(X, in.ldx, in.R, o1, p0, a.pw, in.posg, in.psg);
+        RLU_TRY(last_launch_status());
+      }
+    }
+    if (o1 < in.C) {
+      const int W = o1 - o0;  // <= 96
+      const size_t ub = sizeof(T) * (size_t)W * W + sizeof(int) * (size_t)W;
+      k_lu_u12<T, CROUT><<<(unsigned)ceil_div(in.C - o1, 8), 256, ub, s>>>(X, in.ldx, o0, W, o1,
+                                                                          in.C, in.psg);
+      RLU_TRY(last_launch_status());
+      const dim3 grid((unsigned)ceil_div(in.R, 256), (unsigned)ceil_div(in.C - o1, LR_CH));
+      k_lu_trail<T><<<grid, 256, 0, s>>>(X, in.ldx, in.R, in.C, o0, W, in.posg, in.psg);
       RLU_TRY(last_launch_status());
     }
   }

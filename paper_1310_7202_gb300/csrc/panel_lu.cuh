@@ -20,6 +20,7 @@ struct LuArgs {
   int32_t* psg;        // [C] row at each position < C
   int p0;              // first column of the panel of this launch
   int pw;              // its width
+  int cu;              // the launch solves the pivot rows of columns [p0 + pw, cu) (0: C)
 };
 
 // crout = false: Doolittle (step 3, LU of Y); crout = true: pivot row scaled (step 6 on B^T).

@@ -108,6 +108,24 @@ def test_fp64_deterministic(fp64_512):
 ])
 def test_fp64_shapes(m, n, k, l):
     A = synth.lowrank_plus_noise(m, n, min(60, min(m, n)), 1e-6, seed=m + n)
+    _check_fp64(A, k, l)
+
+
+@pytest.mark.parametrize("m,n,k,l", [
+    (3000, 400, 90, 100),     # 1 row per thread: blocks of two 36-column panels (Y and B^T)
+    (12000, 300, 60, 100),    # 2 rows per thread: blocks of four 18-column panels
+    (20000, 300, 60, 130),    # 4 rows per thread: blocks of eleven 6-column panels
+    (300, 20000, 90, 100),    # B^T with 4 rows per thread (Crout form), two blocks
+])
+def test_fp64_blocked_panels(m, n, k, l):
+    """Panels grouped into column blocks: within a block each panel updates the rest of the
+    block; the block's pivot rows are then solved and its update applied to the columns
+    after it. A full-rank Gaussian A keeps every one of the l steps on signal."""
+    A = np.random.default_rng(m + 7 * n).standard_normal((m, n))
+    _check_fp64(A, k, l)
+
+
+def _check_fp64(A, k, l):
     g = run_gpu(A, k, l, 3, "f64")
     o = oracle_for(A, k, l, 3, "f64")
     assert np.array_equal(g["G"], o["G"])
@@ -191,9 +209,11 @@ def test_fp32_error_within_tolerance(m, n, k, l):
     assert abs(fro_d.item() - fro_g) <= 1e-9 * fro_g
 
 
-@pytest.mark.parametrize("m,n,k,l", [(12000, 300, 30, 40), (20000, 300, 30, 40)])
+@pytest.mark.parametrize("m,n,k,l", [(12000, 300, 30, 40), (20000, 300, 30, 40),
+                                     (20000, 400, 80, 150), (400, 16000, 100, 110)])
 def test_fp32_tall_register_configs(m, n, k, l):
-    """Y taller than one row per thread of a 16-CTA cluster: 2 and 4 rows per thread."""
+    """Y (or B^T) taller than one row per thread of a 16-CTA cluster: 2 and 4 rows per
+    thread, with l = 150 (Y) and k = 100 (B^T) spanning several column blocks."""
     A, g, o, sigma = _fp32_case(m, n, k, l, "inv_square", 2)
     fro_o, _ = O.reconstruct_error(A, o["P"], o["Q"], o["L"], o["U"], spectral=False)
     fro_g, _ = O.reconstruct_error(A, g["P"], g["Q"], g["L"], g["U"], spectral=False)
