@@ -300,6 +300,61 @@ __device__ __forceinline__ void ldl_cols(float (&a)[LB], int lane, float* d_out,
   (ldl_col<ts>(a, lane, d_out, bad), ...);
 }
 
+// One warp: LDL^T of the 32 x 32 block BJJ in place (L unit lower, zero above), D into dJ
+// and W = L^{-1} (row-major, padded rows) into W, as in ldl32_body. Returns true in the
+// lanes whose pivot was not positive and finite.
+__device__ __forceinline__ bool ldl_diag_block(float* BJJ, float* dJ, float* W, int lane) {
+  float a[LB];
+#pragma unroll
+  for (int c = 0; c < LB; ++c) a[c] = BJJ[lane * LBP + c];
+  bool bad = false;
+  ldl_cols(a, lane, dJ, bad, std::make_integer_sequence<int, LB>{});
+#pragma unroll
+  for (int c = 0; c < LB; ++c) BJJ[lane * LBP + c] = (c < lane) ? a[c] : (c == lane ? 1.f : 0.f);
+  __syncwarp();
+  // W = L^{-1}: lane i holds row i; row t is final at step t
+  float w[LB];
+#pragma unroll
+  for (int c = 0; c < LB; ++c) w[c] = (c == lane) ? 1.f : 0.f;
+#pragma unroll
+  for (int t = 0; t < LB; ++t) {
+    const float lit = (lane > t) ? BJJ[lane * LBP + t] : 0.f;
+#pragma unroll
+    for (int c = 0; c <= t; ++c) {
+      const float wtc = __shfl_sync(0xffffffffu, w[c], t);
+      w[c] = fmaf(-lit, wtc, w[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < LB; ++c) W[lane * LBP + c] = (c <= lane) ? w[c] : 0.f;
+  __syncwarp();
+  return bad;
+}
+
+// C (32 x 32 block) -= A B^T for 32 x 32 blocks A, B (padded rows), one 4 x 4 register tile
+// (tile 0..63) per call.
+__device__ __forceinline__ void gemm_nt_tile(float* C, const float* A, const float* B, int tile) {
+  const int r0 = (tile / 8) * 4, c0 = (tile % 8) * 4;
+  float acc[4][4] = {};
+#pragma unroll 8
+  for (int t = 0; t < LB; ++t) {
+    float lv[4], uv[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      lv[x] = A[(r0 + x) * LBP + t];
+      uv[x] = B[(c0 + x) * LBP + t];
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(lv[x], uv[y], acc[x][y]);
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) C[(r0 + x) * LBP + c0 + y] -= acc[x][y];
+}
+
 __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
                                            const LdlOut<float>& o, int32_t* __restrict__ status) {
   extern __shared__ __align__(16) float l32_smem[];
@@ -489,6 +544,200 @@ static int32_t ldl_cluster_f64(double* M, int k, double* dinv, int32_t* status, 
   return last_launch_status();
 }
 
+// FP32 LDL^T for k <= 512 on a thread-block cluster of nc <= 8 CTAs: the blocked
+// algorithm of k_ldl32 with the block rows of the lower triangle dealt round-robin (row I
+// to CTA I mod nc, blocks (I, 0..I) in its shared memory). Block step J:
+//   the owner of row J factors the diagonal block (one warp): D_J, L_JJ, W_J = L_JJ^{-1};
+//   cluster barrier; every CTA copies W_J and D_J and forms U_IJ = M_IJ W_J^T and
+//     L_IJ = U_IJ D_J^{-1} for its rows I > J;
+//   cluster barrier; every CTA copies the U_KJ it needs (K > J) from their owners and
+//     updates its blocks M_IK -= L_IJ U_KJ^T (I >= K > J).
+// Two cluster barriers per block step; the trailing work is spread over the cluster.
+static constexpr int LC_NT = 512;
+static constexpr int LC_MAXB = 16;  // k <= 512
+static constexpr int LC_BS = LB * LBP;
+
+__host__ __device__ __forceinline__ int lc_mine(int nb, int me, int nc) {
+  return (nb - me + nc - 1) / nc;
+}
+// blocks held before owned row q (rows me, me + nc, ...: row I holds I + 1 blocks)
+__host__ __device__ __forceinline__ int lc_row_off(int q, int me, int nc) {
+  return q * (me + 1) + nc * q * (q - 1) / 2;
+}
+
+__global__ void __launch_bounds__(LC_NT, 1) k_ldl32c(const double* __restrict__ M, int k,
+                                                    LdlOut<float> o,
+                                                    int32_t* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int nc = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (k + LB - 1) / LB;
+  const int mine = lc_mine(nb, me, nc);
+  // the same layout in every CTA (remote addresses are mapped from local ones): room for
+  // the largest row set and the most rows of any CTA
+  int most = 0;
+  for (int c = 0; c < nc; ++c) most = max(most, lc_row_off(lc_mine(nb, c, nc), c, nc));
+  const int mmax = lc_mine(nb, 0, nc);
+  extern __shared__ __align__(16) float lc_smem[];
+  float* Rw = lc_smem;                     // owned rows' blocks
+  float* Ub = Rw + (size_t)most * LC_BS;   // [mmax] U_IJ of the owned rows I > J
+  float* Uf = Ub + (size_t)mmax * LC_BS;   // [nb] U_KJ of this step, fetched
+  float* Wo = Uf + (size_t)nb * LC_BS;     // W_J when this CTA owns row J
+  float* Wf = Wo + LC_BS;                  // W_J of this step, fetched
+  float* dd = Wf + LC_BS;                  // [nb * LB] D
+  __shared__ int s_bad;
+  if (tid == 0) s_bad = 0;
+  auto blk = [&](int q, int K) { return Rw + (size_t)(lc_row_off(q, me, nc) + K) * LC_BS; };
+
+  for (int q = 0; q < mine; ++q) {
+    const int I = me + q * nc;
+    float* R = blk(q, 0);
+    const int ne = (I + 1) * LB * LB;
+    for (int e0 = tid; e0 < ne; e0 += LC_NT * 4) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * LC_NT;
+        const int K = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
+        const int i = I * LB + r, j = K * LB + c;
+        v[u] = (e < ne && i < k && j < k) ? (float)M[(int64_t)i * k + j] : (i == j ? 1.f : 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * LC_NT;
+        const int K = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
+        if (e < ne) R[(size_t)K * LC_BS + r * LBP + c] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  const int imax = me + (mine - 1) * nc;  // last owned row (mine >= 1: nc <= nb)
+
+  for (int J = 0; J < nb; ++J) {
+    const int ow = J % nc;
+    if (me == ow && warp == 0) {
+      const int q = (J - me) / nc;
+      const bool bad = ldl_diag_block(blk(q, J), dd + J * LB, Wo, lane);
+      if (bad && J * LB + lane < k) s_bad = 1;
+      for (int e = lane; e < LB * LB; e += 32) {  // W_J and its transpose for the solves
+        const int r = e / LB, c = e % LB;
+        o.W[(size_t)J * LB * LB + e] = Wo[r * LBP + c];
+        o.WT[(size_t)J * LB * LB + e] = Wo[c * LBP + r];
+      }
+    }
+    cluster_arrive();
+    cluster_wait();
+    {
+      const float* src = cl.map_shared_rank(Wo, ow);
+      for (int e = tid; e < LC_BS; e += LC_NT) Wf[e] = src[e];
+      if (me != ow && tid < LB) dd[J * LB + tid] = cl.map_shared_rank(dd, ow)[J * LB + tid];
+    }
+    __syncthreads();
+    // U_IJ = M_IJ W_J^T for the owned rows I > J
+    const int q0 = (J < me) ? 0 : (J - me) / nc + 1;  // first owned row below J
+    for (int q = q0; q < mine; ++q) {
+      const float* Mr = blk(q, J);
+      float* U = Ub + (size_t)q * LC_BS;
+      for (int e = tid; e < LB * LB; e += LC_NT) {
+        const int r = e / LB, c = e % LB;
+        float acc = 0.f;
+#pragma unroll
+        for (int t = 0; t < LB; ++t) acc = fmaf(Mr[r * LBP + t], Wf[c * LBP + t], acc);
+        U[r * LBP + c] = acc;
+      }
+    }
+    __syncthreads();
+    for (int q = q0; q < mine; ++q) {  // L_IJ = U_IJ D_J^{-1} in place
+      float* Lr = blk(q, J);
+      const float* U = Ub + (size_t)q * LC_BS;
+      for (int e = tid; e < LB * LB; e += LC_NT) {
+        const int r = e / LB, c = e % LB;
+        Lr[r * LBP + c] = U[r * LBP + c] / dd[J * LB + c];
+      }
+    }
+    cluster_arrive();
+    cluster_wait();
+    if (imax > J) {  // fetch U_KJ, J < K <= imax, from the owners of rows K
+      const int nf = (imax - J) * LC_BS;
+      for (int e = tid; e < nf; e += LC_NT) {
+        const int K = J + 1 + e / LC_BS, x = e % LC_BS;
+        const int own = K % nc;
+        Uf[(size_t)K * LC_BS + x] = cl.map_shared_rank(Ub, own)[(size_t)((K - own) / nc) * LC_BS + x];
+      }
+    }
+    __syncthreads();
+    for (int q = q0; q < mine; ++q) {  // M_IK -= L_IJ U_KJ^T, J < K <= I
+      const int I = me + q * nc;
+      const float* Lr = blk(q, J);
+      const int ntask = (I - J) * 64;
+      for (int t = tid; t < ntask; t += LC_NT) {
+        const int K = J + 1 + t / 64;
+        gemm_nt_tile(blk(q, K), Lr, Uf + (size_t)K * LC_BS, t % 64);
+      }
+    }
+    __syncthreads();
+  }
+  // the owned rows of L (unit lower, zero above, identity past k) in both layouts, 1/D
+  const int kp = o.kp;
+  for (int q = 0; q < mine; ++q) {
+    const int I = me + q * nc;
+    for (int e = tid; e < LB * kp; e += LC_NT) {
+      const int r = e / kp, c = e % kp, i = I * LB + r;
+      if (i >= kp) continue;
+      float v = 0.f;
+      if (i > c) v = blk(q, c / LB)[(r)*LBP + c % LB];
+      else if (i == c) v = 1.f;
+      o.LR[(size_t)i * kp + c] = v;
+      o.LT[(size_t)c * kp + i] = v;
+    }
+    for (int r = tid; r < LB; r += LC_NT) {
+      const int i = I * LB + r;
+      if (i < k) o.dinv[i] = 1.0 / (double)dd[i];
+    }
+  }
+  if (tid == 0 && s_bad && status) *status = RLU_EINVAL;
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+static size_t ldl32c_smem_bytes(int k, int nc) {
+  const int nb = (k + LB - 1) / LB;
+  int most = 0, mmax = 0;
+  for (int me = 0; me < nc; ++me) {
+    const int mine = lc_mine(nb, me, nc);
+    most = std::max(most, lc_row_off(mine, me, nc));
+    mmax = std::max(mmax, mine);
+  }
+  return sizeof(float) * ((size_t)(most + mmax + nb + 2) * LC_BS + (size_t)nb * LB);
+}
+
+static int32_t ldl32_cluster(const double* M, int k, const LdlOut<float>& o, int32_t* status,
+                             cudaStream_t s) {
+  const int nb = (k + LB - 1) / LB;
+  const int nc = nb < 8 ? nb : 8;
+  const size_t bytes = ldl32c_smem_bytes(k, nc);
+  int dev = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  int optin = 0;
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (bytes + 1024 > (size_t)optin) return RLU_EUNSUPPORTED;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_ldl32c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(nc);
+  cfg.blockDim = dim3(LC_NT);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_ldl32c, M, k, o, status));
+  return last_launch_status();
+}
+
 template <typename T>
 int32_t ldl_factor(double* M, int k, const LdlOut<T>& o, int32_t* status, cudaStream_t s) {
   if (sizeof(T) == sizeof(float) && k <= L32_MAXB * LB) {
@@ -497,6 +746,8 @@ int32_t ldl_factor(double* M, int k, const LdlOut<T>& o, int32_t* status, cudaSt
     k_ldl32<<<1, L32_NT, bytes, s>>>(M, k, reinterpret_cast<const LdlOut<float>&>(o), status);
     return last_launch_status();
   }
+  if (sizeof(T) == sizeof(float) && k <= LC_MAXB * LB)
+    return ldl32_cluster(M, k, reinterpret_cast<const LdlOut<float>&>(o), status, s);
   RLU_TRY(ldl_cluster_f64(M, k, o.dinv, status, s));
   k_diag_inv<T><<<(unsigned)ceil_div(k, TB), 32, 0, s>>>(M, k, o);
   return last_launch_status();

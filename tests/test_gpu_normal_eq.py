@@ -1,9 +1,9 @@
 """Step 5 of Algorithm 1 on its own: B = L_y^+ P A through the normal equations (Gram
 matrix, LDL^T factorization, blocked triangular solves), checked against an FP64
 least-squares solve with the GPU's own L_y and P, so that pivot choices of the earlier
-steps do not enter. The FP32 LDL^T on one CTA serves k <= 256; larger k take the FP64
-cluster factorization; the FP64 path at k = 400 takes the narrow-block triangular solve.
-GPU only."""
+steps do not enter. The FP32 LDL^T runs on one CTA for k <= 256 and on a cluster of up to
+8 CTAs for 256 < k <= 512; the FP64 path takes the FP64 cluster factorization (at k = 400
+also the narrow-block triangular solve). GPU only."""
 import numpy as np
 import pytest
 
@@ -29,7 +29,9 @@ def _case(m, n, k, l, prec, seed):
     (2000, 1500, 200, 210, "f32"),    # FP32 LDL^T on one CTA, 7 diagonal blocks, ragged
     (2000, 1500, 200, 210, "mixed"),  # tensor-core Gram and C
     (1200, 1000, 256, 260, "f32"),    # the largest k of the one-CTA factorization
-    (1200, 1000, 300, 310, "f32"),    # FP64 cluster LDL^T, FP32 triangular solves
+    (1200, 1000, 300, 310, "f32"),    # FP32 cluster LDL^T: 10 block rows on 8 CTAs
+    (1000, 900, 257, 265, "mixed"),   # the smallest cluster case: a 1-wide last block
+    (1500, 1200, 512, 520, "f32"),    # the largest: 16 block rows, two per CTA
     (700, 650, 33, 40, "f32"),        # one full block and a 1-wide tail
 ])
 def test_normal_equations_single(m, n, k, l, prec):
