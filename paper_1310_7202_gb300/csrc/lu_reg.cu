@@ -455,6 +455,7 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
       for (int q = 0; q < NQ; ++q) {
         const int t = lane + 32 * q;
         if (t < w && prows[t] >= 0) X[(int64_t)c * ldx + prows[t]] = fin[q];
+        if (t < w) static_cast<T*>(a.u12)[(int64_t)t * a.ldu + c] = prows[t] >= 0 ? fin[q] : T(0);
       }
     }
   }
@@ -491,47 +492,135 @@ __global__ void __launch_bounds__(NT, 1) k_lu_reg_batched(const LuArgs* __restri
   lu_reg_body<T, CROUT, RT, NB, NT>(table[blockIdx.x / csize]);
 }
 
-// Rank-w update of the trailing columns [c_begin, C) of every row whose position is at
-// least p0 + w: X[r][c] -= sum_s X[r][p0+s] * U12[s][c], U12 = the panel's pivot rows
-// (already solved by the panel launch). One thread per row, 32 columns per CTA.
+// Asynchronous global -> shared copies (cp.async): 16 bytes, or one element.
+__device__ __forceinline__ void lr_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n"
+               ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void lr_cp(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n"
+               ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void lr_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void lr_cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Rank-w update (w <= 96) of the columns [c_begin, c_end) of every row whose position is at
+// least p0 + w: X[r][c] -= sum_s X[r][p0 + s] U[s][c], U = the solved pivot rows, dense in
+// u12 (row s at u12 + s * ldu). A CTA takes 256 rows (128 threads, 2 rows each) and nch
+// chunks of 32 columns. Its rows' multipliers are copied to shared memory once and each
+// chunk of U while the previous chunk is computed (cp.async, many copies in flight); every
+// thread keeps 2 x 32 accumulators in registers. vec: X's columns start on 16-byte
+// boundaries, so the multipliers move in 16-byte copies.
+static constexpr int TR_T = 128;
+static constexpr int TR_R = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_lu_trail(T* __restrict__ X, int64_t ldx, int R, int C,
-                                                 int p0, int w, const int32_t* __restrict__ posg,
-                                                 const int32_t* __restrict__ psg) {
-  __shared__ __align__(16) T U12[128 + 16][LR_CH];
-  const int c0 = p0 + w + blockIdx.y * LR_CH;
-  const int cw = min(LR_CH, C - c0);
-  const int wpad = (w + 15) / 16 * 16;
-  for (int e = threadIdx.x; e < wpad * LR_CH; e += 256) {
-    const int s = e / LR_CH, q = e % LR_CH;
-    U12[s][q] = (q < cw && s < w) ? X[(int64_t)(c0 + q) * ldx + psg[p0 + s]] : T(0);
+__global__ void __launch_bounds__(TR_T) k_lu_trail(T* __restrict__ X, int64_t ldx, int R,
+                                                  int c_begin, int c_end, int p0, int w,
+                                                  const int32_t* __restrict__ posg,
+                                                  const T* __restrict__ u12, int64_t ldu,
+                                                  int nch, bool vec) {
+  extern __shared__ __align__(16) unsigned char tr_smem[];
+  T* Ls = reinterpret_cast<T*>(tr_smem);  // [w][TR_R] multipliers of this CTA's rows
+  T* Us = Ls + (size_t)w * TR_R;          // [2][w][LR_CH] chunks of U
+  const int tid = threadIdx.x;
+  const int rb = (int)blockIdx.x * TR_R;
+  const int r0 = rb + tid, r1 = rb + tid + TR_T;
+  const bool u0 = r0 < R && posg[r0] >= p0 + w;
+  const bool u1 = r1 < R && posg[r1] >= p0 + w;
+  // the multipliers: rows rb .. rb + 255 of columns p0 .. p0 + w - 1 (rows past the column's
+  // storage, ldx, read as zero)
+  constexpr int EPC = 16 / (int)sizeof(T);
+  if (vec) {
+    for (int e = tid; e < w * (TR_R / EPC); e += TR_T) {
+      const int s = e / (TR_R / EPC), i = (e % (TR_R / EPC)) * EPC;
+      T* d = Ls + (size_t)s * TR_R + i;
+      if (rb + i + EPC <= ldx) {
+        lr_cp16(d, X + (int64_t)(p0 + s) * ldx + rb + i);
+      } else {
+#pragma unroll
+        for (int u = 0; u < EPC; ++u) d[u] = T(0);
+      }
+    }
+  } else {
+    for (int e = tid; e < w * TR_R; e += TR_T) {
+      const int s = e / TR_R, i = e % TR_R;
+      if (rb + i < ldx) lr_cp<sizeof(T)>(Ls + e, X + (int64_t)(p0 + s) * ldx + rb + i);
+      else Ls[e] = T(0);
+    }
   }
-  __syncthreads();
-  const int r = blockIdx.x * 256 + threadIdx.x;
-  if (r >= R || posg[r] < p0 + w) return;
-  T acc[LR_CH];
+  const int cb = c_begin + (int)blockIdx.y * nch * LR_CH;
+  int nc = (c_end - cb + LR_CH - 1) / LR_CH;
+  nc = nc < nch ? nc : nch;
+  auto issue = [&](int ch) {  // chunk ch of U into buffer ch & 1
+    const int c0 = cb + ch * LR_CH, cw = min(LR_CH, c_end - c0);
+    T* d = Us + (size_t)(ch & 1) * w * LR_CH;
+    for (int e = tid; e < w * LR_CH; e += TR_T) {
+      const int s = e / LR_CH, q = e % LR_CH;
+      if (q < cw) lr_cp<sizeof(T)>(d + e, u12 + (int64_t)s * ldu + c0 + q);
+      else d[e] = T(0);
+    }
+  };
+  issue(0);
+  lr_cp_commit();
+  for (int ch = 0; ch < nc; ++ch) {
+    const int c0 = cb + ch * LR_CH, cw = min(LR_CH, c_end - c0);
+    if (ch + 1 < nc) issue(ch + 1);
+    lr_cp_commit();
+    T acc0[LR_CH], acc1[LR_CH];
 #pragma unroll
-  for (int q = 0; q < LR_CH; ++q) acc[q] = q < cw ? X[(int64_t)(c0 + q) * ldx + r] : T(0);
-  // the row's multipliers in batches of 16 independent loads, so that their latencies overlap
-  constexpr int LB16 = 16;
-  for (int s0 = 0; s0 < w; s0 += LB16) {
-    T lv[LB16];
-#pragma unroll
-    for (int u = 0; u < LB16; ++u) lv[u] = (s0 + u < w) ? X[(int64_t)(p0 + s0 + u) * ldx + r] : T(0);
-#pragma unroll
-    for (int u = 0; u < LB16; ++u) {
+    for (int q = 0; q < LR_CH; ++q) {
+      acc0[q] = (u0 && q < cw) ? X[(int64_t)(c0 + q) * ldx + r0] : T(0);
+      acc1[q] = (u1 && q < cw) ? X[(int64_t)(c0 + q) * ldx + r1] : T(0);
+    }
+    lr_cp_wait<1>();  // everything but the chunk just issued has landed
+    __syncthreads();
+    const T* U = Us + (size_t)(ch & 1) * w * LR_CH;
+#pragma unroll 2
+    for (int s = 0; s < w; ++s) {
+      const T l0 = Ls[s * TR_R + tid], l1 = Ls[s * TR_R + tid + TR_T];
 #pragma unroll
       for (int q = 0; q < LR_CH; q += 4) {
         T uv[4];
-        ld4(&U12[s0 + u][q], uv);
+        ld4(&U[s * LR_CH + q], uv);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[q + v] = fma(-lv[u], uv[v], acc[q + v]);
+        for (int v = 0; v < 4; ++v) {
+          acc0[q + v] = fma(-l0, uv[v], acc0[q + v]);
+          acc1[q + v] = fma(-l1, uv[v], acc1[q + v]);
+        }
       }
     }
-  }
 #pragma unroll
-  for (int q = 0; q < LR_CH; ++q)
-    if (q < cw) X[(int64_t)(c0 + q) * ldx + r] = acc[q];
+    for (int q = 0; q < LR_CH; ++q) {
+      if (u0 && q < cw) X[(int64_t)(c0 + q) * ldx + r0] = acc0[q];
+      if (u1 && q < cw) X[(int64_t)(c0 + q) * ldx + r1] = acc1[q];
+    }
+    __syncthreads();  // buffer ch & 1 is free for chunk ch + 2
+  }
+  lr_cp_wait<0>();
+}
+
+// Launches k_lu_trail on the columns [c_begin, c_end): chunks of 32 columns are grouped
+// per CTA only while the grid keeps at least two CTAs per SM.
+template <typename T>
+static int32_t launch_trail(T* X, int64_t ldx, int R, int c_begin, int c_end, int p0, int w,
+                            const int32_t* posg, const T* u12, int64_t ldu, cudaStream_t s) {
+  const int rows = (int)ceil_div(R, TR_R);
+  const int chunks = (int)ceil_div(c_end - c_begin, LR_CH);
+  int nch = 1;
+  while (nch < 4 && (int64_t)rows * ceil_div(chunks, nch + 1) >= 2 * sm_count()) ++nch;
+  const size_t smem = sizeof(T) * (size_t)w * (TR_R + 2 * LR_CH);
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_lu_trail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  const bool vec = ((uintptr_t)X % 16 == 0) && (ldx * (int64_t)sizeof(T)) % 16 == 0;
+  const dim3 grid((unsigned)rows, (unsigned)ceil_div(chunks, nch));
+  k_lu_trail<T><<<grid, TR_T, smem, s>>>(X, ldx, R, c_begin, c_end, p0, w, posg, u12, ldu, nch,
+                                         vec);
+  return last_launch_status();
 }
 
 // Pivot rows of a block of W <= 96 columns [o0, o0 + W), for the columns [c_begin, c_end):
@@ -541,15 +630,25 @@ __global__ void __launch_bounds__(256) k_lu_trail(T* __restrict__ X, int64_t ldx
 template <typename T, bool CROUT>
 __global__ void __launch_bounds__(256) k_lu_u12(T* __restrict__ X, int64_t ldx, int o0, int W,
                                                int c_begin, int c_end,
-                                               const int32_t* __restrict__ psg) {
+                                               const int32_t* __restrict__ psg,
+                                               T* __restrict__ u12, int64_t ldu) {
   extern __shared__ __align__(16) unsigned char u12_smem[];
   T* L11 = reinterpret_cast<T*>(u12_smem);           // [W][W]
   int* prow = reinterpret_cast<int*>(L11 + W * W);   // [W]
   for (int t = threadIdx.x; t < W; t += blockDim.x) prow[t] = psg[o0 + t];
   __syncthreads();
-  for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
-    const int t = e / W, s = e % W;
-    L11[e] = prow[t] >= 0 ? X[(int64_t)(o0 + s) * ldx + prow[t]] : T(0);
+  // gathered from scattered rows: batches of independent loads, so that latencies overlap
+  constexpr int LB8 = 8;
+  for (int e0 = threadIdx.x; e0 < W * W; e0 += (int)blockDim.x * LB8) {
+    T v[LB8];
+#pragma unroll
+    for (int u = 0; u < LB8; ++u) {
+      const int e = e0 + u * (int)blockDim.x, t = e / W, s = e % W;
+      v[u] = (e < W * W && prow[t] >= 0) ? X[(int64_t)(o0 + s) * ldx + prow[t]] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < LB8; ++u)
+      if (e0 + u * (int)blockDim.x < W * W) L11[e0 + u * (int)blockDim.x] = v[u];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -583,6 +682,7 @@ __global__ void __launch_bounds__(256) k_lu_u12(T* __restrict__ X, int64_t ldx, 
   for (int q = 0; q < NQ; ++q) {
     const int t = lane + 32 * q;
     if (t < W && prow[t] >= 0) X[(int64_t)c * ldx + prow[t]] = fin[q];
+    if (t < W) u12[(int64_t)t * ldu + c] = prow[t] >= 0 ? fin[q] : T(0);
   }
 }
 
@@ -630,7 +730,8 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
       return RLU_OK;
     }
   }
-  if (!in.posg || !in.psg) return RLU_OK;  // no position state: use the one-launch kernel
+  // no position state or pivot-row buffer: the one-launch kernel takes the problem
+  if (!in.posg || !in.psg || !in.u12) return RLU_OK;
   LuArgs a = in;
   a.rpc = rpc;
   a.nb = NB - 1;
@@ -643,6 +744,7 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
     --np;
   const int wo = pw_max >= 64 ? in.C : np * pw_max;
   T* X = static_cast<T*>(in.X);
+  T* U12 = static_cast<T*>(in.u12);
   for (int o0 = 0; o0 < in.C; o0 += wo) {
     const int o1 = min(in.C, o0 + wo);
     for (int p0 = o0; p0 < o1; p0 += pw_max) {
@@ -652,21 +754,17 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
       RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
       RLU_TRY(last_launch_status());
       *launched = true;
-      if (p0 + a.pw < o1) {
-        const dim3 grid((unsigned)ceil_div(in.R, 256), (unsigned)ceil_div(o1 - p0 - a.pw, LR_CH));
-        k_lu_trail<T><<<grid, 256, 0, s>>>(X, in.ldx, in.R, o1, p0, a.pw, in.posg, in.psg);
-        RLU_TRY(last_launch_status());
-      }
+      if (p0 + a.pw < o1)
+        RLU_TRY(launch_trail<T>(X, in.ldx, in.R, p0 + a.pw, o1, p0, a.pw, in.posg, U12, in.ldu, s));
     }
     if (o1 < in.C) {
       const int W = o1 - o0;  // <= 96
       const size_t ub = sizeof(T) * (size_t)W * W + sizeof(int) * (size_t)W;
       k_lu_u12<T, CROUT><<<(unsigned)ceil_div(in.C - o1, 8), 256, ub, s>>>(X, in.ldx, o0, W, o1,
-                                                                          in.C, in.psg);
+                                                                          in.C, in.psg, U12,
+                                                                          in.ldu);
       RLU_TRY(last_launch_status());
-      const dim3 grid((unsigned)ceil_div(in.R, 256), (unsigned)ceil_div(in.C - o1, LR_CH));
-      k_lu_trail<T><<<grid, 256, 0, s>>>(X, in.ldx, in.R, in.C, o0, W, in.posg, in.psg);
-      RLU_TRY(last_launch_status());
+      RLU_TRY(launch_trail<T>(X, in.ldx, in.R, o1, in.C, o0, W, in.posg, U12, in.ldu, s));
     }
   }
   return RLU_OK;

@@ -21,6 +21,8 @@ struct LuArgs {
   int p0;              // first column of the panel of this launch
   int pw;              // its width
   int cu;              // the launch solves the pivot rows of columns [p0 + pw, cu) (0: C)
+  void* u12;           // [96][ldu] the solved pivot rows of the current panel or block,
+  int64_t ldu;         //   dense (row s = pivot p0 + s), read by the trailing update
 };
 
 // crout = false: Doolittle (step 3, LU of Y); crout = true: pivot row scaled (step 6 on B^T).

@@ -106,12 +106,12 @@ struct Plan {
   size_t esz = 4;
   int64_t m = 0, n = 0;
   int k = 0, l = 0;
-  int64_t ldg = 0, ldy = 0, ldl = 0, ldb = 0;
+  int64_t ldg = 0, ldy = 0, ldl = 0, ldb = 0, ldu12 = 0;
   int split_y = 1, split_g = 1, split_c = 1;
   size_t off_G = 0, off_Y = 0, off_Lt = 0, off_Lp = 0, off_M = 0, off_dinv = 0, off_LT = 0,
          off_LR = 0, off_W = 0, off_WT = 0,
          off_C = 0, off_T = 0, off_B = 0, off_Lb = 0, off_part = 0, off_Lhi = 0, off_Llo = 0,
-         off_pos = 0, off_ps = 0, off_Bh = 0, off_Bm = 0, off_Bl = 0, total = 0;
+         off_pos = 0, off_ps = 0, off_u12 = 0, off_Bh = 0, off_Bm = 0, off_Bl = 0, total = 0;
 };
 
 static size_t carve(size_t& cur, size_t bytes) {
@@ -176,6 +176,8 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
   p.off_part = carve(cur, part);
   p.off_pos = carve(cur, (size_t)(m > n ? m : n) * sizeof(int32_t));  // LU position state
   p.off_ps = carve(cur, (size_t)l * sizeof(int32_t));
+  p.ldu12 = round_up(l, 4);  // the LUs' solved pivot rows, dense (<= 96 rows of <= l columns)
+  p.off_u12 = carve(cur, (size_t)96 * p.ldu12 * e);
   if (prec == RLU_PREC_MIXED || prec == RLU_PREC_BF16) {
     p.off_Lhi = carve(cur, (size_t)p.ldl * k * e);
     p.off_Llo = carve(cur, (size_t)p.ldl * k * e);
@@ -280,6 +282,8 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
     a.status = info ? &info->status : nullptr;
     a.posg = reinterpret_cast<int32_t*>(ws + p.off_pos);
     a.psg = reinterpret_cast<int32_t*>(ws + p.off_ps);
+    a.u12 = ws + p.off_u12;
+    a.ldu = p.ldu12;
     RLU_TRY(launch_cluster_lu(p.dt, false, a, s));
   }
   RLU_TRY(tm.rec(2, true, s));
@@ -391,6 +395,8 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
     a.status = info ? &info->status : nullptr;
     a.posg = reinterpret_cast<int32_t*>(ws + p.off_pos);
     a.psg = reinterpret_cast<int32_t*>(ws + p.off_ps);
+    a.u12 = ws + p.off_u12;
+    a.ldu = p.ldu12;
     RLU_TRY(launch_cluster_lu(p.dt, true, a, s));
   }
   RLU_TRY(tm.rec(8, true, s));
