@@ -151,7 +151,7 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
     p.split_g = umma3_splits(k, m, k);
     p.split_c = umma3_splits(n, m, k);
   }
-  if (prec == RLU_PREC_BF16) p.split_c = umma_bf16_splits(n, m, k, 128);
+  if (prec == RLU_PREC_BF16) p.split_c = umma_bf16_splits(k, m, n, 256);
   size_t part = 0;
   auto upd = [&](size_t b) { part = b > part ? b : part; };
   if (p.split_y > 1) upd((size_t)p.split_y * m * l * p.esz);
@@ -338,7 +338,7 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
     RLU_CUDA_TRY(cudaEventRecord(ss->join, ss->side));
     // C = L~^T A (k x n, row-major)
     RLU_TRY(tm.rec(6, false, s));
-    if (bf16) {  // C^T = A^T L~ with BF16 A and L~ in three BF16 parts
+    if (bf16) {  // C = L~^T A with L~ in three BF16 parts and BF16 A
       UmmaBf16Op op{};
       op.A = Av;
       op.lda = lda;
@@ -346,12 +346,12 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
       op.B1 = bp.mid;
       op.B2 = bp.lo;
       op.ldb = p.ldl;
-      op.M = n;
-      op.N = k;
+      op.M = k;
+      op.N = n;
       op.K = m;
       op.out = reinterpret_cast<float*>(Cb);
       op.ldo = p.ldb;
-      op.out_colmajor = true;
+      op.out_colmajor = false;
       op.splits = p.split_c;
       op.partial = reinterpret_cast<float*>(part);
       op.status = info ? &info->status : nullptr;

@@ -59,7 +59,8 @@ int32_t umma3_batched(int mode, const U3Job* jobs_dev, int count, int max_m, int
 
 // BF16 products (see umma_bf16.cu), same output conventions as Umma3Op.
 // Y : A (M x K row-major BF16, lda), B0 = G^T (N x K row-major BF16, ldb), one product.
-// C3: A stored K x M row-major BF16 (lda); B0/B1/B2 = hi/mid/lo BF16 parts (N x K, ldb).
+// C3: D = sum over the parts of B_p A: A stored K x N row-major BF16 (lda); B0/B1/B2 =
+//     hi/mid/lo BF16 parts of the M x K left factor (K contiguous, ldb).
 enum { UB_MODE_Y = 0, UB_MODE_C3 = 1 };
 struct UmmaBf16Op {
   const void* A;

@@ -6,12 +6,15 @@
 //               contiguous); both arrive by TMA in 128-byte-swizzled K-major tiles. One
 //               product: the range finder only needs Y's column space, so BF16 A and G with
 //               FP32 accumulation suffice.
-//   UB_MODE_C3  C^T = A^T L~ (step 5): A is stored m x n row-major, so the operand A^T
-//               (M = n, K = m) is M-major; it arrives by TMA in 128-byte-swizzled boxes of
-//               64 (n) x 64 (m) and the MMA reads it as an MN-major operand (A is exact in
-//               BF16, nothing to split or transpose). L~ comes as three BF16 parts
-//               hi + mid + lo (8 significant bits each, FP32 accurate), so three products
-//               A L_hi + A L_mid + A L_lo accumulate in FP32.
+//   UB_MODE_C3  C = L~^T A (step 5), k x n: the A operand is L~ in three BF16 parts
+//               hi + mid + lo (8 significant bits each, FP32 accurate), K-major (L~ is
+//               column-major, so a row of L~^T is contiguous), 64-byte-swizzled boxes of
+//               32 (m) x 128 (k); the B operand is A itself: A is stored m x n row-major, so
+//               the operand is N-major, 128-byte-swizzled boxes of 64 (n) x 32 (m) that the
+//               MMA reads MN-major (A is exact in BF16: nothing to split or transpose). The
+//               three products L_hi^T A + L_mid^T A + L_lo^T A accumulate in FP32. With the
+//               three parts as the 128-row operand and 256 columns of A as the other, one
+//               k-step moves 40 KB into shared memory for six 128 x 256 x 16 MMAs.
 //
 // N tiles: BN columns each, the last one only as wide as the columns left (rounded up to
 // 16), so that no MMA work is spent on padding.
@@ -28,9 +31,10 @@
 namespace rlu {
 
 static constexpr int UB_BM = 128;
-static constexpr int UB_BK = 64;  // BF16 elements: one 128-byte swizzle row
+static constexpr int UB_BK = 64;   // Y: BF16 elements of K per k-step (one 128-byte row)
+static constexpr int UB_BKC = 32;  // C: 32 elements (one 64-byte row of the L~ parts)
 static constexpr int UB_THREADS = 192;
-static constexpr int UB_MAXST = 4;
+static constexpr int UB_MAXST = 6;
 
 struct UbSmem {
   uint64_t full[UB_MAXST];
@@ -86,11 +90,16 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
          ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// MN-major operand in 128-byte-swizzled boxes of 64 (MN) x 64 (K): a row of the box holds 64
+// K-major operand in 64-byte-swizzled rows: 8-row groups 512 bytes apart
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(512u >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+// MN-major operand in 128-byte-swizzled boxes of 64 (MN) x rows (K): a row of a box holds 64
 // consecutive MN elements of one K index; groups of 8 K rows lie 1024 bytes apart (stride
-// offset) and the next 64 MN elements start one box (8192 bytes) further (leading offset).
-__device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(8192u >> 4) << 16) |
+// offset) and the next 64 MN elements start one box further (leading offset, box bytes).
+__device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr, uint32_t box_bytes) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(box_bytes >> 4) << 16) |
          ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
@@ -106,23 +115,27 @@ __device__ __forceinline__ void commit(uint32_t bar) {
 }  // namespace ub
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B BF16
-// (bits 7-9, 10-12 = 1), A MN-major if a_mn (bit 15), B K-major, N >> 3 at bit 17, M >> 4
+// (bits 7-9, 10-12 = 1), A K-major, B MN-major if b_mn (bit 16), N >> 3 at bit 17, M >> 4
 // at bit 24.
-__host__ __device__ constexpr uint32_t ub_idesc(int M, int N, bool a_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
+__host__ __device__ constexpr uint32_t ub_idesc(int M, int N, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn ? 1u : 0u) << 16) |
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// One ring slot. Y: a0 = A tile (128 x 64, K-major), b0 = G tile (BN x 64).
+// C3: a0..a2 = the L~ parts (128 x 32 each, K-major), b0 = four 64 (n) x 32 (m) boxes of A.
 struct UbLayout {
-  uint32_t a0, b0, b1, b2, stage, tx;
+  uint32_t a0, a1, a2, b0, stage, tx;
 };
 __host__ __device__ inline UbLayout ub_layout(int mode, int BN) {
   UbLayout L{};
-  const uint32_t at = UB_BM * 128, bt = (uint32_t)BN * 128;
-  if (mode == UB_MODE_Y) {  // a0: A (K-major), b0: G
-    L.a0 = 0; L.b0 = at; L.b1 = L.b2 = L.b0; L.stage = at + bt;
-  } else {                  // a0: A^T as two MN-major 64 x 64 boxes, b0..b2: L~ parts
-    L.a0 = 0; L.b0 = at; L.b1 = at + bt; L.b2 = at + 2 * bt; L.stage = at + 3 * bt;
+  if (mode == UB_MODE_Y) {
+    const uint32_t at = UB_BM * 128, bt = (uint32_t)BN * 128;
+    L.a0 = L.a1 = L.a2 = 0; L.b0 = at; L.stage = at + bt;
+  } else {
+    const uint32_t pt = UB_BM * 64;  // one part: 128 rows of 64 bytes
+    L.a0 = 0; L.a1 = pt; L.a2 = 2 * pt; L.b0 = 3 * pt;
+    L.stage = 3 * pt + (uint32_t)BN * UB_BKC * 2;
   }
   L.tx = L.stage;
   L.stage = (L.stage + 1023u) & ~1023u;
@@ -141,16 +154,20 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
   const UbLayout lay = ub_layout(MODE, a.BN);
   const int S = a.stages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grid x = (row tile, N tile), N tile fastest: the CTAs sharing an A tile run together and
-  // A is fetched from DRAM once, the other N tiles hitting L2
-  const int m0 = ((int)blockIdx.x / a.ntiles) * UB_BM;
+  // The CTAs that read the same tiles of BF16 A run together, so that A is fetched from
+  // DRAM once and the other CTAs hit L2. Y: grid x = (row tile, N tile), N tile fastest.
+  // C3: A is the N operand, grid x = (N tile, row tile), row tile fastest.
+  constexpr int BK = MODE == UB_MODE_Y ? UB_BK : UB_BKC;
+  const int mtiles = (a.M + UB_BM - 1) / UB_BM;
+  const int mt = MODE == UB_MODE_Y ? (int)blockIdx.x / a.ntiles : (int)blockIdx.x % mtiles;
+  const int nt = MODE == UB_MODE_Y ? (int)blockIdx.x % a.ntiles : (int)blockIdx.x / mtiles;
+  const int m0 = mt * UB_BM;
   const int kz = blockIdx.y;
-  const int nt = (int)blockIdx.x % a.ntiles;
   const int nb0 = nt * a.BN;
   const int bn = nt == a.ntiles - 1 ? a.bn_last : a.BN;  // this tile's MMA width
   const int k_begin = kz * a.kchunk;
   const int k_end = min(a.K, k_begin + a.kchunk);
-  const int nk = (k_end - k_begin + UB_BK - 1) / UB_BK;
+  const int nk = (k_end - k_begin + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -181,7 +198,7 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
       }
       const uint32_t base = tiles + s * lay.stage;
       const uint32_t bar = su32(&sh.full[s]);
-      const int kx = k_begin + kt * UB_BK;
+      const int kx = k_begin + kt * BK;
       if (MODE == UB_MODE_Y) {
         // the last N tile loads only its bn rows of G (map B1 has a box of bn_last rows)
         const bool narrow = bn < a.BN;
@@ -190,11 +207,11 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
         tma2d(base + lay.b0, narrow ? &mB1 : &mB0, kx, nb0, bar);
       } else {
         mb_expect_tx(bar, lay.tx);
-        tma2d(base + lay.a0, &mA, m0, kx, bar);  // A^T: x = n (64 wide), y = m (64)
-        tma2d(base + lay.a0 + 8192u, &mA, m0 + 64, kx, bar);
-        tma2d(base + lay.b0, &mB0, kx, nb0, bar);
-        tma2d(base + lay.b1, &mB1, kx, nb0, bar);
-        tma2d(base + lay.b2, &mB2, kx, nb0, bar);
+        tma2d(base + lay.a0, &mB0, kx, m0, bar);  // L~ parts: x = m (32 wide), y = k (128)
+        tma2d(base + lay.a1, &mB1, kx, m0, bar);
+        tma2d(base + lay.a2, &mB2, kx, m0, bar);
+        for (int j = 0; j < a.BN / 64; ++j)        // A: x = n (64 wide), y = m (32)
+          tma2d(base + lay.b0 + (uint32_t)j * 4096u, &mA, nb0 + 64 * j, kx, bar);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -209,16 +226,21 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t base = tiles + s * lay.stage;
+      if (MODE == UB_MODE_Y) {  // 4 MMAs of K = 16 along the 128-byte rows
 #pragma unroll
-      for (int kk = 0; kk < UB_BK / 16; ++kk) {
-        const uint32_t off = kk * 32;  // 16 K elements along a K-major row
-        // MN-major A: 16 K rows further (two 8-row groups)
-        const uint64_t da = MODE == UB_MODE_C3 ? desc_mn_sw128(base + lay.a0 + kk * 2048u)
-                                               : desc_sw128(base + lay.a0 + off);
-        mma_bf16(tmem, da, desc_sw128(base + lay.b0 + off), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-        if (MODE == UB_MODE_C3) {
-          mma_bf16(tmem, da, desc_sw128(base + lay.b1 + off), idesc, 1u);
-          mma_bf16(tmem, da, desc_sw128(base + lay.b2 + off), idesc, 1u);
+        for (int kk = 0; kk < UB_BK / 16; ++kk) {
+          const uint32_t off = kk * 32;
+          mma_bf16(tmem, desc_sw128(base + lay.a0 + off), desc_sw128(base + lay.b0 + off), idesc,
+                   (kt > 0 || kk > 0) ? 1u : 0u);
+        }
+      } else {  // 2 x 3 MMAs of K = 16: 32 bytes along the parts' rows, 16 rows of the A boxes
+#pragma unroll
+        for (int kk = 0; kk < UB_BKC / 16; ++kk) {
+          const uint64_t db = desc_mn_sw128(base + lay.b0 + kk * 2048u, 4096u);
+          const uint32_t off = kk * 32;
+          mma_bf16(tmem, desc_sw64(base + lay.a0 + off), db, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(tmem, desc_sw64(base + lay.a1 + off), db, idesc, 1u);
+          mma_bf16(tmem, desc_sw64(base + lay.a2 + off), db, idesc, 1u);
         }
       }
       commit(su32(&sh.empty[s]));
@@ -232,6 +254,7 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
     const int quarter = warp & 3;
     const int row = m0 + quarter * 32 + lane;
     float* __restrict__ out = a.out + (size_t)kz * a.split_stride;
+    const bool vec_out = ((uintptr_t)out % 16 == 0) && a.ldo % 4 == 0;
     for (int c0 = 0; c0 < bn; c0 += 32) {
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
@@ -248,15 +271,24 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
       if (ok && row < a.M) {
+        const int col0 = nb0 + c0;
+        if (!a.out_colmajor && vec_out && col0 + 32 <= a.N && c0 + 32 <= bn) {
+          float4* o4 = reinterpret_cast<float4*>(out + (size_t)row * a.ldo + col0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = nb0 + c0 + j;
-          if (c0 + j < bn && col < a.N) {
-            const float f = __uint_as_float(v[j]);
-            if (a.out_colmajor)
-              out[(size_t)col * a.ldo + row] = f;
-            else
-              out[(size_t)row * a.ldo + col] = f;
+          for (int j = 0; j < 8; ++j)
+            o4[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = col0 + j;
+            if (c0 + j < bn && col < a.N) {
+              const float f = __uint_as_float(v[j]);
+              if (a.out_colmajor)
+                out[(size_t)col * a.ldo + row] = f;
+              else
+                out[(size_t)row * a.ldo + col] = f;
+            }
           }
         }
       }
@@ -286,7 +318,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 ub_encode_fn() {
 
 // BF16 row-major (rows x cols, ld elements) tensor map with a box of box_x x box_y.
 static int32_t map2d_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
-                          int64_t ld, int box_x, int box_y, bool swizzle) {
+                          int64_t ld, int box_x, int box_y, CUtensorMapSwizzle swizzle) {
   auto enc = ub_encode_fn();
   if (!enc) return RLU_ECUDA;
   if (((uintptr_t)base & 15u) != 0 || (ld * 2) % 16 != 0) return RLU_EINVAL;
@@ -296,7 +328,7 @@ static int32_t map2d_bf16(CUtensorMap* map, const void* base, int64_t rows, int6
   cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                         swizzle,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? RLU_OK : RLU_ECUDA;
 }
@@ -304,9 +336,9 @@ static int32_t map2d_bf16(CUtensorMap* map, const void* base, int64_t rows, int6
 template <int MODE>
 static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
   if (op.M <= 0 || op.N <= 0 || op.K <= 0) return RLU_EINVAL;
-  // N tiles: up to 256 columns for Y; 128 for C3, whose slot holds three B tiles
-  const int bnmax = MODE == UB_MODE_Y ? 256 : 128;
-  const int BN = op.N > bnmax ? bnmax : (int)round_up(op.N, 16);
+  // N tiles of up to 256 columns (C3: whole 64-column boxes of A)
+  constexpr int BK = MODE == UB_MODE_Y ? UB_BK : UB_BKC;
+  const int BN = op.N > 256 ? 256 : (int)round_up(op.N, MODE == UB_MODE_Y ? 16 : 64);
   const int ntiles = (int)ceil_div(op.N, BN);
   const int bn_last = (int)round_up(op.N - (int64_t)(ntiles - 1) * BN, 16);
   const UbLayout lay = ub_layout(MODE, BN);
@@ -320,20 +352,22 @@ static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
   if (stages < 2) return RLU_EUNSUPPORTED;
   const size_t smem = (size_t)ctrl + (size_t)stages * lay.stage;
   CUtensorMap mA{}, b0{}, b1{}, b2{};
+  const auto SW128 = CU_TENSOR_MAP_SWIZZLE_128B, SW64 = CU_TENSOR_MAP_SWIZZLE_64B;
   if (MODE == UB_MODE_Y) {
-    RLU_TRY(map2d_bf16(&mA, op.A, op.M, op.K, op.lda, UB_BK, UB_BM, true));
-    RLU_TRY(map2d_bf16(&b0, op.B0, op.N, op.K, op.ldb, UB_BK, BN, true));
-    RLU_TRY(map2d_bf16(&b1, op.B0, op.N, op.K, op.ldb, UB_BK, bn_last, true));
+    RLU_TRY(map2d_bf16(&mA, op.A, op.M, op.K, op.lda, UB_BK, UB_BM, SW128));
+    RLU_TRY(map2d_bf16(&b0, op.B0, op.N, op.K, op.ldb, UB_BK, BN, SW128));
+    RLU_TRY(map2d_bf16(&b1, op.B0, op.N, op.K, op.ldb, UB_BK, bn_last, SW128));
     b2 = b0;
   } else {
-    // A stored row-major K x M (rows = K index, M contiguous): swizzled boxes 64 (M) x 64 (K)
-    RLU_TRY(map2d_bf16(&mA, op.A, op.K, op.M, op.lda, 64, UB_BK, true));
-    RLU_TRY(map2d_bf16(&b0, op.B0, op.N, op.K, op.ldb, UB_BK, BN, true));
-    RLU_TRY(map2d_bf16(&b1, op.B1, op.N, op.K, op.ldb, UB_BK, BN, true));
-    RLU_TRY(map2d_bf16(&b2, op.B2, op.N, op.K, op.ldb, UB_BK, BN, true));
+    // A stored row-major K x N (rows = K index, N contiguous): boxes 64 (N) x 32 (K);
+    // the L~ parts M x K (K contiguous): boxes 32 (K) x 128 (M)
+    RLU_TRY(map2d_bf16(&mA, op.A, op.K, op.N, op.lda, 64, UB_BKC, SW128));
+    RLU_TRY(map2d_bf16(&b0, op.B0, op.M, op.K, op.ldb, UB_BKC, UB_BM, SW64));
+    RLU_TRY(map2d_bf16(&b1, op.B1, op.M, op.K, op.ldb, UB_BKC, UB_BM, SW64));
+    RLU_TRY(map2d_bf16(&b2, op.B2, op.M, op.K, op.ldb, UB_BKC, UB_BM, SW64));
   }
   int splits = op.splits < 1 ? 1 : op.splits;
-  const int kchunk = (int)round_up(ceil_div(op.K, splits), UB_BK);
+  const int kchunk = (int)round_up(ceil_div(op.K, splits), BK);
   splits = (int)ceil_div(op.K, kchunk);
   Umma3Args a{};
   a.M = (int)op.M;
