@@ -357,17 +357,30 @@ def check_dims(m: int, n: int, k: int, l: int) -> None:
         raise ValueError(f"need 1 <= k <= l <= min(m, n); got m={m} n={n} k={k} l={l}")
 
 
+def project(A: np.ndarray, G: np.ndarray, q: int = 0) -> np.ndarray:
+    """Step 2, Y = A G, or with the power iterations of Section 5 ("Power Iterations"):
+    Y = (A A^*)^q A G for a small integer q, unnormalised, applied as q rounds of
+    Y <- A (A^T Y) (A real, so A^* = A^T)."""
+    if q < 0:
+        raise ValueError("q must be >= 0")
+    Y = A @ G
+    for _ in range(q):
+        Y = A @ (A.T @ Y)
+    return Y
+
+
 def rlu_factor(A: np.ndarray, k: int, l: int, seed: int, stream_id: int = 0,
-               G: np.ndarray | None = None) -> dict:
+               G: np.ndarray | None = None, q: int = 0) -> dict:
     """Algorithm 1, steps 1-8, in FP64. A is upcast exactly. Returns P, Q (gather form),
     L (m x k, unit lower trapezoidal), U (k x n, upper trapezoidal) and the intermediates
-    G, Y (A G), Y_lu (factored Y), L_y, B, plus zero-pivot steps and per-step pivot gaps."""
+    G, Y (A G, or (A A^T)^q A G with q power iterations), Y_lu (factored Y), L_y, B, plus
+    zero-pivot steps and per-step pivot gaps."""
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     check_dims(m, n, k, l)
     if G is None:
         G = gaussian(seed, stream_id, n, l)                 # step 1
-    Y = A @ G                                               # step 2
+    Y = project(A, G, q)                                    # step 2
     Y_lu, P, zero_y, gaps_y = lu_partial_pivot(Y)           # step 3
     Ly = np.tril(Y_lu[:, :k], -1) + np.eye(m, k)            # step 4: first k columns
     B = pinv_apply(Ly, A[P, :])                             # step 5

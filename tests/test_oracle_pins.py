@@ -245,6 +245,59 @@ def test_exact_rank_k_reconstructs_to_rounding():
     assert spec < 1e-12
 
 
+# ----------------------------------------------------------------------------------------
+# Section 5, power iterations: step 2 becomes Y = (A A^T)^q A G.
+# ----------------------------------------------------------------------------------------
+
+def test_project_power_closed_form():
+    """(A A^T)^q A = U diag(sigma^(2q+1)) V^T for A = U diag(sigma) V^T: the oracle's q
+    rounds of Y <- A (A^T Y) against that closed form. A transposed operand, a missing or
+    extra round, or A^T A in place of A A^T changes the exponent or the singular vectors."""
+    rng = np.random.default_rng(3)
+    m, n, l = 40, 30, 6
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sigma = np.linspace(1.5, 0.2, n)
+    A = (U * sigma) @ V.T
+    G = rng.standard_normal((n, l))
+    for q in (0, 1, 2, 3):
+        want = (U * sigma ** (2 * q + 1)) @ (V.T @ G)
+        got = O.project(A, G, q)
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), q
+    with pytest.raises(ValueError):
+        O.project(A, G, -1)
+
+
+@pytest.mark.parametrize("spec", ["paper_exp", "paper_slow"])
+def test_power_iteration_lowers_the_error(spec):
+    """The power-iteration subsection of Section 5: one power iteration lowers the error of
+    Algorithm 1 for the exponentially decaying spectrum and for the slow decay
+    sigma_k = 100 / (9 + k)^2 (normalised to sigma_1 = 1). Every rank-k error stays at or
+    above sigma_{k+1}, the optimum."""
+    m = n = 300
+    k, l = 20, 25
+    sigma = synth.spectrum(spec, n)
+    e0, e1 = [], []
+    for seed in range(3):
+        A = synth.prescribed_matrix(m, n, sigma, 10 + seed, 20 + seed)
+        for q, errs in ((0, e0), (1, e1)):
+            r = O.rlu_factor(A, k, l, seed=seed, q=q)
+            _, spec2 = O.reconstruct_error(A, r["P"], r["Q"], r["L"], r["U"])
+            assert spec2 >= sigma[k] * (1 - 1e-9)
+            errs.append(spec2)
+    assert np.median(e1) < np.median(e0), (e0, e1)
+
+
+def test_power_iteration_keeps_exact_rank():
+    m, n, k, l = 120, 90, 10, 14
+    A = synth.prescribed_matrix(m, n, synth.spectrum("rank_k", min(m, n), k), 3, 4)
+    for q in (1, 2):
+        res = O.rlu_factor(A, k, l, seed=5, q=q)
+        _check_structure(res, m, n, k)
+        fro, _ = O.reconstruct_error(A, res["P"], res["Q"], res["L"], res["U"], spectral=False)
+        assert fro / np.linalg.norm(A) < 1e-12
+
+
 def test_full_rank_k_equals_n_is_exact_lu():
     n = 24
     rng = np.random.default_rng(4)
