@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--prec", choices=["f32", "mixed", "f64", "bf16"], default=None,
                     help="arithmetic of the path (default: the workload's storage type)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-power", action="store_true",
+                    help="skip the power-iteration (q = 1) measurement")
     ap.add_argument("--serve-lambdas", default="300,1000,3000",
                     help="Poisson arrival rates (requests/s) of the serving measurement")
     ap.add_argument("--serve-secs", type=float, default=2.0, help="arrival window per rate")
@@ -544,6 +546,34 @@ def run_ours(args):
                        "workspace and outputs; the same input"}
         del fzb
 
+    # ---- power iterations (Section 5): Y = (A A^T)^q A G with q = 1, same input ------
+    power = None
+    if prec in ("mixed", "bf16", "f32", "f64") and sigma is not None and not args.no_power:
+        fq = rlu.Factorizer(m, n, k, l, prec, 1)
+        for _ in range(2):
+            fq(A, w["seed_g"])
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nq = max(3, K // 4)
+        q0.record(stream)
+        for _ in range(nq):
+            fq(A, w["seed_g"])
+        q1.record(stream)
+        torch.cuda.synchronize()
+        qms = q0.elapsed_time(q1) / nq
+        Pq, Qq, Lq, Uq, iq = fq(A, w["seed_g"])
+        fro_q, _ = rlu.reconstruct_error(A, Pq, Qq, Lq, Uq)
+        torch.cuda.synchronize()
+        # the rounds are unnormalised: directions below (sigma_{k+1}/sigma_1)^3 of the top
+        # one are resolved only when that ratio is above the path's rounding unit
+        amp = float((sigma[k] / sigma[0]) ** 3)
+        unit = 2.0 ** -52 if prec == "f64" else 2.0 ** -23
+        power = {"q": 1, "value": 1e3 / qms, "unit": "LU/s", "ms_per_step": qms,
+                 "fro": fro_q.item(), "fro_q0": err.get("fro"),
+                 "sigma_ratio_cubed": amp, "resolved": amp > unit,
+                 "info": iq.cpu().tolist()}
+        del fq
+
     serve = None
     if not args.no_serve and args.workload == WORKLOAD:
         serve = serve_run([float(x) for x in args.serve_lambdas.split(",") if x], args.serve_secs)
@@ -580,6 +610,7 @@ def run_ours(args):
         "gemm_tflops": gemm_tflops,
         "plain_fp32": plain,
         "two_in_flight": two,
+        "power": power,
         "serve": serve,
         "clocks": clocks.summary(),
         "e2e": e2e,

@@ -118,9 +118,10 @@ size_t rlu_workspace_size(int64_t m, int64_t n, int32_t k, int32_t l, int32_t pr
  *   workspace : device scratch of at least rlu_workspace_size() bytes, 256-byte aligned.
  * Step 3 is LU with partial pivoting over all l columns (getf2 tie rule: first maximum in
  * the current row order); step 5 uses the normal equations
- * L_y^+ = (L_y^T L_y)^{-1} L_y^T (remark after Algorithm 1) with a Cholesky factor of the
- * k x k Gram matrix in FP64; step 6 pivots on the largest entry of row j of the current
- * Schur complement and keeps the unit diagonal on L_b.
+ * L_y^+ = (L_y^T L_y)^{-1} L_y^T (remark after Algorithm 1) with an LDL^T (Cholesky)
+ * factorization of the k x k Gram matrix: FP64 for RLU_PREC_F64 and for k > 512, FP32 on
+ * the single-precision paths otherwise; step 6 pivots on the largest entry of row j of the
+ * current Schur complement and keeps the unit diagonal on L_b.
  * Errors: RLU_EINVAL (dimensions, NULL pointers, strides), RLU_EUNSUPPORTED (dtype does
  * not match prec), RLU_ENOMEM (workspace too small), RLU_ECUDA (launch failure). */
 int32_t rlu_factor(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
@@ -166,6 +167,22 @@ int32_t rlu_factor_stages(const void* A, int32_t dtype, int64_t m, int64_t n, in
                           int32_t* P, int32_t* Q, void* L, int64_t ldl, void* U,
                           int64_t ldu, rlu_info* info, void* workspace, size_t ws_bytes,
                           const rlu_stage_outputs* stages, void* stream);
+
+/* Power iterations (Section 5, "Power Iterations"): step 2 becomes
+ * Y = (A A^T)^q A G, applied as q rounds of Z = A^T Y, Y = A Z (unnormalised, so q should
+ * stay small: the paper's scheme for larger q normalises between rounds). The products of
+ * the rounds are FP32 accurate on RLU_PREC_MIXED (three TF32 products) and RLU_PREC_BF16
+ * (three BF16 products against the exact BF16 A); plain FP32 / FP64 SIMT otherwise.
+ * 0 <= q <= 16 (q = 0 is rlu_factor_stages). Workspace: rlu_workspace_size_power, which
+ * adds Z (n x l) and the splits of Y and Z to rlu_workspace_size. Other arguments, outputs
+ * and errors as rlu_factor_stages; RLU_EINVAL also for q outside [0, 16]. */
+size_t rlu_workspace_size_power(int64_t m, int64_t n, int32_t k, int32_t l, int32_t prec,
+                                int32_t q);
+int32_t rlu_factor_power(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                         int32_t k, int32_t l, uint64_t seed, int32_t prec, int32_t q,
+                         int32_t* P, int32_t* Q, void* L, int64_t ldl, void* U, int64_t ldu,
+                         rlu_info* info, void* workspace, size_t ws_bytes,
+                         const rlu_stage_outputs* stages, void* stream);
 
 /* Bytes of workspace rlu_reconstruct_error needs. */
 size_t rlu_reconstruct_workspace_size(int64_t m, int64_t n, int32_t k);

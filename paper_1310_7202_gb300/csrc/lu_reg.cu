@@ -633,8 +633,9 @@ __global__ void __launch_bounds__(256) k_lu_u12(T* __restrict__ X, int64_t ldx, 
                                                const int32_t* __restrict__ psg,
                                                T* __restrict__ u12, int64_t ldu) {
   extern __shared__ __align__(16) unsigned char u12_smem[];
-  T* L11 = reinterpret_cast<T*>(u12_smem);           // [W][W]
-  int* prow = reinterpret_cast<int*>(L11 + W * W);   // [W]
+  const int WP = W | 1;                               // odd row stride: no bank conflicts
+  T* L11 = reinterpret_cast<T*>(u12_smem);           // [W][WP]
+  int* prow = reinterpret_cast<int*>(L11 + W * WP);  // [W]
   for (int t = threadIdx.x; t < W; t += blockDim.x) prow[t] = psg[o0 + t];
   __syncthreads();
   // gathered from scattered rows: batches of independent loads, so that latencies overlap
@@ -647,8 +648,10 @@ __global__ void __launch_bounds__(256) k_lu_u12(T* __restrict__ X, int64_t ldx, 
       v[u] = (e < W * W && prow[t] >= 0) ? X[(int64_t)(o0 + s) * ldx + prow[t]] : T(0);
     }
 #pragma unroll
-    for (int u = 0; u < LB8; ++u)
-      if (e0 + u * (int)blockDim.x < W * W) L11[e0 + u * (int)blockDim.x] = v[u];
+    for (int u = 0; u < LB8; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < W * W) L11[(e / W) * WP + e % W] = v[u];
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -667,14 +670,14 @@ __global__ void __launch_bounds__(256) k_lu_u12(T* __restrict__ X, int64_t ldx, 
     for (int s = 32 * q; s < min(W, 32 * q + 32); ++s) {
       T us = __shfl_sync(0xffffffffu, u[q], s - 32 * q);
       if (CROUT) {
-        const T pv = L11[s * W + s];
+        const T pv = L11[s * WP + s];
         if (pv != T(0)) us = us * rcp_piv(pv);
       }
       if (lane == s - 32 * q) fin[q] = us;
 #pragma unroll
       for (int qq = q; qq < NQ; ++qq) {
         const int t = lane + 32 * qq;
-        if (t > s && t < W) u[qq] = fma(-L11[t * W + s], us, u[qq]);
+        if (t > s && t < W) u[qq] = fma(-L11[t * WP + s], us, u[qq]);
       }
     }
   }
@@ -740,7 +743,7 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
   const int pw_max = NB - 1;
   int np = (64 + pw_max / 2) / pw_max;
   while (np > 1 && (np * pw_max > 96 ||
-                    sizeof(T) * (size_t)(np * pw_max) * (np * pw_max) + 4 * (np * pw_max) > 48 * 1024))
+                    sizeof(T) * (size_t)(np * pw_max) * ((np * pw_max) | 1) + 4 * (np * pw_max) > 48 * 1024))
     --np;
   const int wo = pw_max >= 64 ? in.C : np * pw_max;
   T* X = static_cast<T*>(in.X);
@@ -759,7 +762,7 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
     }
     if (o1 < in.C) {
       const int W = o1 - o0;  // <= 96
-      const size_t ub = sizeof(T) * (size_t)W * W + sizeof(int) * (size_t)W;
+      const size_t ub = sizeof(T) * (size_t)W * (W | 1) + sizeof(int) * (size_t)W;
       k_lu_u12<T, CROUT><<<(unsigned)ceil_div(in.C - o1, 8), 256, ub, s>>>(X, in.ldx, o0, W, o1,
                                                                           in.C, in.psg, U12,
                                                                           in.ldu);

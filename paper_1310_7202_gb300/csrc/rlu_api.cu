@@ -108,6 +108,10 @@ struct Plan {
   int k = 0, l = 0;
   int64_t ldg = 0, ldy = 0, ldl = 0, ldb = 0, ldu12 = 0;
   int split_y = 1, split_g = 1, split_c = 1;
+  int q = 0;                      // power iterations (Section 5)
+  int split_z = 1, split_y3 = 1;  // their products Z = A^T Y and Y = A Z
+  size_t off_Z = 0, off_Yh = 0, off_Yl = 0, off_Zh = 0, off_Zl = 0, off_Yb[3] = {0, 0, 0},
+         off_Zb[3] = {0, 0, 0};
   size_t off_G = 0, off_Y = 0, off_Lt = 0, off_Lp = 0, off_M = 0, off_dinv = 0, off_LT = 0,
          off_LR = 0, off_W = 0, off_WT = 0,
          off_C = 0, off_T = 0, off_B = 0, off_Lb = 0, off_part = 0, off_Lhi = 0, off_Llo = 0,
@@ -120,8 +124,10 @@ static size_t carve(size_t& cur, size_t bytes) {
   return at;
 }
 
-static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p) {
+static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p, int q = 0) {
   p.prec = prec;
+  if (q < 0 || q > 16) return false;
+  p.q = q;
   if (prec == RLU_PREC_F64) {
     p.dt = RLU_F64;
     p.esz = 8;
@@ -152,8 +158,20 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
     p.split_c = umma3_splits(n, m, k);
   }
   if (prec == RLU_PREC_BF16) p.split_c = umma_bf16_splits(k, m, n, 256);
+  // power iterations: Z = A^T Y (as C, with l columns of Y) and Y = A Z (as Y)
+  p.split_z = split_for(l, n, m, bm, bn);
+  p.split_y3 = p.split_y;
+  if (prec == RLU_PREC_MIXED) p.split_z = umma3_splits(n, m, l);
+  if (prec == RLU_PREC_BF16) {
+    p.split_z = umma_bf16_splits(l, m, n, 256);
+    p.split_y3 = umma_bf16_splits(m, n, l, 128);
+  }
   size_t part = 0;
   auto upd = [&](size_t b) { part = b > part ? b : part; };
+  if (q > 0) {
+    if (p.split_z > 1) upd((size_t)p.split_z * l * n * p.esz);
+    if (p.split_y3 > 1) upd((size_t)p.split_y3 * m * l * p.esz);
+  }
   if (p.split_y > 1) upd((size_t)p.split_y * m * l * p.esz);
   upd((size_t)(p.split_g + 1) * k * k * p.esz);
   if (p.split_c > 1) upd((size_t)p.split_c * k * n * p.esz);
@@ -186,6 +204,20 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p)
     p.off_Bh = carve(cur, (size_t)p.ldl * k * 2);
     p.off_Bm = carve(cur, (size_t)p.ldl * k * 2);
     p.off_Bl = carve(cur, (size_t)p.ldl * k * 2);
+  }
+  if (q > 0) {  // Z (n x l, ld ldg) and the splits of Y and Z for the accurate products
+    p.off_Z = carve(cur, (size_t)p.ldg * l * e);
+    if (prec == RLU_PREC_MIXED) {
+      p.off_Yh = carve(cur, (size_t)p.ldy * l * 4);
+      p.off_Yl = carve(cur, (size_t)p.ldy * l * 4);
+      p.off_Zh = carve(cur, (size_t)p.ldg * l * 4);
+      p.off_Zl = carve(cur, (size_t)p.ldg * l * 4);
+    }
+    if (prec == RLU_PREC_BF16)
+      for (int t = 0; t < 3; ++t) {
+        p.off_Yb[t] = carve(cur, (size_t)p.ldy * l * 2);
+        p.off_Zb[t] = carve(cur, (size_t)p.ldg * l * 2);
+      }
   }
   p.total = cur;
   return true;
@@ -269,6 +301,100 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
   } else {
     GemmOp op{A, lda, true, G, p.ldg, true, Y, p.ldy, false, m, l, n, p.split_y, part, false};
     RLU_TRY((gemm_simt<T, T>(op, s)));
+  }
+  // power iterations (Section 5): Y <- A (A^T Y), q times, with FP32-accurate products on
+  // the reduced-precision paths (Z and Y are not random matrices whose rounding is harmless)
+  for (int it = 0; it < p.q; ++it) {
+    T* Z = reinterpret_cast<T*>(ws + p.off_Z);  // n x l, column-major, ld ldg
+    if (bf16) {
+      Bf16Parts yp{}, zp{};
+      yp.hi = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Yb[0]);
+      yp.mid = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Yb[1]);
+      yp.lo = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Yb[2]);
+      zp.hi = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Zb[0]);
+      zp.mid = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Zb[1]);
+      zp.lo = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Zb[2]);
+      RLU_TRY(split_parts(reinterpret_cast<const float*>(Y), p.ldy, m, l, nullptr, nullptr, yp, s));
+      UmmaBf16Op zo{};  // Z^T (l x n, row-major = Z column-major) = Y^T A
+      zo.A = Av;
+      zo.lda = lda;
+      zo.B0 = yp.hi;
+      zo.B1 = yp.mid;
+      zo.B2 = yp.lo;
+      zo.ldb = p.ldy;
+      zo.M = l;
+      zo.N = n;
+      zo.K = m;
+      zo.out = reinterpret_cast<float*>(Z);
+      zo.ldo = p.ldg;
+      zo.out_colmajor = false;
+      zo.splits = p.split_z;
+      zo.partial = reinterpret_cast<float*>(part);
+      zo.status = info ? &info->status : nullptr;
+      RLU_TRY(umma_bf16_gemm(UB_MODE_C3, zo, s));
+      RLU_TRY(split_parts(reinterpret_cast<const float*>(Z), p.ldg, n, l, nullptr, nullptr, zp, s));
+      UmmaBf16Op yo{};  // Y = A Z, Z in three BF16 parts
+      yo.A = Av;
+      yo.lda = lda;
+      yo.B0 = zp.hi;
+      yo.B1 = zp.mid;
+      yo.B2 = zp.lo;
+      yo.ldb = p.ldg;
+      yo.M = m;
+      yo.N = l;
+      yo.K = n;
+      yo.out = reinterpret_cast<float*>(Y);
+      yo.ldo = p.ldy;
+      yo.out_colmajor = true;
+      yo.splits = p.split_y3;
+      yo.partial = reinterpret_cast<float*>(part);
+      yo.status = info ? &info->status : nullptr;
+      RLU_TRY(umma_bf16_gemm(UB_MODE_Y3, yo, s));
+    } else if (p.prec == RLU_PREC_MIXED && tma_ok) {
+      float* Yh = reinterpret_cast<float*>(ws + p.off_Yh);
+      float* Yl = reinterpret_cast<float*>(ws + p.off_Yl);
+      float* Zh = reinterpret_cast<float*>(ws + p.off_Zh);
+      float* Zl = reinterpret_cast<float*>(ws + p.off_Zl);
+      RLU_TRY(split_parts(reinterpret_cast<const float*>(Y), p.ldy, m, l, Yh, Yl, Bf16Parts{}, s));
+      Umma3Op zo{};  // Z (n x l, column-major) = A^T Y, three TF32 products
+      zo.A0 = reinterpret_cast<const float*>(A);
+      zo.lda = lda;
+      zo.B0 = Yh;
+      zo.B1 = Yl;
+      zo.ldb = p.ldy;
+      zo.M = n;
+      zo.N = l;
+      zo.K = m;
+      zo.out = reinterpret_cast<float*>(Z);
+      zo.ldo = p.ldg;
+      zo.out_colmajor = true;
+      zo.splits = p.split_z;
+      zo.partial = reinterpret_cast<float*>(part);
+      zo.status = info ? &info->status : nullptr;
+      RLU_TRY(umma3_gemm(U3_MODE_C3, zo, s));
+      RLU_TRY(split_parts(reinterpret_cast<const float*>(Z), p.ldg, n, l, Zh, Zl, Bf16Parts{}, s));
+      Umma3Op yo{};  // Y = A Z, three TF32 products
+      yo.A0 = reinterpret_cast<const float*>(A);
+      yo.lda = lda;
+      yo.B0 = Zh;
+      yo.B1 = Zl;
+      yo.ldb = p.ldg;
+      yo.M = m;
+      yo.N = l;
+      yo.K = n;
+      yo.out = reinterpret_cast<float*>(Y);
+      yo.ldo = p.ldy;
+      yo.out_colmajor = true;
+      yo.splits = p.split_y3;
+      yo.partial = reinterpret_cast<float*>(part);
+      yo.status = info ? &info->status : nullptr;
+      RLU_TRY(umma3_gemm(U3_MODE_Y3, yo, s));
+    } else {
+      GemmOp zo{Y, p.ldy, true, A, lda, false, Z, p.ldg, true, l, n, m, p.split_z, part, false};
+      RLU_TRY((gemm_simt<T, T>(zo, s)));
+      GemmOp yo{A, lda, true, Z, p.ldg, true, Y, p.ldy, false, m, l, n, p.split_y3, part, false};
+      RLU_TRY((gemm_simt<T, T>(yo, s)));
+    }
   }
   RLU_TRY(tm.rec(1, true, s));
   if (st && st->Y) RLU_TRY(copy_cm<T>(Y, p.ldy, static_cast<T*>(st->Y), m, m, l, s));
@@ -464,15 +590,22 @@ extern "C" size_t rlu_workspace_size(int64_t m, int64_t n, int32_t k, int32_t l,
   return p.total;
 }
 
-extern "C" int32_t rlu_factor_stages(const void* A, int32_t dtype, int64_t m, int64_t n,
-                                     int64_t lda, int32_t k, int32_t l, uint64_t seed,
-                                     int32_t prec, int32_t* P, int32_t* Q, void* L, int64_t ldl,
-                                     void* U, int64_t ldu, rlu_info* info, void* workspace,
-                                     size_t ws_bytes, const rlu_stage_outputs* stages,
-                                     void* stream) {
+extern "C" size_t rlu_workspace_size_power(int64_t m, int64_t n, int32_t k, int32_t l,
+                                           int32_t prec, int32_t q) {
+  Plan p;
+  if (!make_plan(m, n, k, l, prec, p, q)) return 0;
+  return p.total;
+}
+
+extern "C" int32_t rlu_factor_power(const void* A, int32_t dtype, int64_t m, int64_t n,
+                                    int64_t lda, int32_t k, int32_t l, uint64_t seed,
+                                    int32_t prec, int32_t q, int32_t* P, int32_t* Q, void* L,
+                                    int64_t ldl, void* U, int64_t ldu, rlu_info* info,
+                                    void* workspace, size_t ws_bytes,
+                                    const rlu_stage_outputs* stages, void* stream) {
   RLU_TRY(validate(A, dtype, m, n, lda, k, l, prec, P, Q, L, ldl, U, ldu));
   Plan p;
-  if (!make_plan(m, n, k, l, prec, p)) return RLU_EINVAL;
+  if (!make_plan(m, n, k, l, prec, p, q)) return RLU_EINVAL;
   if (workspace == nullptr || ws_bytes < p.total) return RLU_ENOMEM;
   if (((uintptr_t)workspace & 255u) != 0) return RLU_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -481,6 +614,16 @@ extern "C" int32_t rlu_factor_stages(const void* A, int32_t dtype, int64_t m, in
                             (char*)workspace, stages, s);
   return factor_t<float>(p, A, lda, seed, P, Q, (float*)L, ldl, (float*)U, ldu, info,
                          (char*)workspace, stages, s);
+}
+
+extern "C" int32_t rlu_factor_stages(const void* A, int32_t dtype, int64_t m, int64_t n,
+                                     int64_t lda, int32_t k, int32_t l, uint64_t seed,
+                                     int32_t prec, int32_t* P, int32_t* Q, void* L, int64_t ldl,
+                                     void* U, int64_t ldu, rlu_info* info, void* workspace,
+                                     size_t ws_bytes, const rlu_stage_outputs* stages,
+                                     void* stream) {
+  return rlu_factor_power(A, dtype, m, n, lda, k, l, seed, prec, 0, P, Q, L, ldl, U, ldu, info,
+                          workspace, ws_bytes, stages, stream);
 }
 
 extern "C" int32_t rlu_factor(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,

@@ -12,6 +12,12 @@ struct Bf16Parts {
   __nv_bfloat16* lo = nullptr;
 };
 
+// Exact TF32 pairs (hi, lo) and/or three BF16 parts of a column-major FP32 matrix, same ld
+// (the operands of the FP32-accurate products of the power iterations); null outputs are
+// skipped.
+int32_t split_parts(const float* X, int64_t ld, int64_t rows, int cols, float* hi, float* lo,
+                    Bf16Parts bp, cudaStream_t s);
+
 template <typename T>
 int32_t build_ly(const T* Y, int64_t ldy, int64_t m, int k, const int32_t* perm, T* Lt, T* Lp,
                  int64_t ldl, cudaStream_t s, T* Lhi = nullptr, T* Llo = nullptr,

@@ -8,7 +8,7 @@
 namespace rlu {
 
 // FP32-accurate tensor-core products from exact TF32 splits (see umma3.cu).
-enum { U3_MODE_Y2 = 0, U3_MODE_C3 = 1, U3_MODE_G3 = 2 };
+enum { U3_MODE_Y2 = 0, U3_MODE_C3 = 1, U3_MODE_G3 = 2, U3_MODE_Y3 = 3 };
 
 struct Umma3Args {
   float* out;
@@ -24,6 +24,7 @@ struct Umma3Args {
 // Y2: A0 = A (M x K row-major, lda), B0 = G^T (N x K row-major, ldb).
 // C3: A0 = A stored K x M row-major (lda), B0/B1 = hi/lo of B (N x K row-major, ldb).
 // G3: A0/A1 = hi/lo of A (M x K, lda), B0/B1 = hi/lo of B (N x K, ldb).
+// Y3: A0 = A (M x K row-major, split on chip), B0/B1 = hi/lo of B (N x K row-major, ldb).
 // out == nullptr: only the row-major FP32 partial slices (splits x M x N) are written.
 struct Umma3Op {
   const float* A0;
@@ -61,7 +62,8 @@ int32_t umma3_batched(int mode, const U3Job* jobs_dev, int count, int max_m, int
 // Y : A (M x K row-major BF16, lda), B0 = G^T (N x K row-major BF16, ldb), one product.
 // C3: D = sum over the parts of B_p A: A stored K x N row-major BF16 (lda); B0/B1/B2 =
 //     hi/mid/lo BF16 parts of the M x K left factor (K contiguous, ldb).
-enum { UB_MODE_Y = 0, UB_MODE_C3 = 1 };
+// Y3: A as for Y; B0/B1/B2 = hi/mid/lo BF16 parts of the N x K right factor (ldb).
+enum { UB_MODE_Y = 0, UB_MODE_C3 = 1, UB_MODE_Y3 = 2 };
 struct UmmaBf16Op {
   const void* A;
   int64_t lda;

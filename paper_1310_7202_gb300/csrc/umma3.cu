@@ -9,6 +9,8 @@
 //            transposed and split on chip into K-major tiles; L~ comes pre-split (hi, lo).
 //            Products Ahi Lhi + Alo Lhi + Ahi Llo.
 //   MODE_G3  Gram L~^T L~ (step 5): both operands pre-split, three products.
+//   MODE_Y3  Y = A Z (the power iterations of Section 5): A split on chip as in MODE_Y2, Z
+//            pre-split (hi, lo); products hi(A) Zhi + lo(A) Zhi + hi(A) Zlo.
 //
 // Warp roles: warp 0 TMA producer (ring of STAGES slots, full/empty mbarriers), warp 1
 // TMEM allocation and MMA issue, warps 2..5 epilogue (tcgen05.ld), warps 6..9 converter
@@ -112,6 +114,8 @@ __host__ __device__ inline U3Layout u3_layout(int mode, int BN) {
   const uint32_t at = U3_BM * 128, bt = (uint32_t)BN * 128;
   if (mode == U3_MODE_Y2) {         // a0: TMA A -> hi in place, a1: lo, b0: G
     L.a0 = 0; L.a1 = at; L.b0 = 2 * at; L.b1 = L.b0; L.a2 = 0; L.stage = 2 * at + bt;
+  } else if (mode == U3_MODE_Y3) {  // a0: TMA A -> hi in place, a1: lo, b0 Zhi, b1 Zlo
+    L.a0 = 0; L.a1 = at; L.b0 = 2 * at; L.b1 = 2 * at + bt; L.a2 = 0; L.stage = 2 * at + 2 * bt;
   } else if (mode == U3_MODE_C3) {  // a2: raw A (n-contiguous), a0 hi, a1 lo, b0 Lhi, b1 Llo
     L.a2 = 0; L.a0 = at; L.a1 = 2 * at; L.b0 = 3 * at; L.b1 = 3 * at + bt; L.stage = 3 * at + 2 * bt;
   } else {                          // G3: a0 hi, a1 lo, b0 hi, b1 lo (all TMA)
@@ -167,6 +171,7 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
     if (MODE == U3_MODE_Y2) tx = 2 * 0 + U3_BM * 128 + (uint32_t)a.BN * 128;
     if (MODE == U3_MODE_C3) tx = U3_BM * 128 + 2 * (uint32_t)a.BN * 128;
     if (MODE == U3_MODE_G3) tx = 2 * U3_BM * 128 + 2 * (uint32_t)a.BN * 128;
+    if (MODE == U3_MODE_Y3) tx = U3_BM * 128 + 2 * (uint32_t)a.BN * 128;
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % S;
       if (kt >= S && !mb_wait(su32(&sh.empty[s]), (uint32_t)(((kt / S) - 1) & 1))) {
@@ -180,6 +185,10 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
       if (MODE == U3_MODE_Y2) {
         tma2d(base + lay.a0, &mA0, kx, m0, bar);
         tma2d(base + lay.b0, &mB0, kx, nb0, bar);
+      } else if (MODE == U3_MODE_Y3) {
+        tma2d(base + lay.a0, &mA0, kx, m0, bar);
+        tma2d(base + lay.b0, &mB0, kx, nb0, bar);
+        tma2d(base + lay.b1, &mB1, kx, nb0, bar);
       } else if (MODE == U3_MODE_C3) {
         tma2d(base + lay.a2, &mA0, m0, kx, bar);   // raw A: x = n (128 wide), y = m
         tma2d(base + lay.b0, &mB0, kx, nb0, bar);
@@ -262,7 +271,7 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
         break;
       }
       const uint32_t base = tiles + s * lay.stage;
-      if (MODE == U3_MODE_Y2) {
+      if (MODE == U3_MODE_Y2 || MODE == U3_MODE_Y3) {
         // row r of the swizzled A tile: 8 chunks of 16 bytes, position-preserving split
         float* hi = reinterpret_cast<float*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 32;
         float* lo = reinterpret_cast<float*>(u3_smem + (base + lay.a1 - su32(u3_smem))) + r * 32;
@@ -383,6 +392,11 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
     RLU_TRY(map2d(&n0, op.B0, op.N, op.K, op.ldb, U3_BK, BN, true));
     m1 = m0;
     n1 = n0;
+  } else if (MODE == U3_MODE_Y3) {
+    RLU_TRY(map2d(&m0, op.A0, op.M, op.K, op.lda, U3_BK, U3_BM, true));
+    RLU_TRY(map2d(&n0, op.B0, op.N, op.K, op.ldb, U3_BK, BN, true));
+    RLU_TRY(map2d(&n1, op.B1, op.N, op.K, op.ldb, U3_BK, BN, true));
+    m1 = m0;
   } else if (MODE == U3_MODE_C3) {
     // A stored row-major K x M (rows = K index, M contiguous): box 128 (M) x 32 (K)
     RLU_TRY(map2d(&m0, op.A0, op.K, op.M, op.lda, U3_BM, U3_BK, false));
@@ -503,6 +517,7 @@ int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s) {
   if (mode == U3_MODE_Y2) return launch_u3<U3_MODE_Y2>(op, s);
   if (mode == U3_MODE_C3) return launch_u3<U3_MODE_C3>(op, s);
   if (mode == U3_MODE_G3) return launch_u3<U3_MODE_G3>(op, s);
+  if (mode == U3_MODE_Y3) return launch_u3<U3_MODE_Y3>(op, s);
   return RLU_EINVAL;
 }
 

@@ -16,6 +16,10 @@
 //               three parts as the 128-row operand and 256 columns of A as the other, one
 //               k-step moves 40 KB into shared memory for six 128 x 256 x 16 MMAs.
 //
+//   UB_MODE_Y3  Y = A Z (the power iterations of Section 5): A as in UB_MODE_Y, Z in three
+//               BF16 parts (FP32 accurate; Z is not a random matrix whose rounding is
+//               harmless), three products A Z_hi + A Z_mid + A Z_lo; N tiles of 128.
+//
 // N tiles: BN columns each, the last one only as wide as the columns left (rounded up to
 // 16), so that no MMA work is spent on padding.
 //
@@ -123,6 +127,7 @@ __host__ __device__ constexpr uint32_t ub_idesc(int M, int N, bool b_mn) {
 }
 
 // One ring slot. Y: a0 = A tile (128 x 64, K-major), b0 = G tile (BN x 64).
+// Y3: a0 = A tile, b0..b2 = the Z parts (BN x 64 each).
 // C3: a0..a2 = the L~ parts (128 x 32 each, K-major), b0 = four 64 (n) x 32 (m) boxes of A.
 struct UbLayout {
   uint32_t a0, a1, a2, b0, stage, tx;
@@ -132,6 +137,9 @@ __host__ __device__ inline UbLayout ub_layout(int mode, int BN) {
   if (mode == UB_MODE_Y) {
     const uint32_t at = UB_BM * 128, bt = (uint32_t)BN * 128;
     L.a0 = L.a1 = L.a2 = 0; L.b0 = at; L.stage = at + bt;
+  } else if (mode == UB_MODE_Y3) {
+    const uint32_t at = UB_BM * 128, bt = (uint32_t)BN * 128;
+    L.a0 = 0; L.b0 = at; L.a1 = at + bt; L.a2 = at + 2 * bt; L.stage = at + 3 * bt;
   } else {
     const uint32_t pt = UB_BM * 64;  // one part: 128 rows of 64 bytes
     L.a0 = 0; L.a1 = pt; L.a2 = 2 * pt; L.b0 = 3 * pt;
@@ -157,10 +165,11 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
   // The CTAs that read the same tiles of BF16 A run together, so that A is fetched from
   // DRAM once and the other CTAs hit L2. Y: grid x = (row tile, N tile), N tile fastest.
   // C3: A is the N operand, grid x = (N tile, row tile), row tile fastest.
-  constexpr int BK = MODE == UB_MODE_Y ? UB_BK : UB_BKC;
+  constexpr bool YM = MODE == UB_MODE_Y || MODE == UB_MODE_Y3;  // A is the M operand
+  constexpr int BK = YM ? UB_BK : UB_BKC;
   const int mtiles = (a.M + UB_BM - 1) / UB_BM;
-  const int mt = MODE == UB_MODE_Y ? (int)blockIdx.x / a.ntiles : (int)blockIdx.x % mtiles;
-  const int nt = MODE == UB_MODE_Y ? (int)blockIdx.x % a.ntiles : (int)blockIdx.x / mtiles;
+  const int mt = YM ? (int)blockIdx.x / a.ntiles : (int)blockIdx.x % mtiles;
+  const int nt = YM ? (int)blockIdx.x % a.ntiles : (int)blockIdx.x / mtiles;
   const int m0 = mt * UB_BM;
   const int kz = blockIdx.y;
   const int nb0 = nt * a.BN;
@@ -205,6 +214,12 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
         mb_expect_tx(bar, narrow ? lay.tx - (uint32_t)(a.BN - bn) * 128u : lay.tx);
         tma2d(base + lay.a0, &mA, kx, m0, bar);
         tma2d(base + lay.b0, narrow ? &mB1 : &mB0, kx, nb0, bar);
+      } else if (MODE == UB_MODE_Y3) {
+        mb_expect_tx(bar, lay.tx);
+        tma2d(base + lay.a0, &mA, kx, m0, bar);
+        tma2d(base + lay.b0, &mB0, kx, nb0, bar);  // Z parts: x = K, y = N
+        tma2d(base + lay.a1, &mB1, kx, nb0, bar);
+        tma2d(base + lay.a2, &mB2, kx, nb0, bar);
       } else {
         mb_expect_tx(bar, lay.tx);
         tma2d(base + lay.a0, &mB0, kx, m0, bar);  // L~ parts: x = m (32 wide), y = k (128)
@@ -232,6 +247,15 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
           const uint32_t off = kk * 32;
           mma_bf16(tmem, desc_sw128(base + lay.a0 + off), desc_sw128(base + lay.b0 + off), idesc,
                    (kt > 0 || kk > 0) ? 1u : 0u);
+        }
+      } else if (MODE == UB_MODE_Y3) {  // 4 x 3 MMAs of K = 16, the three parts of Z
+#pragma unroll
+        for (int kk = 0; kk < UB_BK / 16; ++kk) {
+          const uint32_t off = kk * 32;
+          const uint64_t da = desc_sw128(base + lay.a0 + off);
+          mma_bf16(tmem, da, desc_sw128(base + lay.b0 + off), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(tmem, da, desc_sw128(base + lay.a1 + off), idesc, 1u);
+          mma_bf16(tmem, da, desc_sw128(base + lay.a2 + off), idesc, 1u);
         }
       } else {  // 2 x 3 MMAs of K = 16: 32 bytes along the parts' rows, 16 rows of the A boxes
 #pragma unroll
@@ -337,8 +361,9 @@ template <int MODE>
 static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
   if (op.M <= 0 || op.N <= 0 || op.K <= 0) return RLU_EINVAL;
   // N tiles of up to 256 columns (C3: whole 64-column boxes of A)
-  constexpr int BK = MODE == UB_MODE_Y ? UB_BK : UB_BKC;
-  const int BN = op.N > 256 ? 256 : (int)round_up(op.N, MODE == UB_MODE_Y ? 16 : 64);
+  constexpr int BK = MODE == UB_MODE_C3 ? UB_BKC : UB_BK;
+  const int bnmax = MODE == UB_MODE_Y3 ? 128 : 256;
+  const int BN = op.N > bnmax ? bnmax : (int)round_up(op.N, MODE == UB_MODE_C3 ? 64 : 16);
   const int ntiles = (int)ceil_div(op.N, BN);
   const int bn_last = (int)round_up(op.N - (int64_t)(ntiles - 1) * BN, 16);
   const UbLayout lay = ub_layout(MODE, BN);
@@ -358,6 +383,11 @@ static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
     RLU_TRY(map2d_bf16(&b0, op.B0, op.N, op.K, op.ldb, UB_BK, BN, SW128));
     RLU_TRY(map2d_bf16(&b1, op.B0, op.N, op.K, op.ldb, UB_BK, bn_last, SW128));
     b2 = b0;
+  } else if (MODE == UB_MODE_Y3) {
+    RLU_TRY(map2d_bf16(&mA, op.A, op.M, op.K, op.lda, UB_BK, UB_BM, SW128));
+    RLU_TRY(map2d_bf16(&b0, op.B0, op.N, op.K, op.ldb, UB_BK, BN, SW128));
+    RLU_TRY(map2d_bf16(&b1, op.B1, op.N, op.K, op.ldb, UB_BK, BN, SW128));
+    RLU_TRY(map2d_bf16(&b2, op.B2, op.N, op.K, op.ldb, UB_BK, BN, SW128));
   } else {
     // A stored row-major K x N (rows = K index, N contiguous): boxes 64 (N) x 32 (K);
     // the L~ parts M x K (K contiguous): boxes 32 (K) x 128 (M)
@@ -403,6 +433,7 @@ static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
 int32_t umma_bf16_gemm(int mode, const UmmaBf16Op& op, cudaStream_t s) {
   if (mode == UB_MODE_Y) return launch_ub<UB_MODE_Y>(op, s);
   if (mode == UB_MODE_C3) return launch_ub<UB_MODE_C3>(op, s);
+  if (mode == UB_MODE_Y3) return launch_ub<UB_MODE_Y3>(op, s);
   return RLU_EINVAL;
 }
 

@@ -33,7 +33,8 @@ EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian"
             "rlu_reconstruct_error_static", "rlu_server_create", "rlu_server_submit",
             "rlu_server_poll", "rlu_server_wait_all", "rlu_server_stats", "rlu_server_destroy",
             "rlu_batch_workspace_size", "rlu_batch_create", "rlu_factor_batched",
-            "rlu_batch_launches", "rlu_batch_destroy")
+            "rlu_batch_launches", "rlu_batch_destroy", "rlu_workspace_size_power",
+            "rlu_factor_power")
 
 RLU_REQ_QUEUED, RLU_REQ_RUNNING, RLU_REQ_DONE, RLU_REQ_FAILED = 0, 1, 2, 3
 
@@ -104,6 +105,11 @@ def load_library(require_cuda: bool = True) -> ctypes.CDLL:
     lib.rlu_factor.argtypes = fac + [vp]
     lib.rlu_factor_stages.restype = i32
     lib.rlu_factor_stages.argtypes = fac + [ctypes.POINTER(_StageOutputs), vp]
+    lib.rlu_workspace_size_power.restype = sz
+    lib.rlu_workspace_size_power.argtypes = [i64, i64, i32, i32, i32, i32]
+    lib.rlu_factor_power.restype = i32
+    lib.rlu_factor_power.argtypes = fac[:9] + [i32] + fac[9:] + [ctypes.POINTER(_StageOutputs),
+                                                                vp]
     lib.rlu_timed_step_name.restype = ctypes.c_char_p
     lib.rlu_timed_step_name.argtypes = [i32]
     lib.rlu_launch_count.restype = ctypes.c_uint64
@@ -190,13 +196,14 @@ class Factorizer:
     """Reusable buffers (outputs, workspace, info) for repeated rlu_factor calls of one
     size and precision."""
 
-    def __init__(self, m: int, n: int, k: int, l: int, prec: int | str = RLU_PREC_F32):
+    def __init__(self, m: int, n: int, k: int, l: int, prec: int | str = RLU_PREC_F32,
+                 q: int = 0):
         self.lib = load_library()
         self.prec = PREC_BY_NAME[prec] if isinstance(prec, str) else int(prec)
-        self.m, self.n, self.k, self.l = m, n, k, l
+        self.m, self.n, self.k, self.l, self.q = m, n, k, l, q
         dt = _TORCH_OF_PREC[self.prec]
         self.dtype = dt
-        ws = self.lib.rlu_workspace_size(m, n, k, l, self.prec)
+        ws = self.lib.rlu_workspace_size_power(m, n, k, l, self.prec, q)
         if ws == 0:
             raise RluError(f"invalid sizes m={m} n={n} k={k} l={l} prec={self.prec}")
         self.workspace = torch.empty(ws, dtype=torch.uint8, device="cuda")
@@ -216,8 +223,11 @@ class Factorizer:
                 _dev_ptr(self.P), _dev_ptr(self.Q), _dev_ptr(self.L), self.L.stride(1),
                 _dev_ptr(self.U), self.U.stride(0), _dev_ptr(self.info),
                 _dev_ptr(self.workspace), self.workspace.numel()]
-        if stages is None:
+        if stages is None and self.q == 0:
             st = self.lib.rlu_factor(*args, _stream_ptr(stream))
+        elif stages is None:
+            st = self.lib.rlu_factor_power(*args[:9], self.q, *args[9:], None,
+                                           _stream_ptr(stream))
         else:
             ev = stages.get("events")
             ev_arr, n_ev = None, 0
@@ -231,7 +241,8 @@ class Factorizer:
                                _dev_ptr(stages.get("Ly")), _dev_ptr(stages.get("B")),
                                ctypes.cast(ev_arr, ctypes.POINTER(ctypes.c_void_p))
                                if ev_arr is not None else None, n_ev)
-            st = self.lib.rlu_factor_stages(*args, ctypes.byref(so), _stream_ptr(stream))
+            st = self.lib.rlu_factor_power(*args[:9], self.q, *args[9:], ctypes.byref(so),
+                                           _stream_ptr(stream))
         _check(st, "rlu_factor")
         return self.P, self.Q, self.L, self.U, self.info
 
@@ -244,13 +255,13 @@ class Factorizer:
 
 
 def factor(A: torch.Tensor, k: int, l: int, seed: int, prec: int | str | None = None,
-           stages: bool = False) -> dict:
+           stages: bool = False, q: int = 0) -> dict:
     """One randomized LU of A (CUDA tensor, row-major). Returns P, Q, L, U, info (device
     tensors) and, with ``stages=True``, the intermediates G, Y, Ly, B."""
     if prec is None:
         prec = {torch.float64: RLU_PREC_F64, torch.bfloat16: RLU_PREC_BF16}.get(A.dtype,
                                                                                RLU_PREC_F32)
-    f = Factorizer(A.shape[0], A.shape[1], k, l, prec)
+    f = Factorizer(A.shape[0], A.shape[1], k, l, prec, q)
     st = f.stage_buffers() if stages else None
     P, Q, L, U, info = f(A, seed, stages=st)
     out = {"P": P, "Q": Q, "L": L, "U": U, "info": info}

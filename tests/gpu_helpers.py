@@ -7,10 +7,11 @@ import oracle as O
 from paper_1310_7202_gb300 import rlu
 
 
-def run_gpu(A: np.ndarray, k: int, l: int, seed: int, prec: str):
-    """Factor A on the GPU through rlu_factor_stages; returns numpy copies."""
+def run_gpu(A: np.ndarray, k: int, l: int, seed: int, prec: str, q: int = 0):
+    """Factor A on the GPU through rlu_factor_power (q power iterations) with the stage
+    outputs; returns numpy copies."""
     At = torch.from_numpy(np.ascontiguousarray(A)).cuda()
-    f = rlu.Factorizer(A.shape[0], A.shape[1], k, l, prec)
+    f = rlu.Factorizer(A.shape[0], A.shape[1], k, l, prec, q)
     st = f.stage_buffers()
     P, Q, L, U, info = f(At, seed, stages=st)
     torch.cuda.synchronize()
@@ -22,12 +23,12 @@ def run_gpu(A: np.ndarray, k: int, l: int, seed: int, prec: str):
     return out
 
 
-def oracle_for(A: np.ndarray, k: int, l: int, seed: int, prec: str):
+def oracle_for(A: np.ndarray, k: int, l: int, seed: int, prec: str, q: int = 0):
     """The oracle on the same stored A; the FP32 path's G definition for prec 'f32'."""
     G = None
     if prec == "f32":
         G = O.gaussian_f32(seed, 0, A.shape[1], l).astype(np.float64)
-    return O.rlu_factor(np.asarray(A, dtype=np.float64), k, l, seed=seed, G=G)
+    return O.rlu_factor(np.asarray(A, dtype=np.float64), k, l, seed=seed, G=G, q=q)
 
 
 def rel_max(a, b) -> float:
