@@ -16,7 +16,7 @@ from .rlu_oracle import (  # noqa: F401
     series_ln, series_sincos_2pi, box_muller, gaussian,
     box_muller_f32, gaussian_f32,
     lu_partial_pivot, lu_column_pivot, pinv_apply, project,
-    rlu_factor, reconstruct_error, spectral_norm,
+    rlu_factor, reconstruct_error, spectral_norm, rdls_apply, rdls_solve,
     theorem1_constant, theorem1_success_probability, theorem1_failure_terms,
     check_dims,
 )

@@ -392,6 +392,38 @@ def rlu_factor(A: np.ndarray, k: int, l: int, seed: int, stream_id: int = 0,
 
 
 # ---------------------------------------------------------------------------------------
+# Algorithm 3 (Section 5, "Rank Deficient Least Squares"): min ||A x - b|| from the factors
+# of Algorithm 1. With A ~ P^T L U Q^T: c = P b, y = L^+ c (a full-rank least-squares
+# problem, normal equations as in step 5), z_1 = U_1^{-1} y with U_1 the leading k x k block
+# of U, z = (z_1, 0), x = Q z. In the gather convention (P A Q)[i][j] = A[P[i]][Q[j]]:
+# c[i] = b[P[i]] and x[Q[j]] = z[j].
+# ---------------------------------------------------------------------------------------
+
+def rdls_apply(P, Q, L, U, b: np.ndarray) -> np.ndarray:
+    """Steps 2-5 of Algorithm 3 on given factors; b is m or m x r (r right-hand sides)."""
+    b = np.asarray(b, dtype=np.float64)
+    vec = b.ndim == 1
+    B = b.reshape(b.shape[0], -1)
+    L = np.asarray(L, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64)
+    k = L.shape[1]
+    n = U.shape[1]
+    c = B[np.asarray(P)]                        # step 2: c = P b
+    y = pinv_apply(L, c)                        #         y = L^+ c
+    z1 = _solve_upper(U[:, :k], y)              # step 3: z_1 = U_1^{-1} y
+    X = np.zeros((n, B.shape[1]))
+    X[np.asarray(Q)[:k]] = z1                   # steps 4-5: z = (z_1, 0), x = Q z
+    return X[:, 0] if vec else X
+
+
+def rdls_solve(A: np.ndarray, b: np.ndarray, k: int, l: int, seed: int, q: int = 0) -> dict:
+    """Algorithm 3: step 1 is Algorithm 1 on A; returns x and the factors."""
+    res = rlu_factor(A, k, l, seed, q=q)
+    res["x"] = rdls_apply(res["P"], res["Q"], res["L"], res["U"], b)
+    return res
+
+
+# ---------------------------------------------------------------------------------------
 # Error of Eq. (1): ||L U - P A Q||, spectral (the paper's norm) and Frobenius.
 # ---------------------------------------------------------------------------------------
 

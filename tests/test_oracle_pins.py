@@ -298,6 +298,47 @@ def test_power_iteration_keeps_exact_rank():
         assert fro / np.linalg.norm(A) < 1e-12
 
 
+# ----------------------------------------------------------------------------------------
+# Algorithm 3 (rank-deficient least squares, Section 5).
+# ----------------------------------------------------------------------------------------
+
+def test_rdls_exact_rank_reaches_the_least_squares_minimum():
+    """For rank(A) = k the randomized LU is exact, so x attains the least-squares minimum:
+    the residual equals numpy.linalg.lstsq's, A^T (A x - b) = 0 (normal equations of the
+    original problem), and x has at most k nonzero entries. A consistent b = A x0 is met to
+    rounding."""
+    m, n, k, l = 160, 120, 9, 14
+    A = synth.prescribed_matrix(m, n, synth.spectrum("rank_k", n, k), 5, 6)
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal((m, 3))
+    res = O.rdls_solve(A, b, k, l, seed=2)
+    x = res["x"]
+    x_ls = np.linalg.lstsq(A, b, rcond=None)[0]
+    r_min = np.linalg.norm(A @ x_ls - b, axis=0)
+    assert np.allclose(np.linalg.norm(A @ x - b, axis=0), r_min, rtol=1e-10, atol=1e-12)
+    assert np.abs(A.T @ (A @ x - b)).max() < 1e-10 * np.abs(A.T @ b).max()
+    assert all(np.count_nonzero(x[:, j]) <= k for j in range(3))
+    x0 = rng.standard_normal(n)
+    xv = O.rdls_apply(res["P"], res["Q"], res["L"], res["U"], A @ x0)
+    assert np.linalg.norm(A @ xv - A @ x0) < 1e-11 * np.linalg.norm(A @ x0)
+
+
+def test_rdls_permutation_conventions_by_brute_force():
+    """Tiny case against a brute-force restatement with explicit permutation matrices: A
+    approximated by P^T L U Q^T, y = argmin ||L y - P b||, z_1 = U_1^{-1} y, x = Q (z_1, 0)."""
+    m, n, k, l = 12, 9, 3, 5
+    A = synth.prescribed_matrix(m, n, synth.spectrum("rank_k", n, k), 7, 8)
+    b = np.random.default_rng(2).standard_normal(m)
+    res = O.rdls_solve(A, b, k, l, seed=3)
+    Pm = np.eye(m)[res["P"]]          # (Pm A)[i] = A[P[i]]
+    Qm = np.eye(n)[:, res["Q"]]       # (A Qm)[:, j] = A[:, Q[j]]
+    assert np.allclose(Pm @ A @ Qm, res["L"] @ res["U"], atol=1e-12)
+    y = np.linalg.lstsq(res["L"], Pm @ b, rcond=None)[0]
+    z = np.zeros(n)
+    z[:k] = np.linalg.solve(res["U"][:, :k], y)
+    assert np.allclose(res["x"], Qm @ z, atol=1e-12)
+
+
 def test_full_rank_k_equals_n_is_exact_lu():
     n = 24
     rng = np.random.default_rng(4)
