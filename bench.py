@@ -546,6 +546,32 @@ def run_ours(args):
                        "workspace and outputs; the same input"}
         del fzb
 
+    # ---- Algorithm 3 (rank-deficient least squares) on the factors of the last run ----
+    lstsq = None
+    if not args.no_power:
+        lstsq = {"nrhs": [], "ms": []}
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(11)
+        for r in (1, 16):
+            bb = torch.randn((r, m), generator=gen, device="cuda", dtype=L.dtype).t()
+            for _ in range(3):
+                xx = rlu.lstsq(P, Q, L, U, bb)
+            torch.cuda.synchronize()
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            for _ in range(10):
+                xx = rlu.lstsq(P, Q, L, U, bb)
+            l1.record(stream)
+            torch.cuda.synchronize()
+            lstsq["nrhs"].append(r)
+            lstsq["ms"].append(l0.elapsed_time(l1) / 10)
+            if r == 1:
+                # Algorithm 3 minimises over the factored operator: ||L U Q^T x - P b||, with
+                # (Q^T x)[j] = x[Q[j]] and (P b)[i] = b[P[i]] in the gather convention
+                xq = xx[Q.long()]
+                res = torch.linalg.vector_norm(L @ (U @ xq) - bb[P.long()]).item()
+                lstsq["rel_residual_factored_nrhs1"] = res / torch.linalg.vector_norm(bb).item()
+
     # ---- power iterations (Section 5): Y = (A A^T)^q A G with q = 1, same input ------
     power = None
     if prec in ("mixed", "bf16", "f32", "f64") and sigma is not None and not args.no_power:
@@ -611,6 +637,7 @@ def run_ours(args):
         "plain_fp32": plain,
         "two_in_flight": two,
         "power": power,
+        "lstsq": lstsq,
         "serve": serve,
         "clocks": clocks.summary(),
         "e2e": e2e,

@@ -184,6 +184,28 @@ int32_t rlu_factor_power(const void* A, int32_t dtype, int64_t m, int64_t n, int
                          rlu_info* info, void* workspace, size_t ws_bytes,
                          const rlu_stage_outputs* stages, void* stream);
 
+/* Algorithm 3 (Section 5, "Rank Deficient Least Squares"): x minimising ||A x - b|| from
+ * the factors of Algorithm 1 (A ~ P^T L U Q^T): c = P b (c[i] = b[P[i]]), y = L^+ c by the
+ * normal equations (FP64 Gram, the LDL^T and blocked substitution of step 5),
+ * z_1 = U_1^{-1} y with U_1 = U[:, 0:k], z = (z_1, 0), x = Q z (x[Q[j]] = z[j]): x has at
+ * most k nonzero entries.
+ *   dtype      : RLU_F32 or RLU_F64, the type of L, U, b and x (as rlu_factor wrote them).
+ *   P (m), Q (n), L (m x k, column-major, ldl >= m), U (k x n, row-major, ldu >= n): the
+ *              factors, device memory, unchanged.
+ *   b          : m x nrhs column-major (ldb >= m); x: n x nrhs column-major (ldx >= n),
+ *                output. nrhs >= 1.
+ *   info       : device rlu_info (may be NULL): status RLU_EINVAL if L^T L is not positive
+ *                definite; first_zero_pivot_b = a zero diagonal entry of U_1 (that entry
+ *                of z_1 is set to 0).
+ *   workspace  : rlu_lstsq_workspace_size bytes, 256-byte aligned.
+ * Errors: RLU_EINVAL (NULL pointers, strides, k outside [1, min(m, n)]), RLU_EUNSUPPORTED
+ * (dtype, k > 4096), RLU_ENOMEM, RLU_ECUDA. Asynchronous on stream. */
+size_t rlu_lstsq_workspace_size(int64_t m, int64_t n, int32_t k, int32_t nrhs, int32_t dtype);
+int32_t rlu_lstsq(int32_t dtype, int64_t m, int64_t n, int32_t k, const int32_t* P,
+                  const int32_t* Q, const void* L, int64_t ldl, const void* U, int64_t ldu,
+                  const void* b, int64_t ldb, int32_t nrhs, void* x, int64_t ldx,
+                  rlu_info* info, void* workspace, size_t ws_bytes, void* stream);
+
 /* Bytes of workspace rlu_reconstruct_error needs. */
 size_t rlu_reconstruct_workspace_size(int64_t m, int64_t n, int32_t k);
 

@@ -112,6 +112,7 @@ struct Plan {
   int split_z = 1, split_y3 = 1;  // their products Z = A^T Y and Y = A Z
   size_t off_Z = 0, off_Yh = 0, off_Yl = 0, off_Zh = 0, off_Zl = 0, off_Yb[3] = {0, 0, 0},
          off_Zb[3] = {0, 0, 0};
+  size_t off_Lbh = 0, off_Lbl = 0;  // TF32 split of L_b (k x k, ld round_up(k, 4))
   size_t off_G = 0, off_Y = 0, off_Lt = 0, off_Lp = 0, off_M = 0, off_dinv = 0, off_LT = 0,
          off_LR = 0, off_W = 0, off_WT = 0,
          off_C = 0, off_T = 0, off_B = 0, off_Lb = 0, off_part = 0, off_Lhi = 0, off_Llo = 0,
@@ -199,6 +200,8 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p,
   if (prec == RLU_PREC_MIXED || prec == RLU_PREC_BF16) {
     p.off_Lhi = carve(cur, (size_t)p.ldl * k * e);
     p.off_Llo = carve(cur, (size_t)p.ldl * k * e);
+    p.off_Lbh = carve(cur, (size_t)round_up(k, 4) * k * 4);
+    p.off_Lbl = carve(cur, (size_t)round_up(k, 4) * k * 4);
   }
   if (prec == RLU_PREC_BF16) {  // L~ in three BF16 parts for the products with BF16 A
     p.off_Bh = carve(cur, (size_t)p.ldl * k * 2);
@@ -532,7 +535,29 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
   RLU_TRY(tm.rec(9, true, s));
   // step 7: L = L_y L_b
   RLU_TRY(tm.rec(10, false, s));
-  {
+  if (p.off_Lbh) {  // three TF32 products: L_y (column-major, i.e. K x M row-major) is
+                    // transposed and split on chip as in the C product; L_b pre-split
+    float* Lbh = reinterpret_cast<float*>(ws + p.off_Lbh);
+    float* Lbl = reinterpret_cast<float*>(ws + p.off_Lbl);
+    const int64_t kb = round_up(k, 4);
+    RLU_TRY(split_parts(reinterpret_cast<const float*>(Lb), k, k, k, Lbh, Lbl, Bf16Parts{}, s,
+                        kb));
+    Umma3Op op{};
+    op.A0 = reinterpret_cast<const float*>(Lp);
+    op.lda = p.ldl;
+    op.B0 = Lbh;
+    op.B1 = Lbl;
+    op.ldb = kb;
+    op.M = m;
+    op.N = k;
+    op.K = k;
+    op.out = reinterpret_cast<float*>(L);
+    op.ldo = ldl_out;
+    op.out_colmajor = true;
+    op.splits = 1;
+    op.status = info ? &info->status : nullptr;
+    RLU_TRY(umma3_gemm(U3_MODE_C3, op, s));
+  } else {
     GemmOp op{Lp, p.ldl, false, Lb, k, true, L, ldl_out, false, m, k, k, 1, nullptr, false};
     RLU_TRY((gemm_simt<T, T>(op, s)));
   }

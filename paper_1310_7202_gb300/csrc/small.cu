@@ -65,23 +65,25 @@ __global__ void k_build_ly(const T* __restrict__ Y, int64_t ldy, int64_t m, int 
 // exact TF32 pairs (hi, lo; when hi != NULL) and/or three BF16 parts (when bp.hi != NULL),
 // written with the same ld.
 __global__ void k_split_parts(const float* __restrict__ X, int64_t ld, int64_t rows, int cols,
-                              float* __restrict__ hi, float* __restrict__ lo, Bf16Parts bp) {
+                              float* __restrict__ hi, float* __restrict__ lo, Bf16Parts bp,
+                              int64_t ldo) {
   const int c = blockIdx.y;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
        r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t at = (int64_t)c * ld + r;
-    const float v = X[at];
+    const float v = X[(int64_t)c * ld + r];
+    const int64_t at = (int64_t)c * ldo + r;
     if (hi) tf32_split(v, hi, lo, at);
     if (bp.hi) bf16_split3(v, bp.hi, bp.mid, bp.lo, at);
   }
 }
 
 int32_t split_parts(const float* X, int64_t ld, int64_t rows, int cols, float* hi, float* lo,
-                    Bf16Parts bp, cudaStream_t s) {
+                    Bf16Parts bp, cudaStream_t s, int64_t ldo) {
   if (rows <= 0 || cols <= 0) return RLU_OK;
   int64_t bx = ceil_div(rows, 256);
   if (bx > 1024) bx = 1024;
-  k_split_parts<<<dim3((unsigned)bx, (unsigned)cols), 256, 0, s>>>(X, ld, rows, cols, hi, lo, bp);
+  k_split_parts<<<dim3((unsigned)bx, (unsigned)cols), 256, 0, s>>>(X, ld, rows, cols, hi, lo, bp,
+                                                                  ldo > 0 ? ldo : ld);
   return last_launch_status();
 }
 

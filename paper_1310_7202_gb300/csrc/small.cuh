@@ -12,11 +12,11 @@ struct Bf16Parts {
   __nv_bfloat16* lo = nullptr;
 };
 
-// Exact TF32 pairs (hi, lo) and/or three BF16 parts of a column-major FP32 matrix, same ld
-// (the operands of the FP32-accurate products of the power iterations); null outputs are
-// skipped.
+// Exact TF32 pairs (hi, lo) and/or three BF16 parts of a column-major FP32 matrix (the
+// operands of FP32-accurate tensor-core products), written with ld ldo (0: the input's ld);
+// null outputs are skipped.
 int32_t split_parts(const float* X, int64_t ld, int64_t rows, int cols, float* hi, float* lo,
-                    Bf16Parts bp, cudaStream_t s);
+                    Bf16Parts bp, cudaStream_t s, int64_t ldo = 0);
 
 template <typename T>
 int32_t build_ly(const T* Y, int64_t ldy, int64_t m, int k, const int32_t* perm, T* Lt, T* Lp,

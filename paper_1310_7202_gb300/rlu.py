@@ -34,7 +34,7 @@ EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian"
             "rlu_server_poll", "rlu_server_wait_all", "rlu_server_stats", "rlu_server_destroy",
             "rlu_batch_workspace_size", "rlu_batch_create", "rlu_factor_batched",
             "rlu_batch_launches", "rlu_batch_destroy", "rlu_workspace_size_power",
-            "rlu_factor_power")
+            "rlu_factor_power", "rlu_lstsq_workspace_size", "rlu_lstsq")
 
 RLU_REQ_QUEUED, RLU_REQ_RUNNING, RLU_REQ_DONE, RLU_REQ_FAILED = 0, 1, 2, 3
 
@@ -105,6 +105,11 @@ def load_library(require_cuda: bool = True) -> ctypes.CDLL:
     lib.rlu_factor.argtypes = fac + [vp]
     lib.rlu_factor_stages.restype = i32
     lib.rlu_factor_stages.argtypes = fac + [ctypes.POINTER(_StageOutputs), vp]
+    lib.rlu_lstsq_workspace_size.restype = sz
+    lib.rlu_lstsq_workspace_size.argtypes = [i64, i64, i32, i32, i32]
+    lib.rlu_lstsq.restype = i32
+    lib.rlu_lstsq.argtypes = [i32, i64, i64, i32, vp, vp, vp, i64, vp, i64, vp, i64, i32, vp,
+                              i64, vp, vp, sz, vp]
     lib.rlu_workspace_size_power.restype = sz
     lib.rlu_workspace_size_power.argtypes = [i64, i64, i32, i32, i32, i32]
     lib.rlu_factor_power.restype = i32
@@ -268,6 +273,34 @@ def factor(A: torch.Tensor, k: int, l: int, seed: int, prec: int | str | None = 
     if st:
         out.update(st)
     return out
+
+
+def lstsq(P: torch.Tensor, Q: torch.Tensor, L: torch.Tensor, U: torch.Tensor,
+          b: torch.Tensor, info: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Algorithm 3: x (n, or n x r) minimising ||A x - b|| from the factors of rlu_factor
+    (L column-major, U row-major, b of L's dtype: (m,) or (m, r) column-major)."""
+    lib = load_library()
+    m, k = L.shape
+    n = U.shape[1]
+    if L.stride(0) != 1 or U.stride(1) != 1:
+        raise RluError("L must be column-major and U row-major")
+    vec = b.dim() == 1
+    B = b.reshape(m, 1) if vec else b
+    if B.stride(0) != 1:
+        B = B.t().contiguous().t()
+    r = B.shape[1]
+    X = torch.empty((r, n), dtype=L.dtype, device="cuda").t()
+    dt = _DT_OF_TORCH[L.dtype]
+    ws_n = lib.rlu_lstsq_workspace_size(m, n, k, r, dt)
+    if ws_n == 0:
+        raise RluError(f"invalid sizes m={m} n={n} k={k} nrhs={r}")
+    ws = torch.empty(ws_n, dtype=torch.uint8, device="cuda")
+    _check(lib.rlu_lstsq(dt, m, n, k, _dev_ptr(P), _dev_ptr(Q), _dev_ptr(L), L.stride(1),
+                         _dev_ptr(U), U.stride(0), _dev_ptr(B), B.stride(1) if r > 1 else m,
+                         r, _dev_ptr(X), X.stride(1) if r > 1 else n, _dev_ptr(info),
+                         _dev_ptr(ws), ws_n, _stream_ptr(stream)),
+           "rlu_lstsq")
+    return X[:, 0] if vec else X
 
 
 def timed_step_names() -> list[str]:
