@@ -174,8 +174,10 @@ STAGE_SOURCE = {"gaussian": "gauss.cu", "gemm_Y": "gemm_simt.cu", "lu_Y": "lu_re
                 "gemm_C": "gemm_simt.cu", "trsm_B": "small.cu", "lu_B": "lu_reg.cu",
                 "gather_Lb_U": "small.cu", "gemm_L": "gemm_simt.cu"}
 # the mixed path runs its three large products on the tensor cores
-MIXED_SOURCE = {"gemm_Y": "umma3.cu", "gram": "umma3.cu", "gemm_C": "umma3.cu"}
-BF16_SOURCE = {"gemm_Y": "umma_bf16.cu", "gram": "umma3.cu", "gemm_C": "umma_bf16.cu"}
+MIXED_SOURCE = {"gemm_Y": "umma3.cu", "gram": "umma3.cu", "gemm_C": "umma3.cu",
+                "gemm_L": "umma3.cu"}
+BF16_SOURCE = {"gemm_Y": "umma_bf16.cu", "gram": "umma3.cu", "gemm_C": "umma_bf16.cu",
+               "gemm_L": "umma3.cu"}
 
 
 def source_sha(stage: str, prec: str = "f32") -> str:

@@ -778,7 +778,9 @@ static int32_t launch_reg_t(const LuArgs& a, cudaStream_t s, bool* launched) {
   // rows per thread RT, register panel NB (NB - 1 columns per panel), threads per CTA
   constexpr int W1 = sizeof(T) == 4 ? 77 : 37;
   constexpr int W2 = sizeof(T) == 4 ? 37 : 19;
-  constexpr int W4 = sizeof(T) == 4 ? 11 : 7;  // no spills at 4 rows per thread
+  // 4 rows per thread: 18 FP32 columns per panel spill ~48 bytes but halve the panel
+  // launches against 10 columns (LU of Y at 32768 x 532: 2.16 -> 2.06 ms)
+  constexpr int W4 = sizeof(T) == 4 ? 19 : 7;
   if (a.R <= 16 * 512) RLU_TRY((try_launch<T, CROUT, 1, W1, 512>(a, s, launched)));
   if (!*launched && a.R <= 16 * 1024) RLU_TRY((try_launch<T, CROUT, 2, W2, 512>(a, s, launched)));
   if (!*launched && a.R <= 16 * 2048) RLU_TRY((try_launch<T, CROUT, 4, W4, 512>(a, s, launched)));
