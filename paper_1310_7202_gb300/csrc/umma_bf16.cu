@@ -126,7 +126,7 @@ __host__ __device__ constexpr uint32_t ub_idesc(int M, int N, bool b_mn) {
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// One ring slot. Y: a0 = A tile (128 x 64, K-major), b0 = G tile (BN x 64).
+// One ring slot. Y: a0, a1 = two A tiles (128 x 64 each, K-major), b0 = G tile (BN x 64).
 // Y3: a0 = A tile, b0..b2 = the Z parts (BN x 64 each).
 // C3: a0..a2 = the L~ parts (128 x 32 each, K-major), b0 = four 64 (n) x 32 (m) boxes of A.
 struct UbLayout {
@@ -134,9 +134,9 @@ struct UbLayout {
 };
 __host__ __device__ inline UbLayout ub_layout(int mode, int BN) {
   UbLayout L{};
-  if (mode == UB_MODE_Y) {
+  if (mode == UB_MODE_Y) {  // two 128-row tiles of A (a0, a1) share the G tile
     const uint32_t at = UB_BM * 128, bt = (uint32_t)BN * 128;
-    L.a0 = L.a1 = L.a2 = 0; L.b0 = at; L.stage = at + bt;
+    L.a0 = 0; L.a1 = at; L.a2 = 0; L.b0 = 2 * at; L.stage = 2 * at + bt;
   } else if (mode == UB_MODE_Y3) {
     const uint32_t at = UB_BM * 128, bt = (uint32_t)BN * 128;
     L.a0 = 0; L.b0 = at; L.a1 = at + bt; L.a2 = at + 2 * bt; L.stage = at + 3 * bt;
@@ -167,10 +167,14 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
   // C3: A is the N operand, grid x = (N tile, row tile), row tile fastest.
   constexpr bool YM = MODE == UB_MODE_Y || MODE == UB_MODE_Y3;  // A is the M operand
   constexpr int BK = YM ? UB_BK : UB_BKC;
-  const int mtiles = (a.M + UB_BM - 1) / UB_BM;
+  // Y: two 128-row accumulators per CTA (TMEM columns 0 and 256), one G tile for both, so
+  // that a k-step moves 64 KB for eight MMAs instead of 48 KB for four
+  constexpr int MT = MODE == UB_MODE_Y ? 2 : 1;
+  constexpr uint32_t TCOLS = MT == 2 ? 512u : 256u;
+  const int mtiles = (a.M + UB_BM * MT - 1) / (UB_BM * MT);
   const int mt = YM ? (int)blockIdx.x / a.ntiles : (int)blockIdx.x % mtiles;
   const int nt = YM ? (int)blockIdx.x % a.ntiles : (int)blockIdx.x / mtiles;
-  const int m0 = mt * UB_BM;
+  const int m0 = mt * UB_BM * MT;
   const int kz = blockIdx.y;
   const int nb0 = nt * a.BN;
   const int bn = nt == a.ntiles - 1 ? a.bn_last : a.BN;  // this tile's MMA width
@@ -188,8 +192,8 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n"
-                 ::"r"(su32(&sh.tmem_base)) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 ::"r"(su32(&sh.tmem_base)), "n"(TCOLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -213,6 +217,7 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
         const bool narrow = bn < a.BN;
         mb_expect_tx(bar, narrow ? lay.tx - (uint32_t)(a.BN - bn) * 128u : lay.tx);
         tma2d(base + lay.a0, &mA, kx, m0, bar);
+        tma2d(base + lay.a1, &mA, kx, m0 + UB_BM, bar);
         tma2d(base + lay.b0, narrow ? &mB1 : &mB0, kx, nb0, bar);
       } else if (MODE == UB_MODE_Y3) {
         mb_expect_tx(bar, lay.tx);
@@ -241,12 +246,14 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t base = tiles + s * lay.stage;
-      if (MODE == UB_MODE_Y) {  // 4 MMAs of K = 16 along the 128-byte rows
+      if (MODE == UB_MODE_Y) {  // 4 x 2 MMAs of K = 16 along the 128-byte rows
 #pragma unroll
         for (int kk = 0; kk < UB_BK / 16; ++kk) {
           const uint32_t off = kk * 32;
-          mma_bf16(tmem, desc_sw128(base + lay.a0 + off), desc_sw128(base + lay.b0 + off), idesc,
-                   (kt > 0 || kk > 0) ? 1u : 0u);
+          const uint64_t db = desc_sw128(base + lay.b0 + off);
+          const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+          mma_bf16(tmem, desc_sw128(base + lay.a0 + off), db, idesc, acc);
+          mma_bf16(tmem + 256u, desc_sw128(base + lay.a1 + off), db, idesc, acc);
         }
       } else if (MODE == UB_MODE_Y3) {  // 4 x 3 MMAs of K = 16, the three parts of Z
 #pragma unroll
@@ -276,12 +283,14 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
     if (!ok) sh.err = 1;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const int quarter = warp & 3;
-    const int row = m0 + quarter * 32 + lane;
     float* __restrict__ out = a.out + (size_t)kz * a.split_stride;
     const bool vec_out = ((uintptr_t)out % 16 == 0) && a.ldo % 4 == 0;
+    for (int t = 0; t < MT; ++t)
     for (int c0 = 0; c0 < bn; c0 += 32) {
+      const int row = m0 + t * UB_BM + quarter * 32 + lane;
       uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+      const uint32_t taddr =
+          tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * 256 + c0);
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
           "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
@@ -322,7 +331,8 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n"
+                 ::"r"(tmem), "n"(TCOLS) : "memory");
   }
   if (threadIdx.x == 0 && sh.err && a.status) atomicExch(a.status, RLU_ETIMEOUT);
 }
@@ -422,7 +432,8 @@ static int32_t launch_ub(const UmmaBf16Op& op, cudaStream_t s) {
   }
   auto kern = k_ummab<MODE>;
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)(ceil_div(op.M, UB_BM) * ntiles), (unsigned)splits);
+  const int rows_per_cta = MODE == UB_MODE_Y ? 2 * UB_BM : UB_BM;
+  dim3 grid((unsigned)(ceil_div(op.M, rows_per_cta) * ntiles), (unsigned)splits);
   kern<<<grid, UB_THREADS, smem, s>>>(mA, b0, b1, b2, a);
   RLU_TRY(last_launch_status());
   if (a.out == op.partial && op.out)
