@@ -34,6 +34,7 @@ def _bf16_case(m, n, k, l, spec, seed):
     (2048, 1024, 64, 74),     # whole tiles
     (1500, 1000, 37, 45),     # ragged M, N, K
     (3000, 2000, 300, 310),   # l > 256: two N tiles of Y; k = 300: three N tiles of C
+    (200, 160, 20, 24),       # one CTA of Y whose second 128-row tile is empty
 ])
 def test_bf16_factorization(m, n, k, l):
     At, A64, sigma, g = _bf16_case(m, n, k, l, "geometric_099", 7)
