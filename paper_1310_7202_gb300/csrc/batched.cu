@@ -42,8 +42,24 @@ struct ProblemLayout {
 
 struct Tables {
   size_t info, gauss, gemm_y, lu_y, build, gemm_g, ldl, gemm_c, trsm, lu_b, gather, gemm_l,
-      u3y, u3c;
+      u3y, u3c, u3y_tiles, u3c_tiles;
+  int n_tiles_y, n_tiles_c;  // 128-row tiles of the two tensor-core products
 };
+
+// LU group of a problem with R rows (see rlu_batch) and its rows per CTA: small problems
+// take one narrow CTA, so that several of them share an SM.
+int lu_group(int64_t R, int rows_per_cta, int* rpc) {
+  if (R <= 128) {
+    *rpc = 128;
+    return 17;
+  }
+  if (R <= 256 && rows_per_cta == 512) {
+    *rpc = 256;
+    return 18;
+  }
+  *rpc = rows_per_cta;
+  return (int)ceil_div(R, rows_per_cta);
+}
 
 bool valid_problem(const rlu_problem& p, int32_t prec) {
   if (!p.A || !p.P || !p.Q || !p.L || !p.U) return false;
@@ -72,10 +88,17 @@ size_t plan_layout(const rlu_problem* probs, int count, int32_t prec, Tables& t,
   t.lu_b = carve(cur, c * sizeof(LuArgs));
   t.gather = carve(cur, c * sizeof(GatherJob));
   t.gemm_l = carve(cur, c * sizeof(GemmArgs));
-  t.u3y = t.u3c = 0;
+  t.u3y = t.u3c = t.u3y_tiles = t.u3c_tiles = 0;
+  t.n_tiles_y = t.n_tiles_c = 0;
   if (prec == RLU_PREC_MIXED) {
     t.u3y = carve(cur, c * sizeof(U3Job));
     t.u3c = carve(cur, c * sizeof(U3Job));
+    for (int i = 0; i < count; ++i) {
+      t.n_tiles_y += (int)ceil_div(probs[i].m, 128);
+      t.n_tiles_c += (int)ceil_div(probs[i].n, 128);
+    }
+    t.u3y_tiles = carve(cur, (size_t)t.n_tiles_y * sizeof(int2));
+    t.u3c_tiles = carve(cur, (size_t)t.n_tiles_c * sizeof(int2));
   }
   for (int i = 0; i < count; ++i) {
     const rlu_problem& p = probs[i];
@@ -133,7 +156,10 @@ struct rlu_batch {
   rlu::Tables t{};
   int64_t max_m = 0, max_n = 0;
   int max_k = 0, max_l = 0, max_kp = 0;
-  int first_y[17] = {}, count_y[17] = {}, first_b[17] = {}, count_b[17] = {};
+  // LU groups: 1..16 = clusters of that many CTAs of lu_rows_per_cta rows; 17 / 18 = one CTA
+  // of 128 / 256 threads for problems of at most 128 / 256 rows
+  int first_y[rlu::kLuGroups] = {}, count_y[rlu::kLuGroups] = {}, first_b[rlu::kLuGroups] = {},
+      count_b[rlu::kLuGroups] = {};
   int launches = 0;
   int u3_stages = 0, u3_stage_bytes = 0;  // tensor-core ring of the mixed precision
   rlu_batch_options opt{};
@@ -240,14 +266,14 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
     u.zero_step = p.info ? &p.info->first_zero_pivot_y : nullptr;
     u.nonfinite = p.info ? &p.info->nonfinite : nullptr;
     u.status = p.info ? &p.info->status : nullptr;
-    u.posg = pos; u.psg = ps; u.p0 = 0; u.pw = p.l; u.rpc = opt.lu_rows_per_cta; u.nb = kMaxL;
+    u.posg = pos; u.psg = ps; u.p0 = 0; u.pw = p.l; u.nb = kMaxL;
+    gy_of[(size_t)i] = lu_group(p.m, opt.lu_rows_per_cta, &u.rpc);
     luy_all[(size_t)i] = u;
     u.X = Bb; u.ldx = L.ldb; u.R = (int)p.n; u.C = p.k; u.perm = p.Q;
     u.zero_step = p.info ? &p.info->first_zero_pivot_b : nullptr;
     u.pw = p.k;
+    gb_of[(size_t)i] = lu_group(p.n, opt.lu_rows_per_cta, &u.rpc);
     lub_all[(size_t)i] = u;
-    gy_of[(size_t)i] = (int)ceil_div(p.m, opt.lu_rows_per_cta);
-    gb_of[(size_t)i] = (int)ceil_div(p.n, opt.lu_rows_per_cta);
     float* Lhi = mixed ? reinterpret_cast<float*>(ws + L.Lhi) : nullptr;
     float* Llo = mixed ? reinterpret_cast<float*>(ws + L.Llo) : nullptr;
     build[(size_t)i] = BuildJob{Y, L.ldy, p.m, p.k, p.P, Lt, Lp, L.ldl, Lhi, Llo};
@@ -299,14 +325,14 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   // LU records grouped by cluster size
   auto group = [&](const std::vector<LuArgs>& all, const std::vector<int>& gof, int* first,
                    int* cnt, std::vector<LuArgs>& sorted) {
-    for (int g = 0; g <= 16; ++g) cnt[g] = 0;
+    for (int g = 0; g < kLuGroups; ++g) cnt[g] = 0;
     for (int v : gof) ++cnt[v];
     int acc = 0;
-    for (int g = 0; g <= 16; ++g) {
+    for (int g = 0; g < kLuGroups; ++g) {
       first[g] = acc;
       acc += cnt[g];
     }
-    std::vector<int> fill(first, first + 17);
+    std::vector<int> fill(first, first + kLuGroups);
     sorted.resize(all.size());
     for (size_t i = 0; i < all.size(); ++i) sorted[(size_t)fill[gof[i]]++] = all[i];
   };
@@ -340,13 +366,23 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
     b->u3_stage_bytes = max_stage;
     if (st == RLU_OK) st = up(t.u3y, u3y.data(), c * sizeof(U3Job));
     if (st == RLU_OK) st = up(t.u3c, u3c.data(), c * sizeof(U3Job));
+    // tile lists: the tiles of one problem next to each other
+    std::vector<int2> ty, tc;
+    ty.reserve((size_t)t.n_tiles_y);
+    tc.reserve((size_t)t.n_tiles_c);
+    for (int i = 0; i < count; ++i) {
+      for (int mt = 0; mt < (int)ceil_div(problems[i].m, 128); ++mt) ty.push_back(make_int2(i, mt));
+      for (int mt = 0; mt < (int)ceil_div(problems[i].n, 128); ++mt) tc.push_back(make_int2(i, mt));
+    }
+    if (st == RLU_OK) st = up(t.u3y_tiles, ty.data(), ty.size() * sizeof(int2));
+    if (st == RLU_OK) st = up(t.u3c_tiles, tc.data(), tc.size() * sizeof(int2));
   }
   if (st != RLU_OK) {
     delete b;
     return st;
   }
   int groups = 0;
-  for (int g = 1; g <= 16; ++g) groups += (b->count_y[g] > 0) + (b->count_b[g] > 0);
+  for (int g = 1; g < kLuGroups; ++g) groups += (b->count_y[g] > 0) + (b->count_b[g] > 0);
   b->launches = 10 + groups;
   *out = b;
   return RLU_OK;
@@ -364,8 +400,9 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
   RLU_TRY(last_launch_status());
   RLU_TRY(launch_gaussian_batched(reinterpret_cast<const GaussJob*>(ws + t.gauss), c, s));
   if (b->prec == RLU_PREC_MIXED)
-    RLU_TRY(umma3_batched(U3_MODE_Y2, reinterpret_cast<const U3Job*>(ws + t.u3y), c,
-                          (int)b->max_m, b->u3_stages, b->u3_stage_bytes, s));
+    RLU_TRY(umma3_batched(U3_MODE_Y2, reinterpret_cast<const U3Job*>(ws + t.u3y),
+                          reinterpret_cast<const int2*>(ws + t.u3y_tiles), t.n_tiles_y,
+                          b->u3_stages, b->u3_stage_bytes, s));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_y),
                                              c, b->max_m, b->max_l, true, true, false, s,
@@ -375,12 +412,14 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
                                 b->count_y, s));
   RLU_TRY(build_ly_batched(reinterpret_cast<const BuildJob*>(ws + t.build), c, b->max_m,
                            b->max_k, s));
+  // the Gram is k x k with k <= 64: one 64 x 64 tile per problem
   RLU_TRY((gemm_simt_batched<float, double>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_g), c,
-                                            b->max_k, b->max_k, true, true, true, s)));
+                                            b->max_k, b->max_k, true, true, true, s, 1)));
   RLU_TRY(ldl32_batched(reinterpret_cast<const Ldl32Job*>(ws + t.ldl), c, b->max_k, s));
   if (b->prec == RLU_PREC_MIXED)
-    RLU_TRY(umma3_batched(U3_MODE_C3, reinterpret_cast<const U3Job*>(ws + t.u3c), c,
-                          (int)b->max_n, b->u3_stages, b->u3_stage_bytes, s));
+    RLU_TRY(umma3_batched(U3_MODE_C3, reinterpret_cast<const U3Job*>(ws + t.u3c),
+                          reinterpret_cast<const int2*>(ws + t.u3c_tiles), t.n_tiles_c,
+                          b->u3_stages, b->u3_stage_bytes, s));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_c),
                                              c, b->max_k, b->max_n, true, false, true, s,

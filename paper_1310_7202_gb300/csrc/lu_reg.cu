@@ -800,8 +800,8 @@ int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s
 // rows_per_cta is 512 (512-thread CTAs) or 256 (256-thread CTAs, twice as many CTAs per
 // problem).
 template <int NT>
-static int32_t lu_batched_nt(bool crout, const LuArgs* table_dev, const int* first,
-                             const int* count, cudaStream_t s) {
+static int32_t lu_batched_group(bool crout, const LuArgs* table_dev, int first, int count, int g,
+                                cudaStream_t s) {
   using T = float;
   constexpr int NB = 77;
   int dev = 0;
@@ -810,34 +810,39 @@ static int32_t lu_batched_nt(bool crout, const LuArgs* table_dev, const int* fir
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t bytes = lr_smem_bytes<T, NB, NT>(NT, 0);
   if (bytes > (size_t)optin) return RLU_EUNSUPPORTED;
-  for (int g = 1; g <= 16; ++g) {
-    if (count[g] == 0) continue;
-    auto kern = crout ? k_lu_reg_batched<T, true, 1, NB, NT> : k_lu_reg_batched<T, false, 1, NB, NT>;
-    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = g;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)(g * count[g]));
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = bytes;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, table_dev + first[g]));
-    RLU_TRY(last_launch_status());
-  }
-  return RLU_OK;
+  auto kern = crout ? k_lu_reg_batched<T, true, 1, NB, NT> : k_lu_reg_batched<T, false, 1, NB, NT>;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = g;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(g * count));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, table_dev + first));
+  return last_launch_status();
 }
 
 int32_t launch_lu_reg_batched(bool crout, int rows_per_cta, const LuArgs* table_dev,
                               const int* first, const int* count, cudaStream_t s) {
-  if (rows_per_cta == 256) return lu_batched_nt<256>(crout, table_dev, first, count, s);
-  if (rows_per_cta == 512) return lu_batched_nt<512>(crout, table_dev, first, count, s);
-  return RLU_EINVAL;
+  if (rows_per_cta != 512 && rows_per_cta != 256) return RLU_EINVAL;
+  for (int g = 1; g <= 16; ++g) {
+    if (count[g] == 0) continue;
+    if (rows_per_cta == 512)
+      RLU_TRY(lu_batched_group<512>(crout, table_dev, first[g], count[g], g, s));
+    else
+      RLU_TRY(lu_batched_group<256>(crout, table_dev, first[g], count[g], g, s));
+  }
+  // one narrow CTA for small problems, several per SM
+  if (count[17] > 0) RLU_TRY(lu_batched_group<128>(crout, table_dev, first[17], count[17], 1, s));
+  if (count[18] > 0) RLU_TRY(lu_batched_group<256>(crout, table_dev, first[18], count[18], 1, s));
+  return RLU_OK;
 }
 
 }  // namespace rlu

@@ -32,10 +32,12 @@ int32_t launch_cluster_lu(int32_t dtype, bool crout, const LuArgs& a, cudaStream
 int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s, bool* launched);
 
 // Batched FP32 LUs of single-panel problems (C <= 76, R <= 16 x rows_per_cta), one cluster
-// each; the device table is grouped by cluster size g = ceil(R / rows_per_cta) (entries
-// first[g] .. first[g] + count[g] - 1; first and count are host arrays of 17 entries). Each
-// entry carries rpc = rows_per_cta (512 or 256), p0 = 0, pw = C and its own position state
-// (posg, psg).
+// each; the device table is grouped (entries first[g] .. first[g] + count[g] - 1; first and
+// count are host arrays of kLuGroups entries): g = 1..16 is the cluster size ceil(R /
+// rows_per_cta) with rows_per_cta-thread CTAs, g = 17 one 128-thread CTA (R <= 128), g = 18
+// one 256-thread CTA (R <= 256). Each entry carries its rpc (rows per CTA), p0 = 0, pw = C
+// and its own position state (posg, psg).
+static constexpr int kLuGroups = 19;
 int32_t launch_lu_reg_batched(bool crout, int rows_per_cta, const LuArgs* table_dev,
                               const int* first, const int* count, cudaStream_t s);
 

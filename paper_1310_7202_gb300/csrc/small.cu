@@ -1091,25 +1091,29 @@ int32_t info_init(rlu_info* info, cudaStream_t s) {
 }
 
 // ---- batched launchers --------------------------------------------------------------------
+// One CTA per problem: its k columns of L_y / L~ (m rows each) in a loop, so that the grid
+// holds no CTAs for the columns and rows small problems do not have.
 __global__ void k_build_ly_batched(const BuildJob* __restrict__ jobs) {
-  const BuildJob j = jobs[blockIdx.z];
-  const int c = blockIdx.y;
-  if (c >= j.k) return;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < j.m;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = j.perm[p];
-    const float v = (c < p) ? j.Y[(int64_t)c * j.ldy + r] : (c == p ? 1.f : 0.f);
-    j.Lp[(int64_t)c * j.ldl + p] = v;
-    j.Lt[(int64_t)c * j.ldl + r] = v;
-    if (j.Lhi) tf32_split(v, j.Lhi, j.Llo, (int64_t)c * j.ldl + r);
+  const BuildJob& j = jobs[blockIdx.x];
+  const int64_t m = j.m;
+  const int k = j.k;
+  for (int c = 0; c < k; ++c) {
+    for (int64_t p = threadIdx.x; p < m; p += blockDim.x) {
+      const int64_t r = j.perm[p];
+      const float v = (c < p) ? j.Y[(int64_t)c * j.ldy + r] : (c == p ? 1.f : 0.f);
+      j.Lp[(int64_t)c * j.ldl + p] = v;
+      j.Lt[(int64_t)c * j.ldl + r] = v;
+      if (j.Lhi) tf32_split(v, j.Lhi, j.Llo, (int64_t)c * j.ldl + r);
+    }
   }
 }
 
 int32_t build_ly_batched(const BuildJob* jobs_dev, int count, int64_t max_m, int max_k,
                          cudaStream_t s) {
   if (count <= 0) return RLU_OK;
-  const unsigned bx = (unsigned)std::min<int64_t>(ceil_div(max_m, 256), 8);
-  k_build_ly_batched<<<dim3(bx, (unsigned)max_k, (unsigned)count), 256, 0, s>>>(jobs_dev);
+  (void)max_m;
+  (void)max_k;
+  k_build_ly_batched<<<(unsigned)count, 256, 0, s>>>(jobs_dev);
   return last_launch_status();
 }
 
@@ -1139,23 +1143,26 @@ int32_t trsm_batched(const TrsmJob* jobs_dev, int count, int max_kp, int64_t max
   return last_launch_status();
 }
 
+// One CTA per problem: U (k rows of n) and L_b (k x k) in loops.
 __global__ void k_gather_batched(const GatherJob* __restrict__ jobs) {
-  const GatherJob j = jobs[blockIdx.z];
-  const int i = blockIdx.y;  // row of U / column of L_b
-  if (i >= j.k) return;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < j.n;
-       c += (int64_t)gridDim.x * blockDim.x)
-    j.U[(int64_t)i * j.ldu + c] = c >= i ? j.B[(int64_t)i * j.ldb + j.Q[c]] : 0.f;
-  // L_b column i: rows r > i from B's row r at the pivot column Q[i]
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < j.k; r += gridDim.x * blockDim.x)
-    j.Lb[(int64_t)i * j.k + r] = r > i ? j.B[(int64_t)r * j.ldb + j.Q[i]] : (r == i ? 1.f : 0.f);
+  const GatherJob& j = jobs[blockIdx.x];
+  const int k = j.k;
+  const int64_t n = j.n;
+  for (int i = 0; i < k; ++i) {
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x)
+      j.U[(int64_t)i * j.ldu + c] = c >= i ? j.B[(int64_t)i * j.ldb + j.Q[c]] : 0.f;
+    // L_b column i: rows r > i from B's row r at the pivot column Q[i]
+    for (int r = threadIdx.x; r < k; r += blockDim.x)
+      j.Lb[(int64_t)i * k + r] = r > i ? j.B[(int64_t)r * j.ldb + j.Q[i]] : (r == i ? 1.f : 0.f);
+  }
 }
 
 int32_t gather_batched(const GatherJob* jobs_dev, int count, int max_k, int64_t max_n,
                        cudaStream_t s) {
   if (count <= 0) return RLU_OK;
-  const unsigned bx = (unsigned)std::min<int64_t>(ceil_div(max_n, 256), 8);
-  k_gather_batched<<<dim3(bx, (unsigned)max_k, (unsigned)count), 256, 0, s>>>(jobs_dev);
+  (void)max_k;
+  (void)max_n;
+  k_gather_batched<<<(unsigned)count, 256, 0, s>>>(jobs_dev);
   return last_launch_status();
 }
 

@@ -54,9 +54,10 @@ struct U3Job {
 int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes);
 // Ring slots that fit for the largest slot size; writes every record's stages field.
 int32_t umma3_stages_for(int stage_bytes);
-// One launch for count records: grid (ceil(max_m / 128), count).
-int32_t umma3_batched(int mode, const U3Job* jobs_dev, int count, int max_m, int stages,
-                      int max_stage_bytes, cudaStream_t s);
+// One launch over a tile list (device, ntiles entries of (record, 128-row tile)): one CTA
+// per tile that exists, so small problems add no idle CTAs.
+int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, int ntiles,
+                      int stages, int max_stage_bytes, cudaStream_t s);
 
 // BF16 products (see umma_bf16.cu), same output conventions as Umma3Op.
 // Y : A (M x K row-major BF16, lda), B0 = G^T (N x K row-major BF16, ldb), one product.

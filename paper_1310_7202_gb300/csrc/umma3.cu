@@ -334,10 +334,11 @@ k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtenso
 // Batched form: problem blockIdx.y (one N tile, no split), 128-row tile blockIdx.x; CTAs past
 // the problem's rows return before any allocation.
 template <int MODE>
-__global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_batched(const U3Job* __restrict__ jobs) {
-  const U3Job& j = jobs[blockIdx.y];
-  if ((int)blockIdx.x * U3_BM >= j.a.M) return;
-  umma3_tile<MODE>(j.map[0], j.map[1], j.map[2], j.map[3], j.a, blockIdx.x, 0, 0);
+__global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_batched(const U3Job* __restrict__ jobs,
+                                                                 const int2* __restrict__ tiles) {
+  const int2 t = tiles[blockIdx.x];  // (problem, 128-row tile): only tiles that exist
+  const U3Job& j = jobs[t.x];
+  umma3_tile<MODE>(j.map[0], j.map[1], j.map[2], j.map[3], j.a, t.y, 0, 0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -493,20 +494,20 @@ int32_t umma3_stages_for(int stage_bytes) {
   return stages > U3_MAXST ? U3_MAXST : stages;
 }
 
-int32_t umma3_batched(int mode, const U3Job* jobs_dev, int count, int max_m, int stages,
-                      int max_stage_bytes, cudaStream_t s) {
-  if (count <= 0) return RLU_OK;
-  if (count > 65535 || stages < 2) return RLU_EINVAL;
+int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, int ntiles,
+                      int stages, int max_stage_bytes, cudaStream_t s) {
+  if (ntiles <= 0) return RLU_OK;
+  if (stages < 2) return RLU_EINVAL;
   const size_t smem = 2048 + (size_t)stages * max_stage_bytes;
-  const dim3 grid((unsigned)ceil_div(max_m, U3_BM), (unsigned)count);
+  const dim3 grid((unsigned)ntiles);
   if (mode == U3_MODE_Y2) {
     RLU_CUDA_TRY(cudaFuncSetAttribute(k_umma3_batched<U3_MODE_Y2>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_umma3_batched<U3_MODE_Y2><<<grid, U3_THREADS, smem, s>>>(jobs_dev);
+    k_umma3_batched<U3_MODE_Y2><<<grid, U3_THREADS, smem, s>>>(jobs_dev, tiles_dev);
   } else if (mode == U3_MODE_C3) {
     RLU_CUDA_TRY(cudaFuncSetAttribute(k_umma3_batched<U3_MODE_C3>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_umma3_batched<U3_MODE_C3><<<grid, U3_THREADS, smem, s>>>(jobs_dev);
+    k_umma3_batched<U3_MODE_C3><<<grid, U3_THREADS, smem, s>>>(jobs_dev, tiles_dev);
   } else {
     return RLU_EINVAL;
   }
