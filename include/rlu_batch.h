@@ -48,12 +48,18 @@ typedef struct {
  *     C = L~^T A and L = L_y L_b: 0 = 128 x 128, 1 = 64 x 64 (Y and C use the tensor cores
  *     under RLU_PREC_MIXED; their knobs are then ignored).
  *   lu_rows_per_cta: rows of an LU held by one CTA of a problem's cluster: 0 or 512 (512
- *     threads), 256 (256 threads, twice the CTAs per problem; m and n <= 4096). */
+ *     threads), 256 (256 threads, twice the CTAs per problem; m and n <= 4096).
+ *   umma_ctas_y, umma_ctas_c: under RLU_PREC_MIXED, CTAs of the tensor-core product Y = A G
+ *     (resp. C = L~^T A) meant to share an SM: 0 or 1 (the deepest staging ring one CTA can
+ *     hold), 2 (a shallower ring, so that two CTAs share the SM; a product whose two-slot
+ *     ring does not fit that way keeps one CTA per SM). Ignored under RLU_PREC_F32. */
 typedef struct {
   int32_t gemm_tile_y;
   int32_t gemm_tile_c;
   int32_t gemm_tile_l;
   int32_t lu_rows_per_cta;
+  int32_t umma_ctas_y;
+  int32_t umma_ctas_c;
 } rlu_batch_options;
 
 /* Workspace bytes for the batch (0 if a problem is invalid for the batched form). */

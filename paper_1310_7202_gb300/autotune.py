@@ -3,7 +3,9 @@
 It times the kernel choices of a batch on the batch itself and keeps the fastest:
 - the SIMT output tile of the three batched products (128 x 128 or 64 x 64);
 - the rows each CTA of a problem's LU cluster holds (512 or 256, which sets the cluster
-  sizes).
+  sizes);
+- under mixed precision, one or two CTAs per SM for each tensor-core product (a deep
+  staging ring, or a shallower one shared by two CTAs).
 
 Each trial is a CUDA-graph replay of the whole batch, timed with CUDA events (median of
 several replays after warm-up). The search is one pass of coordinate descent from the
@@ -29,8 +31,11 @@ KNOBS = {
     "gemm_tile_y": (0, 1),
     "gemm_tile_c": (0, 1),
     "gemm_tile_l": (0, 1),
+    "umma_ctas_y": (1, 2),
+    "umma_ctas_c": (1, 2),
 }
-DEFAULTS = {"lu_rows_per_cta": 512, "gemm_tile_y": 0, "gemm_tile_c": 0, "gemm_tile_l": 0}
+DEFAULTS = {"lu_rows_per_cta": 512, "gemm_tile_y": 0, "gemm_tile_c": 0, "gemm_tile_l": 0,
+            "umma_ctas_y": 1, "umma_ctas_c": 1}
 
 
 def _cache_path() -> str:
@@ -74,8 +79,11 @@ def time_config(problems: list[dict], prec, options: dict, reps: int = 5,
 
 
 def _applicable(knob: str, prec, problems: list[dict], value) -> bool:
-    if prec in ("mixed", rlu.RLU_PREC_MIXED) and knob in ("gemm_tile_y", "gemm_tile_c"):
+    mixed = prec in ("mixed", rlu.RLU_PREC_MIXED)
+    if mixed and knob in ("gemm_tile_y", "gemm_tile_c"):
         return value == DEFAULTS[knob]  # tensor-core products: the SIMT tile is unused
+    if not mixed and knob in ("umma_ctas_y", "umma_ctas_c"):
+        return value == DEFAULTS[knob]  # SIMT products: no tensor-core ring
     if knob == "lu_rows_per_cta":
         tallest = max(max(p["A"].shape) for p in problems)
         return tallest <= 16 * value

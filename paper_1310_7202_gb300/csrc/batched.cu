@@ -42,8 +42,9 @@ struct ProblemLayout {
 
 struct Tables {
   size_t info, gauss, gemm_y, lu_y, build, gemm_g, ldl, gemm_c, trsm, lu_b, gather, gemm_l,
-      u3y, u3c, u3y_tiles, u3c_tiles;
+      u3y, u3c, u3y_tiles, u3c_tiles, trsm_tiles;
   int n_tiles_y, n_tiles_c;  // 128-row tiles of the two tensor-core products
+  int n_tiles_t;             // 64-column blocks of the substitution B = M^{-1} C
 };
 
 // LU group of a problem with R rows (see rlu_batch) and its rows per CTA: small problems
@@ -85,6 +86,9 @@ size_t plan_layout(const rlu_problem* probs, int count, int32_t prec, Tables& t,
   t.ldl = carve(cur, c * sizeof(Ldl32Job));
   t.gemm_c = carve(cur, c * sizeof(GemmArgs));
   t.trsm = carve(cur, c * sizeof(TrsmJob));
+  t.n_tiles_t = 0;
+  for (int i = 0; i < count; ++i) t.n_tiles_t += (int)ceil_div(probs[i].n, 64);
+  t.trsm_tiles = carve(cur, (size_t)t.n_tiles_t * sizeof(int2));
   t.lu_b = carve(cur, c * sizeof(LuArgs));
   t.gather = carve(cur, c * sizeof(GatherJob));
   t.gemm_l = carve(cur, c * sizeof(GemmArgs));
@@ -161,7 +165,8 @@ struct rlu_batch {
   int first_y[rlu::kLuGroups] = {}, count_y[rlu::kLuGroups] = {}, first_b[rlu::kLuGroups] = {},
       count_b[rlu::kLuGroups] = {};
   int launches = 0;
-  int u3_stages = 0, u3_stage_bytes = 0;  // tensor-core ring of the mixed precision
+  // tensor-core rings of the mixed precision (Y = A G, C = L~^T A)
+  int u3y_stages = 0, u3y_stage_bytes = 0, u3c_stages = 0, u3c_stage_bytes = 0;
   rlu_batch_options opt{};
 };
 
@@ -188,6 +193,8 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   if (opt.lu_rows_per_cta != 512 && opt.lu_rows_per_cta != 256) return RLU_EINVAL;
   for (int t : {opt.gemm_tile_y, opt.gemm_tile_c, opt.gemm_tile_l})
     if (t != 0 && t != 1) return RLU_EINVAL;
+  for (int u : {opt.umma_ctas_y, opt.umma_ctas_c})
+    if (u < 0 || u > 2) return RLU_EINVAL;
   for (int i = 0; i < count; ++i)
     if (std::max(problems[i].m, problems[i].n) > 16 * (int64_t)opt.lu_rows_per_cta)
       return RLU_EINVAL;
@@ -219,7 +226,7 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   std::vector<int> gy_of(c), gb_of(c);
   const bool mixed = prec == RLU_PREC_MIXED;
   std::vector<U3Job> u3y(mixed ? c : 0), u3c(mixed ? c : 0);
-  int max_stage = 0;
+  int max_stage_y = 0, max_stage_c = 0;
   for (int i = 0; i < count; ++i) {
     const rlu_problem& p = problems[i];
     const ProblemLayout& L = lay[(size_t)i];
@@ -292,7 +299,7 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
       op.status = p.info ? &p.info->status : nullptr;
       int sb = 0;
       int32_t st = umma3_make_job(U3_MODE_Y2, op, &u3y[(size_t)i], &sb);
-      max_stage = std::max(max_stage, sb);
+      max_stage_y = std::max(max_stage_y, sb);
       op = Umma3Op{};
       op.A0 = static_cast<const float*>(p.A);
       op.lda = p.lda;
@@ -307,7 +314,7 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
       op.out_colmajor = true;
       op.status = p.info ? &p.info->status : nullptr;
       if (st == RLU_OK) st = umma3_make_job(U3_MODE_C3, op, &u3c[(size_t)i], &sb);
-      max_stage = std::max(max_stage, sb);
+      max_stage_c = std::max(max_stage_c, sb);
       if (st != RLU_OK) {
         delete b;
         return st;
@@ -357,13 +364,29 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   if (st == RLU_OK) st = up(t.lu_b, lub.data(), c * sizeof(LuArgs));
   if (st == RLU_OK) st = up(t.gather, gather.data(), c * sizeof(GatherJob));
   if (st == RLU_OK) st = up(t.gemm_l, gl.data(), c * sizeof(GemmArgs));
+  {  // substitution tile list: (problem, 64-column block), the blocks of a problem together
+    std::vector<int2> tt;
+    tt.reserve((size_t)t.n_tiles_t);
+    for (int i = 0; i < count; ++i)
+      for (int cb = 0; cb < (int)ceil_div(problems[i].n, 64); ++cb) tt.push_back(make_int2(i, cb));
+    if (st == RLU_OK) st = up(t.trsm_tiles, tt.data(), tt.size() * sizeof(int2));
+  }
   if (mixed && st == RLU_OK) {
-    const int stages = umma3_stages_for(max_stage);
-    if (stages < 2) st = RLU_EUNSUPPORTED;
-    for (auto& j : u3y) j.a.stages = stages;
-    for (auto& j : u3c) j.a.stages = stages;
-    b->u3_stages = stages;
-    b->u3_stage_bytes = max_stage;
+    // ring depth: the deepest for one CTA per SM, else a ring that lets two CTAs share an
+    // SM when two slots still fit that way
+    auto ring = [&](int stage_bytes, int ctas) {
+      int d = ctas == 2 ? umma3_stages_for(stage_bytes, 2) : 0;
+      if (d < 2) d = umma3_stages_for(stage_bytes, 1);
+      return d;
+    };
+    const int sy = ring(max_stage_y, opt.umma_ctas_y), sc = ring(max_stage_c, opt.umma_ctas_c);
+    if (sy < 2 || sc < 2) st = RLU_EUNSUPPORTED;
+    for (auto& j : u3y) j.a.stages = sy;
+    for (auto& j : u3c) j.a.stages = sc;
+    b->u3y_stages = sy;
+    b->u3y_stage_bytes = max_stage_y;
+    b->u3c_stages = sc;
+    b->u3c_stage_bytes = max_stage_c;
     if (st == RLU_OK) st = up(t.u3y, u3y.data(), c * sizeof(U3Job));
     if (st == RLU_OK) st = up(t.u3c, u3c.data(), c * sizeof(U3Job));
     // tile lists: the tiles of one problem next to each other
@@ -402,7 +425,7 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
   if (b->prec == RLU_PREC_MIXED)
     RLU_TRY(umma3_batched(U3_MODE_Y2, reinterpret_cast<const U3Job*>(ws + t.u3y),
                           reinterpret_cast<const int2*>(ws + t.u3y_tiles), t.n_tiles_y,
-                          b->u3_stages, b->u3_stage_bytes, s));
+                          b->u3y_stages, b->u3y_stage_bytes, s));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_y),
                                              c, b->max_m, b->max_l, true, true, false, s,
@@ -419,12 +442,14 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
   if (b->prec == RLU_PREC_MIXED)
     RLU_TRY(umma3_batched(U3_MODE_C3, reinterpret_cast<const U3Job*>(ws + t.u3c),
                           reinterpret_cast<const int2*>(ws + t.u3c_tiles), t.n_tiles_c,
-                          b->u3_stages, b->u3_stage_bytes, s));
+                          b->u3c_stages, b->u3c_stage_bytes, s));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_c),
                                              c, b->max_k, b->max_n, true, false, true, s,
                                              b->opt.gemm_tile_c)));
-  RLU_TRY(trsm_batched(reinterpret_cast<const TrsmJob*>(ws + t.trsm), c, b->max_kp, b->max_n, s));
+  RLU_TRY(trsm_batched(reinterpret_cast<const TrsmJob*>(ws + t.trsm),
+                       reinterpret_cast<const int2*>(ws + t.trsm_tiles), t.n_tiles_t, b->max_kp,
+                       s));
   RLU_TRY(launch_lu_reg_batched(true, b->opt.lu_rows_per_cta,
                                 reinterpret_cast<const LuArgs*>(ws + t.lu_b), b->first_b,
                                 b->count_b, s));

@@ -57,7 +57,8 @@ int32_t launch_gaussian_batched(const GaussJob* jobs_dev, int count, cudaStream_
 int32_t build_ly_batched(const BuildJob* jobs_dev, int count, int64_t max_m, int max_k,
                          cudaStream_t s);
 int32_t ldl32_batched(const Ldl32Job* jobs_dev, int count, int max_k, cudaStream_t s);
-int32_t trsm_batched(const TrsmJob* jobs_dev, int count, int max_kp, int64_t max_n,
+// over a tile list of (problem, 64-column block) pairs
+int32_t trsm_batched(const TrsmJob* jobs_dev, const int2* tiles_dev, int ntiles, int max_kp,
                      cudaStream_t s);
 int32_t gather_batched(const GatherJob* jobs_dev, int count, int max_k, int64_t max_n,
                        cudaStream_t s);

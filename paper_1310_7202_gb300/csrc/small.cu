@@ -381,6 +381,7 @@ __device__ __forceinline__ void gemm_nt_tile(float* C, const float* A, const flo
     for (int y = 0; y < 4; ++y) C[(r0 + x) * LBP + c0 + y] -= acc[x][y];
 }
 
+template <int NT>
 __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
                                            const LdlOut<float>& o, int32_t* __restrict__ status) {
   extern __shared__ __align__(16) float l32_smem[];
@@ -394,11 +395,11 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_bad = 0;
   // batches of 8 independent loads per thread, so that their latencies overlap
-  for (int e0 = tid; e0 < nblk * LB * LB; e0 += L32_NT * 8) {
+  for (int e0 = tid; e0 < nblk * LB * LB; e0 += NT * 8) {
     float v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * L32_NT;
+      const int e = e0 + u * NT;
       const int b = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
       int I = 0;
       while (tri_blk(I + 1, 0) <= b) ++I;
@@ -409,7 +410,7 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * L32_NT;
+      const int e = e0 + u * NT;
       const int b = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
       if (e < nblk * LB * LB) Bk[(size_t)b * LB * LBP + r * LBP + c] = v[u];
     }
@@ -448,7 +449,7 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
     // U_IJ = M_IJ W_J^T, then L_IJ = U_IJ D_J^{-1} in place
     const int rest = nb - 1 - J;
     const float* W = Wb + (size_t)J * LB * LBP;
-    for (int e = tid; e < rest * LB * LB; e += L32_NT) {
+    for (int e = tid; e < rest * LB * LB; e += NT) {
       const int I = J + 1 + e / (LB * LB), r = (e / LB) % LB, c = e % LB;
       const float* Mr = Bk + (size_t)tri_blk(I, J) * LB * LBP + r * LBP;
       float acc = 0.f;
@@ -457,7 +458,7 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
       Ub[(size_t)(I - J - 1) * LB * LBP + r * LBP + c] = acc;
     }
     __syncthreads();
-    for (int e = tid; e < rest * LB * LB; e += L32_NT) {
+    for (int e = tid; e < rest * LB * LB; e += NT) {
       const int I = J + 1 + e / (LB * LB), r = (e / LB) % LB, c = e % LB;
       Bk[(size_t)tri_blk(I, J) * LB * LBP + r * LBP + c] =
           Ub[(size_t)(I - J - 1) * LB * LBP + r * LBP + c] / dd[J * LB + c];
@@ -465,7 +466,7 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
     __syncthreads();
     // trailing update of the lower-triangle blocks I >= K > J; 64 4x4 tiles per block
     const int ntask = rest * (rest + 1) / 2 * 64;
-    for (int q = tid; q < ntask; q += L32_NT) {
+    for (int q = tid; q < ntask; q += NT) {
       const int pb = q / 64, tile = q % 64;
       int ii = 0;
       while ((ii + 1) * (ii + 2) / 2 <= pb) ++ii;
@@ -499,38 +500,40 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
   // L (unit lower, zero above, identity past k) in both layouts, the diagonal-block
   // inverses and their transposes, 1/D
   const int kp = o.kp;
-  for (int e = tid; e < kp * kp; e += L32_NT) {
+  for (int e = tid; e < kp * kp; e += NT) {
     const int c = e / kp, i = e % kp;
     float v = 0.f;
     if (i > c) v = Bk[(size_t)tri_blk(i / LB, c / LB) * LB * LBP + (i % LB) * LBP + c % LB];
     else if (i == c) v = 1.f;
     o.LT[e] = v;
   }
-  for (int e = tid; e < kp * kp; e += L32_NT) {
+  for (int e = tid; e < kp * kp; e += NT) {
     const int i = e / kp, c = e % kp;
     float v = 0.f;
     if (i > c) v = Bk[(size_t)tri_blk(i / LB, c / LB) * LB * LBP + (i % LB) * LBP + c % LB];
     else if (i == c) v = 1.f;
     o.LR[e] = v;
   }
-  for (int e = tid; e < nb * LB * LB; e += L32_NT) {
+  for (int e = tid; e < nb * LB * LB; e += NT) {
     const int b = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
     o.W[e] = Wb[(size_t)b * LB * LBP + r * LBP + c];
     o.WT[e] = Wb[(size_t)b * LB * LBP + c * LBP + r];
   }
-  for (int i = tid; i < k; i += L32_NT) o.dinv[i] = 1.0 / (double)dd[i];
+  for (int i = tid; i < k; i += NT) o.dinv[i] = 1.0 / (double)dd[i];
   if (tid == 0 && s_bad && status) *status = RLU_EINVAL;
 }
 
 __global__ void __launch_bounds__(L32_NT, 1) k_ldl32(const double* __restrict__ M, int k,
                                                     LdlOut<float> o, int32_t* __restrict__ status) {
-  ldl32_body(M, k, o, status);
+  ldl32_body<L32_NT>(M, k, o, status);
 }
 
-// Batched form: problem blockIdx.x of the table.
-__global__ void __launch_bounds__(L32_NT, 1) k_ldl32_batched(const Ldl32Job* __restrict__ jobs) {
+// Batched form: problem blockIdx.x of the table. Batches whose k stay within 128 (at most
+// four 32 x 32 block columns) take 128 threads, so that several problems share an SM.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ldl32_batched(const Ldl32Job* __restrict__ jobs) {
   const Ldl32Job& j = jobs[blockIdx.x];
-  ldl32_body(j.M, j.k, j.o, j.status);
+  ldl32_body<NT>(j.M, j.k, j.o, j.status);
 }
 
 static size_t ldl32_smem_bytes(int k) {
@@ -969,11 +972,12 @@ __global__ void __launch_bounds__(TB / 2 * TC / 4) k_trsm_ldl(LdlOut<T> o, const
   trsm_body<T, TC>(o, C, ldc, n, B, ldb, blockIdx.x);
 }
 
-// Batched form: problem blockIdx.y, column block blockIdx.x (CTAs past its n return).
-__global__ void __launch_bounds__(TB / 2 * 64 / 4) k_trsm_batched(const TrsmJob* __restrict__ jobs) {
-  const TrsmJob& j = jobs[blockIdx.y];
-  if ((int64_t)blockIdx.x * 64 >= j.n) return;
-  trsm_body<float, 64>(j.o, j.C, j.ldc, j.n, j.B, j.ldb, blockIdx.x);
+// Batched form over a tile list: entry blockIdx.x = (problem, 64-column block).
+__global__ void __launch_bounds__(TB / 2 * 64 / 4) k_trsm_batched(const TrsmJob* __restrict__ jobs,
+                                                                 const int2* __restrict__ tiles) {
+  const int2 t = tiles[blockIdx.x];
+  const TrsmJob& j = jobs[t.x];
+  trsm_body<float, 64>(j.o, j.C, j.ldc, j.n, j.B, j.ldb, t.y);
 }
 
 template <typename T>
@@ -1091,13 +1095,14 @@ int32_t info_init(rlu_info* info, cudaStream_t s) {
 }
 
 // ---- batched launchers --------------------------------------------------------------------
-// One CTA per problem: its k columns of L_y / L~ (m rows each) in a loop, so that the grid
-// holds no CTAs for the columns and rows small problems do not have.
+// CTA (problem blockIdx.x, column group blockIdx.y): columns c = y, y + gridDim.y, ... of
+// L_y / L~ (m rows each) in a loop, so that the grid holds no CTAs for the rows small
+// problems do not have.
 __global__ void k_build_ly_batched(const BuildJob* __restrict__ jobs) {
   const BuildJob& j = jobs[blockIdx.x];
   const int64_t m = j.m;
   const int k = j.k;
-  for (int c = 0; c < k; ++c) {
+  for (int c = blockIdx.y; c < k; c += gridDim.y) {
     for (int64_t p = threadIdx.x; p < m; p += blockDim.x) {
       const int64_t r = j.perm[p];
       const float v = (c < p) ? j.Y[(int64_t)c * j.ldy + r] : (c == p ? 1.f : 0.f);
@@ -1113,7 +1118,7 @@ int32_t build_ly_batched(const BuildJob* jobs_dev, int count, int64_t max_m, int
   if (count <= 0) return RLU_OK;
   (void)max_m;
   (void)max_k;
-  k_build_ly_batched<<<(unsigned)count, 256, 0, s>>>(jobs_dev);
+  k_build_ly_batched<<<dim3((unsigned)count, 8), 256, 0, s>>>(jobs_dev);
   return last_launch_status();
 }
 
@@ -1121,15 +1126,21 @@ int32_t ldl32_batched(const Ldl32Job* jobs_dev, int count, int max_k, cudaStream
   if (count <= 0) return RLU_OK;
   if (max_k > L32_MAXB * LB) return RLU_EUNSUPPORTED;
   const size_t bytes = ldl32_smem_bytes(max_k);
-  RLU_CUDA_TRY(cudaFuncSetAttribute(k_ldl32_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)bytes));
-  k_ldl32_batched<<<(unsigned)count, L32_NT, bytes, s>>>(jobs_dev);
+  if (max_k <= 4 * LB) {
+    RLU_CUDA_TRY(cudaFuncSetAttribute(k_ldl32_batched<128>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    k_ldl32_batched<128><<<(unsigned)count, 128, bytes, s>>>(jobs_dev);
+  } else {
+    RLU_CUDA_TRY(cudaFuncSetAttribute(k_ldl32_batched<L32_NT>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    k_ldl32_batched<L32_NT><<<(unsigned)count, L32_NT, bytes, s>>>(jobs_dev);
+  }
   return last_launch_status();
 }
 
-int32_t trsm_batched(const TrsmJob* jobs_dev, int count, int max_kp, int64_t max_n,
+int32_t trsm_batched(const TrsmJob* jobs_dev, const int2* tiles_dev, int ntiles, int max_kp,
                      cudaStream_t s) {
-  if (count <= 0) return RLU_OK;
+  if (ntiles <= 0) return RLU_OK;
   const size_t bytes = trsm_smem_bytes<float>(max_kp, 64);
   int dev = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
@@ -1138,8 +1149,7 @@ int32_t trsm_batched(const TrsmJob* jobs_dev, int count, int max_kp, int64_t max
   if (bytes > (size_t)optin) return RLU_EUNSUPPORTED;
   RLU_CUDA_TRY(cudaFuncSetAttribute(k_trsm_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)bytes));
-  k_trsm_batched<<<dim3((unsigned)ceil_div(max_n, 64), (unsigned)count), TB / 2 * 64 / 4, bytes,
-                   s>>>(jobs_dev);
+  k_trsm_batched<<<(unsigned)ntiles, TB / 2 * 64 / 4, bytes, s>>>(jobs_dev, tiles_dev);
   return last_launch_status();
 }
 

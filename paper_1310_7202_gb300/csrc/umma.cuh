@@ -52,8 +52,9 @@ struct U3Job {
 };
 // Fills job (host memory) for op; *stage_bytes = its shared-memory slot size.
 int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes);
-// Ring slots that fit for the largest slot size; writes every record's stages field.
-int32_t umma3_stages_for(int stage_bytes);
+// Ring slots (at most 4) of this slot size that fit one CTA, or that still let ctas_per_sm
+// CTAs share an SM's shared memory (each CTA holds 256 of an SM's 512 TMEM columns).
+int32_t umma3_stages_for(int stage_bytes, int ctas_per_sm = 1);
 // One launch over a tile list (device, ntiles entries of (record, 128-row tile)): one CTA
 // per tile that exists, so small problems add no idle CTAs.
 int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, int ntiles,

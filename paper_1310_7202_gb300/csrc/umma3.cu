@@ -17,6 +17,8 @@
 // (MODE_Y2 / MODE_C3): one thread per tile row, writes the 128-byte-swizzled K-major hi/lo
 // tiles, fences them to the async proxy and arrives on a per-slot mbarrier. Every wait is
 // bounded (~1 s) and records an error instead of hanging.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -485,12 +487,16 @@ int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes
   return RLU_EINVAL;
 }
 
-int32_t umma3_stages_for(int stage_bytes) {
+int32_t umma3_stages_for(int stage_bytes, int ctas_per_sm) {
   int dev = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
-  int optin = 0;
+  int optin = 0, per_sm = 0, reserved = 0;
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  int stages = (optin - 2048) / stage_bytes;
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  int budget = optin;
+  if (ctas_per_sm > 1) budget = std::min(budget, per_sm / ctas_per_sm - reserved);
+  int stages = (budget - 2048) / stage_bytes;
   return stages > U3_MAXST ? U3_MAXST : stages;
 }
 

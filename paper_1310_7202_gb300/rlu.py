@@ -62,7 +62,8 @@ class _Problem(ctypes.Structure):
 
 class _BatchOptions(ctypes.Structure):
     _fields_ = [("gemm_tile_y", ctypes.c_int32), ("gemm_tile_c", ctypes.c_int32),
-                ("gemm_tile_l", ctypes.c_int32), ("lu_rows_per_cta", ctypes.c_int32)]
+                ("gemm_tile_l", ctypes.c_int32), ("lu_rows_per_cta", ctypes.c_int32),
+                ("umma_ctas_y", ctypes.c_int32), ("umma_ctas_c", ctypes.c_int32)]
 
 
 class _StageOutputs(ctypes.Structure):
@@ -441,7 +442,8 @@ class Batch:
     def __init__(self, problems: list[dict], prec: int | str = RLU_PREC_F32,
                  options: dict | None = None):
         """options: the kernel choices of include/rlu_batch.h (gemm_tile_y, gemm_tile_c,
-        gemm_tile_l, lu_rows_per_cta); missing keys take the defaults."""
+        gemm_tile_l, lu_rows_per_cta, umma_ctas_y, umma_ctas_c); missing keys take the
+        defaults."""
         self.lib = load_library()
         self.prec = PREC_BY_NAME[prec] if isinstance(prec, str) else int(prec)
         self.options = dict(options or {})

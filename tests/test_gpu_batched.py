@@ -93,11 +93,13 @@ def test_batched_rejects_problems_outside_the_form():
                     "seed": 1}], "mixed")
 
 
-@pytest.mark.parametrize("options", [{"lu_rows_per_cta": 256},
-                                     {"gemm_tile_y": 1, "gemm_tile_c": 1, "gemm_tile_l": 1}])
-def test_batched_kernel_choices_keep_results(options):
-    """The autotuner's alternatives (256-row LU CTAs, 64 x 64 SIMT tiles) factor the same
-    problems within the same tolerance."""
+@pytest.mark.parametrize("prec,options", [("f32", {"lu_rows_per_cta": 256}),
+                                          ("f32", {"gemm_tile_y": 1, "gemm_tile_c": 1,
+                                                   "gemm_tile_l": 1}),
+                                          ("mixed", {"umma_ctas_y": 2, "umma_ctas_c": 2})])
+def test_batched_kernel_choices_keep_results(prec, options):
+    """The autotuner's alternatives (256-row LU CTAs, 64 x 64 SIMT tiles, tensor-core
+    products at two CTAs per SM) factor the same problems within the same tolerance."""
     shapes = synth.batch_shapes(12, seed=9, max_m=1100, max_n=600)
     probs, mats = [], []
     for i, (m, n, k, l) in enumerate(shapes):
@@ -105,9 +107,16 @@ def test_batched_kernel_choices_keep_results(options):
         A = synth.prescribed_matrix(m, n, sigma, 300 + i, 400 + i, dtype=np.float32)
         mats.append((A, sigma))
         probs.append({"A": _padded(A), "k": k, "l": l, "seed": 70 + i})
-    b = rlu.Batch(probs, "f32", options)
+    b = rlu.Batch(probs, prec, options)
     b.run()
     torch.cuda.synchronize()
+    if prec == "mixed":  # a shallower ring keeps the order of every accumulation
+        d = rlu.Batch(probs, prec)
+        d.run()
+        torch.cuda.synchronize()
+        for o, od in zip(b.outs, d.outs):
+            for key in ("P", "Q", "L", "U"):
+                assert torch.equal(o[key], od[key]), key
     for (m, n, k, l), (A, sigma), p, o in zip(shapes, mats, probs, b.outs):
         G = O.gaussian_f32(p["seed"], 0, n, l).astype(np.float64)
         orc = O.rlu_factor(A.astype(np.float64), k, l, seed=p["seed"], G=G)
