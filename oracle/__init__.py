@@ -1,5 +1,6 @@
 """FP64 CPU oracle for the randomized LU decomposition (Shabat, Shmueli, Aizenbud,
-Averbuch, "Randomized LU Decomposition", Algorithm 1).
+Averbuch, "Randomized LU Decomposition", Algorithm 1, with power iterations and the
+rank-deficient least squares of Algorithm 3) and its fast variant (Algorithm 4, complex128).
 
 TEST INFRASTRUCTURE ONLY. Nothing in the product path imports this package: only
 ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
@@ -19,4 +20,8 @@ from .rlu_oracle import (  # noqa: F401
     rlu_factor, reconstruct_error, spectral_norm, rdls_apply, rdls_solve,
     theorem1_constant, theorem1_success_probability, theorem1_failure_terms,
     check_dims,
+)
+from .frlu_oracle import (  # noqa: F401
+    cabs1, srft_matrix, srft_apply, clu_partial_pivot, clu_column_pivot, id_from_lu,
+    cpinv_apply, frlu_factor, creconstruct_error,
 )

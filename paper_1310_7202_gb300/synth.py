@@ -113,6 +113,18 @@ WORKLOADS = {
 }
 
 
+def srft_params(n: int, l: int, seed: int):
+    """Random numbers of the SRFT R = D F S of the fast randomized LU: theta (n FP32 values,
+    uniform on [0, 1)) for the diagonal of D, and s (l distinct int32 indices in [0, n), a
+    uniformly random ordered selection without replacement) for the columns of S."""
+    if not 1 <= l <= n:
+        raise ValueError("need 1 <= l <= n")
+    rng = np.random.default_rng(seed)
+    theta = rng.random(n, dtype=np.float32)
+    s = rng.permutation(n)[:l].astype(np.int32)
+    return theta, s
+
+
 def batch_shapes(count: int, seed: int, max_m: int = 2048, max_n: int = 1024):
     """Problem sizes of the batched workload: m log-uniform in [64, max_m], n log-uniform in
     [64, max_n] and at most m, k uniform in {8..64}, l = k + 10; k is drawn again while
