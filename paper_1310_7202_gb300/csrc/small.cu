@@ -781,6 +781,19 @@ int32_t ldl_factor(double* M, int k, const LdlOut<T>& o, int32_t* status, cudaSt
   k_diag_inv<T><<<(unsigned)ceil_div(k, TB), 32, 0, s>>>(M, k, o);
   return last_launch_status();
 }
+bool ldl_factor_supported(int k, bool f32) {
+  if (k < 1) return false;
+  if (f32 && k <= LC_MAXB * LB) return true;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  const int nblk = (k + CH_CB - 1) / CH_CB;
+  const int mine = (nblk + 15) / 16;
+  return (size_t)(mine + 2) * k * CH_CB * sizeof(double) + 2 * (size_t)k * sizeof(double) + 1024 <=
+         (size_t)optin;
+}
+
 template int32_t ldl_factor<float>(double*, int, const LdlOut<float>&, int32_t*, cudaStream_t);
 template int32_t ldl_factor<double>(double*, int, const LdlOut<double>&, int32_t*, cudaStream_t);
 

@@ -42,6 +42,9 @@ struct LdlOut {
 template <typename T>
 int32_t ldl_factor(double* M, int k, const LdlOut<T>& o, int32_t* status, cudaStream_t s);
 
+// Whether ldl_factor handles a k x k Gram (FP32 outputs: f32).
+bool ldl_factor_supported(int k, bool f32);
+
 // B (k x n, row-major) = L^{-T} D^{-1} L^{-1} C (C k x n row-major).
 template <typename T>
 int32_t trsm_ldl(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t n, T* B, int64_t ldb,

@@ -34,7 +34,9 @@ EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian"
             "rlu_server_poll", "rlu_server_wait_all", "rlu_server_stats", "rlu_server_destroy",
             "rlu_batch_workspace_size", "rlu_batch_create", "rlu_factor_batched",
             "rlu_batch_launches", "rlu_batch_destroy", "rlu_workspace_size_power",
-            "rlu_factor_power", "rlu_lstsq_workspace_size", "rlu_lstsq")
+            "rlu_factor_power", "rlu_lstsq_workspace_size", "rlu_lstsq",
+            "rlu_fast_workspace_size", "rlu_fast_factor", "rlu_srft_workspace_size",
+            "rlu_srft_apply")
 
 RLU_REQ_QUEUED, RLU_REQ_RUNNING, RLU_REQ_DONE, RLU_REQ_FAILED = 0, 1, 2, 3
 
@@ -151,6 +153,15 @@ def load_library(require_cuda: bool = True) -> ctypes.CDLL:
     lib.rlu_batch_launches.argtypes = [vp]
     lib.rlu_batch_destroy.restype = i32
     lib.rlu_batch_destroy.argtypes = [vp]
+    lib.rlu_fast_workspace_size.restype = sz
+    lib.rlu_fast_workspace_size.argtypes = [i64, i64, i32, i32]
+    lib.rlu_srft_workspace_size.restype = sz
+    lib.rlu_srft_workspace_size.argtypes = [i64]
+    lib.rlu_srft_apply.restype = i32
+    lib.rlu_srft_apply.argtypes = [vp, i64, i64, i64, vp, vp, i32, vp, i64, vp, vp, sz, vp]
+    lib.rlu_fast_factor.restype = i32
+    lib.rlu_fast_factor.argtypes = [vp, i64, i64, i64, i32, i32, vp, vp, vp, vp, vp, i64, vp,
+                                    i64, vp, vp, sz, vp]
     _lib = lib
     return lib
 
@@ -302,6 +313,69 @@ def lstsq(P: torch.Tensor, Q: torch.Tensor, L: torch.Tensor, U: torch.Tensor,
                          _dev_ptr(ws), ws_n, _stream_ptr(stream)),
            "rlu_lstsq")
     return X[:, 0] if vec else X
+
+
+class FastFactorizer:
+    """Algorithm 4 (include/rlu_fast.h) for one problem size, with its workspace allocated
+    once: run(A, theta, s) factors a row-major FP32 CUDA matrix with the SRFT random numbers
+    theta (n FP32 in [0, 1)) and s (l distinct int32 indices) and returns P, Q, L (m x k
+    complex64, column-major), U (k x n complex64, row-major) and info."""
+
+    def __init__(self, m: int, n: int, k: int, l: int):
+        self.lib = load_library()
+        self.m, self.n, self.k, self.l = m, n, k, l
+        ws = self.lib.rlu_fast_workspace_size(m, n, k, l)
+        if ws == 0:
+            raise RluError(f"sizes outside the fast randomized LU: m={m} n={n} k={k} l={l}")
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device="cuda")
+
+    def run(self, A: torch.Tensor, theta: torch.Tensor, s: torch.Tensor, out: dict | None = None,
+            stream=None) -> dict:
+        m, n, k, l = self.m, self.n, self.k, self.l
+        if A.shape != (m, n) or A.dtype != torch.float32 or A.stride(1) != 1:
+            raise RluError("A must be a row-major FP32 CUDA matrix of the planned size")
+        if theta.dtype != torch.float32 or theta.numel() != n or s.dtype != torch.int32 or s.numel() != l:
+            raise RluError("theta must hold n FP32 values and s l int32 indices")
+        o = out if out is not None else {
+            "P": torch.empty(m, dtype=torch.int32, device="cuda"),
+            "Q": torch.empty(n, dtype=torch.int32, device="cuda"),
+            "L": torch.empty((k, m), dtype=torch.complex64, device="cuda").t(),
+            "U": torch.empty((k, n), dtype=torch.complex64, device="cuda"),
+            "info": torch.empty(4, dtype=torch.int32, device="cuda")}
+        _check(self.lib.rlu_fast_factor(
+            _dev_ptr(A), m, n, A.stride(0), k, l, _dev_ptr(theta.contiguous()),
+            _dev_ptr(s.contiguous()), _dev_ptr(o["P"]), _dev_ptr(o["Q"]), _dev_ptr(o["L"]),
+            o["L"].stride(1), _dev_ptr(o["U"]), o["U"].stride(0), _dev_ptr(o["info"]),
+            _dev_ptr(self.workspace), self.workspace.numel(), _stream_ptr(stream)),
+            "rlu_fast_factor")
+        return o
+
+
+def srft_apply(A: torch.Tensor, theta: torch.Tensor, s: torch.Tensor,
+               info: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Steps 1-2 of Algorithm 4: Y = A D F S (m x l complex64, row-major)."""
+    lib = load_library()
+    m, n = A.shape
+    l = s.numel()
+    if A.dtype != torch.float32 or A.stride(1) != 1:
+        raise RluError("A must be a row-major FP32 CUDA matrix")
+    ws_n = lib.rlu_srft_workspace_size(n)
+    if ws_n == 0:
+        raise RluError(f"n={n} is outside the row transform's sizes")
+    ws = torch.empty(ws_n, dtype=torch.uint8, device="cuda")
+    Y = torch.empty((m, l), dtype=torch.complex64, device="cuda")
+    _check(lib.rlu_srft_apply(_dev_ptr(A), m, n, A.stride(0), _dev_ptr(theta.contiguous()),
+                              _dev_ptr(s.contiguous()), l, _dev_ptr(Y), l, _dev_ptr(info),
+                              _dev_ptr(ws), ws_n, _stream_ptr(stream)), "rlu_srft_apply")
+    return Y
+
+
+def fast_factor(A: torch.Tensor, k: int, l: int, theta, s, stream=None) -> dict:
+    """One call of Algorithm 4 (allocates its workspace); theta and s may be numpy arrays."""
+    m, n = A.shape
+    th = torch.as_tensor(theta, dtype=torch.float32).cuda()
+    ss = torch.as_tensor(s, dtype=torch.int32).cuda()
+    return FastFactorizer(m, n, k, l).run(A, th, ss, stream=stream)
 
 
 def timed_step_names() -> list[str]:

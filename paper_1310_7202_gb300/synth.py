@@ -108,6 +108,10 @@ WORKLOADS = {
     # batched form: 4096 problems, sizes from batch_shapes, sigma_i = exp(-i/k), FP32
     "batch4096": dict(kind="batch", count=4096, spectrum="exp_k", dtype="f32", seed_shapes=4,
                       seed_u=41, seed_g=5000),
+    # fast randomized LU (Algorithm 4): n x n with l = 3 log2(n)^2 (the timing shape of the
+    # paper's comparison of Algorithms 1 and 4), k = 256, sigma_i = i^-2, FP32
+    "frlu_4096": dict(kind="fast", m=4096, n=4096, k=256, l=432, spectrum="inv_square",
+                      dtype="f32", seed_u=71, seed_v=72, seed_g=73),
     # served form: Poisson arrivals (rates and window from the bench's --serve-* flags)
     "serve": dict(kind="serve", spectrum="inv_1p5", dtype="mixed+bf16"),
 }
