@@ -50,6 +50,7 @@ __device__ __forceinline__ float2 crecip(float2 p) {
 
 static constexpr int FFT_T = 512;    // threads per row transform
 static constexpr int FFT_MAXV = 32;   // values per thread: n <= FFT_T * FFT_MAXV = 16384
+                                      // (kernels for n <= 4096 and 8192 hold 8 and 16)
 static constexpr int FFT_MAXST = 16;  // radix stages
 
 struct FftPlan {
@@ -130,9 +131,9 @@ __device__ __forceinline__ void dft_small<5>(float2 (&v)[5]) {
 // last stage): butterfly j reads j + r n/P, twiddles by exp(-2 pi i (j mod Ns) r / (Ns P)),
 // and writes (j / Ns) Ns P + (j mod Ns) + r Ns. All reads precede all writes (registers).
 // The twiddle powers w^r come from repeated products: a few float ulps for r <= 4.
-template <int P>
+template <int P, int MAXV>
 __device__ __forceinline__ void fft_stage(float2* buf, int n, int Ns) {
-  constexpr int Q = (FFT_MAXV + P - 1) / P;
+  constexpr int Q = (MAXV + P - 1) / P;
   const int nb = n / P;
   float2 v[Q][P];
 #pragma unroll
@@ -171,7 +172,8 @@ __device__ __forceinline__ void fft_stage(float2* buf, int n, int Ns) {
 
 // Row blockIdx.x of Y (row-major, ld ldy): Y[i][j] = scale * FFT(A[i, :] * d)[s_j].
 // An index s_j outside [0, n) sets *status = RLU_EINVAL and yields 0.
-__global__ void __launch_bounds__(FFT_T, 1) k_srft_rows(const float* __restrict__ A, int64_t lda,
+template <int MAXV>
+__global__ void __launch_bounds__(FFT_T) k_srft_rows(const float* __restrict__ A, int64_t lda,
                                                      int n, const float2* __restrict__ d,
                                                      const int32_t* __restrict__ sel, int l,
                                                      float scale, FftPlan plan,
@@ -180,19 +182,31 @@ __global__ void __launch_bounds__(FFT_T, 1) k_srft_rows(const float* __restrict_
   extern __shared__ __align__(16) float2 fbuf[];
   const int64_t row = blockIdx.x;
   const float* a = A + row * lda;
-  for (int c = threadIdx.x; c < n; c += FFT_T) {
-    const float x = a[c];
-    const float2 dc = d[c];
-    fbuf[c] = make_float2(x * dc.x, x * dc.y);
+  {  // all of a thread's loads in flight before its stores
+    float x[MAXV];
+    float2 dc[MAXV];
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int c = threadIdx.x + q * FFT_T;
+      if (c < n) {
+        x[q] = a[c];
+        dc[q] = d[c];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int c = threadIdx.x + q * FFT_T;
+      if (c < n) fbuf[c] = make_float2(x[q] * dc[q].x, x[q] * dc[q].y);
+    }
   }
   __syncthreads();
   // the plan lists its radices grouped (4s, 2s, 3s, 5s): one loop per radix keeps each
   // stage's registers separate
   int Ns = 1, st = 0;
-  for (; st < plan.nst && plan.radix[st] == 4; ++st, Ns *= 4) fft_stage<4>(fbuf, n, Ns);
-  for (; st < plan.nst && plan.radix[st] == 2; ++st, Ns *= 2) fft_stage<2>(fbuf, n, Ns);
-  for (; st < plan.nst && plan.radix[st] == 3; ++st, Ns *= 3) fft_stage<3>(fbuf, n, Ns);
-  for (; st < plan.nst && plan.radix[st] == 5; ++st, Ns *= 5) fft_stage<5>(fbuf, n, Ns);
+  for (; st < plan.nst && plan.radix[st] == 4; ++st, Ns *= 4) fft_stage<4, MAXV>(fbuf, n, Ns);
+  for (; st < plan.nst && plan.radix[st] == 2; ++st, Ns *= 2) fft_stage<2, MAXV>(fbuf, n, Ns);
+  for (; st < plan.nst && plan.radix[st] == 3; ++st, Ns *= 3) fft_stage<3, MAXV>(fbuf, n, Ns);
+  for (; st < plan.nst && plan.radix[st] == 5; ++st, Ns *= 5) fft_stage<5, MAXV>(fbuf, n, Ns);
   for (int j = threadIdx.x; j < l; j += FFT_T) {
     const int sj = sel[j];
     float2 v = make_float2(0.f, 0.f);
@@ -210,17 +224,23 @@ __global__ void __launch_bounds__(FFT_T, 1) k_srft_rows(const float* __restrict_
 // ---------------------------------------------------------------------------------------
 // Steps 3 and 7: complex LU with partial pivoting, all min(rows, cols) steps, as one
 // cooperative launch. CTA b holds rows [b R, b R + R) of the current order in shared memory
-// (row-major, cols entries each). Step j:
-//   * every CTA publishes its best candidate of column j (first maximum of |Re| + |Im| at
-//     positions >= j) with the whole candidate row; the owner of position j publishes row j;
+// (row-major, cols entries each). For step j:
+//   * every CTA offers its best candidate of column j (first maximum of |Re| + |Im| at
+//     positions >= j) by an atomicMax on a packed key (magnitude bits above the inverted
+//     position, so that equal magnitudes go to the smaller position) and publishes the whole
+//     candidate row; the owner of position j publishes row j;
 //   * grid barrier (bounded wait: RLU_ETIMEOUT after 2 s);
-//   * every CTA picks the same winner from the published candidates, reads the pivot row
-//     and performs the physical swap of rows j and r on the rows it owns, then updates its
+//   * every CTA reads the key (the winner's CTA follows from its position), reads the pivot
+//     row, performs the physical swap of rows j and r on the rows it owns, and updates its
 //     rows below j: Doolittle (unit diagonal on L: multipliers divided by the pivot) for Y,
 //     or Crout (unit diagonal on the pivot row: the row is divided by the pivot) for B^T.
-// The published rows are double-buffered by step parity: a CTA writes the buffer of step
-// j + 2 only after the barrier of step j + 1, which every CTA reaches after its reads of
-// step j. A zero pivot skips the swap and the update and is reported (LAPACK getf2).
+// Look-ahead: the update first completes column j + 1, the candidate row of step j + 1 and
+// the row at position j + 1, which are published before the rest of the update, so that
+// the rest overlaps the barrier of step j + 1. Published rows are double-buffered by step
+// parity (a CTA writes the buffer of step j + 2 only after the barrier of step j + 1, which
+// every CTA passes after its reads of step j); keys rotate over three slots, slot (j + 2) % 3
+// being cleared by CTA 0 after the barrier of step j. A zero pivot skips the swap and the
+// update and is reported (LAPACK getf2).
 // ---------------------------------------------------------------------------------------
 
 static constexpr int CLU_T = 512;
@@ -233,9 +253,8 @@ struct CluArgs {
   int rloc;           // rows per CTA
   int32_t* perm;      // gather form: position i holds original row perm[i]
   float2* pub_rows;   // [2][G + 1][cols]
-  float* pub_mag;     // [2][G]
-  int* pub_pos;       // [2][G]
   int* pub_idx;       // [2][G + 1]
+  unsigned long long* key;  // [3], zero before the launch
   unsigned* bar;      // zero before the launch
   int32_t* status;
   int32_t* first_zero;
@@ -252,14 +271,19 @@ __device__ __forceinline__ uint64_t clu_now_ns() {
   return t;
 }
 
-// Arrive and wait until the counter reaches target; false (and RLU_ETIMEOUT in *status)
-// when it does not within 2 s.
-__device__ __forceinline__ bool clu_grid_barrier(unsigned* bar, unsigned target,
-                                                 int32_t* status, int* s_ok) {
+// Arrival at the grid barrier: every thread's prior writes, then one increment.
+__device__ __forceinline__ void clu_arrive(unsigned* bar) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     atomicAdd(bar, 1u);
+  }
+}
+// Wait until the counter reaches target; false (and RLU_ETIMEOUT in *status) when it does
+// not within 2 s.
+__device__ __forceinline__ bool clu_wait(unsigned* bar, unsigned target, int32_t* status,
+                                         int* s_ok) {
+  if (threadIdx.x == 0) {
     bool ok = true;
     if (ld_acquire_u32(bar) < target) {
       const uint64_t t0 = clu_now_ns();
@@ -278,17 +302,58 @@ __device__ __forceinline__ bool clu_grid_barrier(unsigned* bar, unsigned target,
   return *s_ok != 0;
 }
 
-__device__ __forceinline__ void cand_reduce(float& mag, int& pos, int& who) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float om = __shfl_xor_sync(0xffffffffu, mag, off);
-    const int op = __shfl_xor_sync(0xffffffffu, pos, off);
-    const int ow = __shfl_xor_sync(0xffffffffu, who, off);
-    if (cand_better(om, op, mag, pos)) {
-      mag = om;
-      pos = op;
-      who = ow;
+// Packed candidate: |Re| + |Im| (non-negative, so its bits order like the values) above
+// the inverted position; 0 means no candidate.
+__device__ __forceinline__ unsigned long long clu_pack(float mag, int pos) {
+  return ((unsigned long long)__float_as_uint(mag) << 32) | (unsigned)(0xFFFFFFFFu - (unsigned)pos);
+}
+
+template <bool CROUT>
+__device__ __forceinline__ void clu_candidate(const float2* tile, int cols, int nloc, int base,
+                                              int col, int* s_cpos, unsigned long long* key) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    float mag = -1.f;
+    int pos = INT_MAX;
+    for (int r = lane; r < nloc; r += 32) {
+      const int p = base + r;
+      if (p < col) continue;
+      const float2 v = tile[(size_t)r * cols + col];
+      const float mg = fabsf(v.x) + fabsf(v.y);
+      if (cand_better(mg, p, mag, pos)) {
+        mag = mg;
+        pos = p;
+      }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float om = __shfl_xor_sync(0xffffffffu, mag, off);
+      const int op = __shfl_xor_sync(0xffffffffu, pos, off);
+      if (cand_better(om, op, mag, pos)) {
+        mag = om;
+        pos = op;
+      }
+    }
+    if (lane == 0) {
+      *s_cpos = pos;
+      if (pos != INT_MAX) atomicMax(key, clu_pack(mag, pos));
+    }
+  }
+}
+
+// Publish the candidate row (if any) and the row at position col (if owned) for step col.
+__device__ __forceinline__ void clu_publish(const float2* tile, const int* idx, int cols,
+                                            int nloc, int base, int col, int cpos, int b, int G,
+                                            float2* prow, int* pidx) {
+  if (cpos != INT_MAX) {
+    const float2* src = tile + (size_t)(cpos - base) * cols;
+    for (int c = threadIdx.x; c < cols; c += CLU_T) prow[(size_t)b * cols + c] = src[c];
+    if (threadIdx.x == 0) pidx[b] = idx[cpos - base];
+  }
+  if (col >= base && col < base + nloc) {
+    const float2* src = tile + (size_t)(col - base) * cols;
+    for (int c = threadIdx.x; c < cols; c += CLU_T) prow[(size_t)G * cols + c] = src[c];
+    if (threadIdx.x == 0) pidx[G] = idx[col - base];
   }
 }
 
@@ -300,84 +365,48 @@ __global__ void __launch_bounds__(CLU_T, 1) k_clu_coop(CluArgs a) {
   float2* piv = tile + (size_t)a.rloc * cols;                   // [cols]
   int* idx = reinterpret_cast<int*>(piv + cols);                // [rloc]
   __shared__ int s_ok, s_cpos, s_w, s_r;
-  __shared__ float s_cmag;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
   const int base = b * a.rloc;
   const int nloc = max(0, min(a.rloc, a.rows - base));
   const int steps = min(a.rows, cols);
+  const int tx = tid % CLU_TX, ty = tid / CLU_TX;
   for (int e = tid; e < nloc * cols; e += CLU_T)
     tile[e] = a.Y[(int64_t)(base + e / cols) * a.ldy + e % cols];
   for (int r = tid; r < nloc; r += CLU_T) idx[r] = base + r;
   __syncthreads();
+  // step 0's candidates
+  clu_candidate<CROUT>(tile, cols, nloc, base, 0, &s_cpos, a.key);
+  __syncthreads();
+  clu_publish(tile, idx, cols, nloc, base, 0, s_cpos, b, G, a.pub_rows, a.pub_idx);
+  clu_arrive(a.bar);
   for (int j = 0; j < steps; ++j) {
     const int par = j & 1;
-    float2* prow = a.pub_rows + (size_t)par * (G + 1) * cols;
-    float* pmag = a.pub_mag + (size_t)par * G;
-    int* ppos = a.pub_pos + (size_t)par * G;
-    int* pidx = a.pub_idx + (size_t)par * (G + 1);
-    // local candidate of column j
-    if (warp == 0) {
-      float mag = -1.f;
-      int pos = INT_MAX, who = 0;
-      for (int r = lane; r < nloc; r += 32) {
-        const int p = base + r;
-        if (p < j) continue;
-        const float2 v = tile[(size_t)r * cols + j];
-        const float mg = fabsf(v.x) + fabsf(v.y);
-        if (cand_better(mg, p, mag, pos)) {
-          mag = mg;
-          pos = p;
-        }
-      }
-      cand_reduce(mag, pos, who);
-      if (lane == 0) {
-        s_cpos = pos;
-        s_cmag = mag;
-      }
-    }
-    __syncthreads();
-    const int cpos = s_cpos;
-    if (cpos != INT_MAX) {
-      const float2* src = tile + (size_t)(cpos - base) * cols;
-      for (int c = tid; c < cols; c += CLU_T) prow[(size_t)b * cols + c] = src[c];
-      if (tid == 0) pidx[b] = idx[cpos - base];
-    }
+    const float2* prow = a.pub_rows + (size_t)par * (G + 1) * cols;
+    const int* pidx = a.pub_idx + (size_t)par * (G + 1);
+    if (!clu_wait(a.bar, (unsigned)G * (unsigned)(j + 1), a.status, &s_ok)) return;
     if (tid == 0) {
-      pmag[b] = s_cmag;
-      ppos[b] = cpos;
-    }
-    const bool own_j = j >= base && j < base + nloc;
-    if (own_j) {
-      const float2* src = tile + (size_t)(j - base) * cols;
-      for (int c = tid; c < cols; c += CLU_T) prow[(size_t)G * cols + c] = src[c];
-      if (tid == 0) pidx[G] = idx[j - base];
-    }
-    if (!clu_grid_barrier(a.bar, (unsigned)G * (unsigned)(j + 1), a.status, &s_ok)) return;
-    // the winner: the same reduction over the same published values in every CTA
-    if (warp == 0) {
-      float mag = -1.f;
-      int pos = INT_MAX, who = -1;
-      for (int g = lane; g < G; g += 32) {
-        const int p = __ldcg(ppos + g);
-        if (p == INT_MAX) continue;
-        const float mg = __ldcg(pmag + g);
-        if (cand_better(mg, p, mag, pos)) {
-          mag = mg;
-          pos = p;
-          who = g;
-        }
-      }
-      cand_reduce(mag, pos, who);
-      if (lane == 0) {
-        s_w = (mag > 0.f) ? who : -1;  // zero (or no finite) pivot: -1
-        s_r = pos;
-      }
+      const unsigned long long kv = __ldcg(a.key + j % 3);
+      const float mag = __uint_as_float((unsigned)(kv >> 32));
+      const int pos = (int)(0xFFFFFFFFu - (unsigned)(kv & 0xFFFFFFFFu));
+      const bool valid = kv != 0ull && pos >= j && pos < a.rows;
+      s_w = (valid && mag > 0.f) ? pos / a.rloc : -1;  // zero (or no finite) pivot: -1
+      s_r = pos;
+      if (b == 0) a.key[(j + 2) % 3] = 0ull;             // the slot of step j + 2
     }
     __syncthreads();
     const int w = s_w, r = s_r;
-    if (w < 0) {
+    const bool last = j + 1 >= steps;
+    const int parn = (j + 1) & 1;
+    float2* prown = a.pub_rows + (size_t)parn * (G + 1) * cols;
+    int* pidxn = a.pub_idx + (size_t)parn * (G + 1);
+    if (w < 0) {  // nothing to eliminate: the next step's candidates as they stand
       if (b == 0 && tid == 0 && a.first_zero) atomicCAS(a.first_zero, -1, j);
+      if (!last) {
+        clu_candidate<CROUT>(tile, cols, nloc, base, j + 1, &s_cpos, a.key + (j + 1) % 3);
+        __syncthreads();
+        clu_publish(tile, idx, cols, nloc, base, j + 1, s_cpos, b, G, prown, pidxn);
+        clu_arrive(a.bar);
+      }
       continue;
     }
     const float2* wsrc = prow + (size_t)w * cols;
@@ -394,23 +423,50 @@ __global__ void __launch_bounds__(CLU_T, 1) k_clu_coop(CluArgs a) {
       for (int c = tid; c < cols; c += CLU_T) tile[(size_t)(r - base) * cols + c] = __ldcg(src + c);
       if (tid == 0) idx[r - base] = __ldcg(pidx + G);
     }
-    if (own_j) {
+    if (j >= base && j < base + nloc) {
       for (int c = tid; c < cols; c += CLU_T) tile[(size_t)(j - base) * cols + c] = piv[c];
       if (tid == 0) idx[j - base] = __ldcg(pidx + w);
     }
     __syncthreads();
-    // rows below position j
+    // rows below position j: multipliers (Doolittle) and column j + 1
     const int r0 = max(j + 1 - base, 0);
-    if (!CROUT) {
-      for (int rr = r0 + tid; rr < nloc; rr += CLU_T)
-        tile[(size_t)rr * cols + j] = cmul(tile[(size_t)rr * cols + j], pinv);
-      __syncthreads();
+    for (int rr = r0 + tid; rr < nloc; rr += CLU_T) {
+      float2* trow = tile + (size_t)rr * cols;
+      float2 lv = trow[j];
+      if (!CROUT) {
+        lv = cmul(lv, pinv);
+        trow[j] = lv;
+      }
+      if (!last) trow[j + 1] = cfms(trow[j + 1], lv, piv[j + 1]);
     }
-    const int tx = tid % CLU_TX, ty = tid / CLU_TX;
+    __syncthreads();
+    int ca = -1, cb = -1;  // local rows updated ahead of the others
+    if (!last) {
+      clu_candidate<CROUT>(tile, cols, nloc, base, j + 1, &s_cpos, a.key + (j + 1) % 3);
+      __syncthreads();
+      const int cpos = s_cpos;
+      ca = cpos != INT_MAX ? cpos - base : -1;
+      cb = (j + 1 >= base && j + 1 < base + nloc) ? j + 1 - base : -1;
+      if (cb == ca) cb = -1;
+      // complete the two rows the next step publishes (warp 0: ca, warp 1: cb)
+      const int wid = tid >> 5, lane = tid & 31;
+      const int rr = wid == 0 ? ca : (wid == 1 ? cb : -1);
+      if (rr >= 0) {
+        float2* trow = tile + (size_t)rr * cols;
+        const float2 lv = trow[j];
+        for (int c = j + 2 + lane; c < cols; c += 32) trow[c] = cfms(trow[c], lv, piv[c]);
+      }
+      __syncthreads();
+      clu_publish(tile, idx, cols, nloc, base, j + 1, cpos, b, G, prown, pidxn);
+      clu_arrive(a.bar);
+    }
+    // the rest of the update overlaps the barrier of step j + 1
+    const int c0 = last ? j + 1 : j + 2;
     for (int rr = r0 + ty; rr < nloc; rr += CLU_TY) {
+      if (rr == ca || rr == cb) continue;
       float2* trow = tile + (size_t)rr * cols;
       const float2 lv = trow[j];
-      for (int c = j + 1 + tx; c < cols; c += CLU_TX) trow[c] = cfms(trow[c], lv, piv[c]);
+      for (int c = c0 + tx; c < cols; c += CLU_TX) trow[c] = cfms(trow[c], lv, piv[c]);
     }
     __syncthreads();
   }
@@ -424,10 +480,9 @@ static size_t clu_smem_bytes(int rloc, int cols) {
          (size_t)rloc * sizeof(int);
 }
 
-// Workspace of the published rows for up to G CTAs.
+// Workspace of the barrier, the keys and the published rows for up to G CTAs.
 static size_t clu_pub_bytes(int G, int cols) {
-  return 2 * (size_t)(G + 1) * cols * sizeof(float2) + 2 * (size_t)G * (sizeof(float) + sizeof(int)) +
-         2 * (size_t)(G + 1) * sizeof(int) + 256;
+  return 256 + 2 * (size_t)(G + 1) * cols * sizeof(float2) + 2 * (size_t)(G + 1) * sizeof(int);
 }
 
 // CTAs and rows per CTA for a rows x cols LU; false when the rows do not fit.
@@ -436,6 +491,7 @@ static bool clu_shape(int rows, int cols, int* G, int* rloc) {
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
+  if (rows < 1) return false;
   int g = (int)ceil_div(rows, 8);
   if (g > sm_count()) g = sm_count();
   if (g < 1) g = 1;
@@ -459,14 +515,11 @@ static int32_t clu_coop(bool crout, float2* Y, int64_t ldy, int rows, int cols, 
   a.cols = cols;
   a.rloc = rloc;
   a.perm = perm;
-  a.bar = reinterpret_cast<unsigned*>(p);
+  a.bar = reinterpret_cast<unsigned*>(p);                      // header: barrier, 3 keys
+  a.key = reinterpret_cast<unsigned long long*>(p + 64);
   p += 256;
   a.pub_rows = reinterpret_cast<float2*>(p);
   p += 2 * (size_t)(G + 1) * cols * sizeof(float2);
-  a.pub_mag = reinterpret_cast<float*>(p);
-  p += 2 * (size_t)G * sizeof(float);
-  a.pub_pos = reinterpret_cast<int*>(p);
-  p += 2 * (size_t)G * sizeof(int);
   a.pub_idx = reinterpret_cast<int*>(p);
   a.status = status;
   a.first_zero = first_zero;
@@ -477,7 +530,7 @@ static int32_t clu_coop(bool crout, float2* Y, int64_t ldy, int rows, int cols, 
   int per_sm = 0;
   RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, CLU_T, smem));
   if (per_sm * sm_count() < G) return RLU_EUNSUPPORTED;
-  RLU_CUDA_TRY(cudaMemsetAsync(a.bar, 0, sizeof(unsigned), s));
+  RLU_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 256, s));
   void* args[] = {&a};
   RLU_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(CLU_T), args, smem, s));
   return last_launch_status();
@@ -543,47 +596,104 @@ __global__ void k_frlu_embed(const double* __restrict__ V, int64_t ldv, int k, i
 }
 
 // W = V L_1^{-1} (k x l) for the unit lower L_1 (the leading l x l block of the factored Y):
-// warp a solves w L_1 = V[a, :] by columns from the last, w_b = v_b, then v_c -= w_b L_1[b][c]
-// for c < b. Lane t holds entries c = lane + 32 s (s < NS, l <= 32 NS). Writes the planes
+// row a solves w L_1 = V[a, :] by 32-column blocks from the last. Each row is held by
+// WS_PARTS warps: lane t of part q holds the entries c = lane + 32 s for the blocks
+// s = q + WS_PARTS u (u < NS / WS_PARTS, l <= 32 NS). For block sb the CTA stages rows
+// 32 sb .. 32 sb + 31 of L_1 (columns up to the block's end) in shared memory; the part that
+// holds the block finalises its columns from the last down (w_b = v_b, then
+// v_c -= w_b L_1[b][c] for c < b inside the block) and shares the 32 values w; then every
+// part updates its blocks left of sb, v_c -= sum_b w_b L_1[b][c]. Writes the planes
 // Wst[a] = Re w, Wst[k + a] = Im w (2k x l row-major, ld ldw).
+static constexpr int WS_ROWS = 4;   // rows of W per CTA
+static constexpr int WS_PARTS = 4;  // warps per row
+static constexpr int WS_T = 32 * WS_ROWS * WS_PARTS;
+
 template <int NS>
-__global__ void __launch_bounds__(256) k_frlu_wsolve(const double* __restrict__ V, int64_t ldv,
-                                                     int k, int l, const float2* __restrict__ Y,
-                                                     int64_t ldy, float* __restrict__ Wst,
-                                                     int64_t ldw) {
-  const int a = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (a >= k) return;
-  float2 v[NS];
+__global__ void __launch_bounds__(WS_T) k_frlu_wsolve(const double* __restrict__ V, int64_t ldv,
+                                                      int k, int l, const float2* __restrict__ Y,
+                                                      int64_t ldy, float* __restrict__ Wst,
+                                                      int64_t ldw) {
+  extern __shared__ __align__(16) float2 ws_rows[];  // [32][32 NS]
+  __shared__ float2 wbuf[WS_ROWS][32];
+  constexpr int LDS = 32 * NS;
+  constexpr int NU = (NS + WS_PARTS - 1) / WS_PARTS;  // blocks per part
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = warp / WS_PARTS, q = warp % WS_PARTS;
+  const int a = blockIdx.x * WS_ROWS + row;
+  const bool active = a < k;
+  float2 v[NU];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const int c = lane + 32 * s;
-    v[s] = c < l ? make_float2((float)V[(int64_t)a * ldv + c], (float)V[(int64_t)a * ldv + l + c])
-                 : make_float2(0.f, 0.f);
+  for (int u = 0; u < NU; ++u) {
+    const int c = lane + 32 * (q + WS_PARTS * u);
+    v[u] = (active && c < l)
+               ? make_float2((float)V[(int64_t)a * ldv + c], (float)V[(int64_t)a * ldv + l + c])
+               : make_float2(0.f, 0.f);
   }
 #pragma unroll
   for (int sb = NS - 1; sb >= 0; --sb) {
-    for (int li = 31; li >= 0; --li) {
-      const int bcol = 32 * sb + li;
-      if (bcol >= l) continue;
-      const float2 wb = make_float2(__shfl_sync(0xffffffffu, v[sb].x, li),
-                                    __shfl_sync(0xffffffffu, v[sb].y, li));
-      const float2* Lrow = Y + (int64_t)bcol * ldy;
+    if (32 * sb >= l) continue;  // the same for every thread
+    const int ncol = min(32 * sb + 32, l);
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += WS_T) {  // 8 independent loads in flight
 #pragma unroll
-      for (int s = 0; s <= sb; ++s) {
-        const int c = lane + 32 * s;
-        if (c < bcol) v[s] = cfms(v[s], wb, Lrow[c]);
+      for (int i0 = 0; i0 < 32; i0 += 8) {
+        float2 t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int bi = 32 * sb + i0 + u;
+          t[u] = bi < l ? Y[(int64_t)bi * ldy + c] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ws_rows[(i0 + u) * LDS + c] = t[u];
+      }
+    }
+    __syncthreads();
+    // the part holding block sb solves it
+    if (q == sb % WS_PARTS) {
+      float2 x = v[sb / WS_PARTS];
+      for (int li = 31; li >= 0; --li) {
+        if (32 * sb + li >= l) continue;
+        const float2 wb = make_float2(__shfl_sync(0xffffffffu, x.x, li),
+                                      __shfl_sync(0xffffffffu, x.y, li));
+        if (lane < li) x = cfms(x, wb, ws_rows[li * LDS + 32 * sb + lane]);
+      }
+      v[sb / WS_PARTS] = x;
+      wbuf[row][lane] = x;
+    }
+    __syncthreads();
+    if (sb > 0) {
+      for (int bb = 0; bb < 32; ++bb) {
+        if (32 * sb + bb >= l) break;
+        const float2 wb = wbuf[row][bb];
+        const float2* Lrow = ws_rows + bb * LDS + lane;
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int sblk = q + WS_PARTS * u;
+          if (sblk < sb) v[u] = cfms(v[u], wb, Lrow[32 * sblk]);
+        }
       }
     }
   }
+  if (!active) return;
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const int c = lane + 32 * s;
+  for (int u = 0; u < NU; ++u) {
+    const int c = lane + 32 * (q + WS_PARTS * u);
     if (c < l) {
-      Wst[(int64_t)a * ldw + c] = v[s].x;
-      Wst[(int64_t)(k + a) * ldw + c] = v[s].y;
+      Wst[(int64_t)a * ldw + c] = v[u].x;
+      Wst[(int64_t)(k + a) * ldw + c] = v[u].y;
     }
   }
+}
+
+template <int NS>
+static int32_t wsolve_launch(const double* V, int64_t ldv, int k, int l, const float2* Y,
+                             int64_t ldy, float* Wst, int64_t ldw, cudaStream_t s) {
+  const size_t smem = 32 * 32 * NS * sizeof(float2);
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_frlu_wsolve<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  k_frlu_wsolve<NS><<<(unsigned)ceil_div(k, WS_ROWS), WS_T, smem, s>>>(V, ldv, k, l, Y, ldy, Wst,
+                                                                       ldw);
+  return last_launch_status();
 }
 
 // A(J,:) (l x n, row-major, ld ldaj): row i is row perm[i] of A.
@@ -725,11 +835,16 @@ static int32_t srft_apply(const float* A, int64_t m, int64_t n, int64_t lda, con
   k_srft_phase<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(theta, (int)n, d);
   RLU_TRY(last_launch_status());
   const size_t fsmem = (size_t)n * sizeof(float2);
-  RLU_CUDA_TRY(cudaFuncSetAttribute(k_srft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
-  k_srft_rows<<<(unsigned)m, FFT_T, fsmem, s>>>(A, lda, (int)n, d, sel, l,
-                                                (float)(1.0 / std::sqrt((double)n)), f, Y, ldy,
-                                                status);
-  return last_launch_status();
+  const float scale = (float)(1.0 / std::sqrt((double)n));
+  // the narrowest register array that holds n values over FFT_T threads
+  auto go = [&](auto kern) -> int32_t {
+    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    kern<<<(unsigned)m, FFT_T, fsmem, s>>>(A, lda, (int)n, d, sel, l, scale, f, Y, ldy, status);
+    return last_launch_status();
+  };
+  if (n <= FFT_T * 8) return go(k_srft_rows<8>);
+  if (n <= FFT_T * 16) return go(k_srft_rows<16>);
+  return go(k_srft_rows<FFT_MAXV>);
 }
 
 static int32_t fast_factor(const FastPlan& p, const float* A, int64_t m, int64_t n, int64_t lda,
@@ -779,15 +894,16 @@ static int32_t fast_factor(const FastPlan& p, const float* A, int64_t m, int64_t
   o.kp = p.kp;
   RLU_TRY(ldl_factor<float>(Mre, k2, o, status, s));
   {
-    const unsigned blocks = (unsigned)ceil_div(k, 8);
+    const int64_t ldv = 2 * (int64_t)l;
+    int32_t st;
     switch (p.ns) {
-      case 1: k_frlu_wsolve<1><<<blocks, 256, 0, s>>>(V, 2 * (int64_t)l, k, l, Y, l, Wst, l); break;
-      case 2: k_frlu_wsolve<2><<<blocks, 256, 0, s>>>(V, 2 * (int64_t)l, k, l, Y, l, Wst, l); break;
-      case 4: k_frlu_wsolve<4><<<blocks, 256, 0, s>>>(V, 2 * (int64_t)l, k, l, Y, l, Wst, l); break;
-      case 8: k_frlu_wsolve<8><<<blocks, 256, 0, s>>>(V, 2 * (int64_t)l, k, l, Y, l, Wst, l); break;
-      default: k_frlu_wsolve<16><<<blocks, 256, 0, s>>>(V, 2 * (int64_t)l, k, l, Y, l, Wst, l); break;
+      case 1: st = wsolve_launch<1>(V, ldv, k, l, Y, l, Wst, l, s); break;
+      case 2: st = wsolve_launch<2>(V, ldv, k, l, Y, l, Wst, l, s); break;
+      case 4: st = wsolve_launch<4>(V, ldv, k, l, Y, l, Wst, l, s); break;
+      case 8: st = wsolve_launch<8>(V, ldv, k, l, Y, l, Wst, l, s); break;
+      default: st = wsolve_launch<16>(V, ldv, k, l, Y, l, Wst, l, s); break;
     }
-    RLU_TRY(last_launch_status());
+    RLU_TRY(st);
   }
   k_frlu_gather_aj<<<dim3((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)l), 256, 0, s>>>(
       A, lda, (int)n, P, AJ, p.ldn);
@@ -796,7 +912,7 @@ static int32_t fast_factor(const FastPlan& p, const float* A, int64_t m, int64_t
     GemmOp op{Wst, l, true, AJ, p.ldn, false, Cst, p.ldn, true, k2, n, l, 1, nullptr, false};
     RLU_TRY((gemm_simt<float, float>(op, s)));
   }
-  RLU_TRY(trsm_ldl<float>(o, Cst, p.ldn, n, Bst, p.ldn, s));
+  RLU_TRY(trsm_ldl<float>(o, Cst, p.ldn, n, Bst, p.ldn, s, ceil_div(n, 64) < sm_count()));
   // step 7: B Q = L_b U_b through the Crout LU of B^T
   k_frlu_pack_bt<<<dim3((unsigned)ceil_div(n, 32), (unsigned)ceil_div(k, 32)), dim3(32, 8), 0, s>>>(
       Bst, p.ldn, k, (int)n, Bt, k);

@@ -1010,11 +1010,13 @@ static int32_t trsm_launch(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t 
 
 template <typename T>
 int32_t trsm_ldl(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t n, T* B, int64_t ldb,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool narrow) {
   int dev = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
   int optin = 0;
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (narrow && trsm_smem_bytes<T>(o.kp, 32) <= (size_t)optin)
+    return trsm_launch<T, 32>(o, C, ldc, n, B, ldb, trsm_smem_bytes<T>(o.kp, 32), s);
   if (trsm_smem_bytes<T>(o.kp, 64) <= (size_t)optin)
     return trsm_launch<T, 64>(o, C, ldc, n, B, ldb, trsm_smem_bytes<T>(o.kp, 64), s);
   if (trsm_smem_bytes<T>(o.kp, 32) <= (size_t)optin)
@@ -1022,9 +1024,9 @@ int32_t trsm_ldl(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t n, T* B, i
   return RLU_EUNSUPPORTED;
 }
 template int32_t trsm_ldl<float>(const LdlOut<float>&, const float*, int64_t, int64_t, float*,
-                                 int64_t, cudaStream_t);
+                                 int64_t, cudaStream_t, bool);
 template int32_t trsm_ldl<double>(const LdlOut<double>&, const double*, int64_t, int64_t, double*,
-                                  int64_t, cudaStream_t);
+                                  int64_t, cudaStream_t, bool);
 
 // L_b (k x k, column-major, ld k): L_b[i][j] = X^T-stored B[i][Q[j]] for i > j, 1 on the
 // diagonal, 0 above. B is row-major k x n (ld ldb).

@@ -45,10 +45,11 @@ int32_t ldl_factor(double* M, int k, const LdlOut<T>& o, int32_t* status, cudaSt
 // Whether ldl_factor handles a k x k Gram (FP32 outputs: f32).
 bool ldl_factor_supported(int k, bool f32);
 
-// B (k x n, row-major) = L^{-T} D^{-1} L^{-1} C (C k x n row-major).
+// B (k x n, row-major) = L^{-T} D^{-1} L^{-1} C (C k x n row-major). narrow: 32 columns per
+// CTA (twice the CTAs of the default 64, for right-hand sides too few to fill the GPU).
 template <typename T>
 int32_t trsm_ldl(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t n, T* B, int64_t ldb,
-                 cudaStream_t s);
+                 cudaStream_t s, bool narrow = false);
 
 template <typename T>
 int32_t gather_lb_u(const T* B, int64_t ldb, const int32_t* Q, int k, int64_t n, T* Lb, T* U,
