@@ -46,7 +46,8 @@ typedef struct {
 /* Kernel choices of a batch (the autotuner's knobs; zero-initialised = defaults).
  *   gemm_tile_y, gemm_tile_c, gemm_tile_l: SIMT output tile of the products Y = A G,
  *     C = L~^T A and L = L_y L_b: 0 = 128 x 128, 1 = 64 x 64 (Y and C use the tensor cores
- *     under RLU_PREC_MIXED; their knobs are then ignored).
+ *     under RLU_PREC_MIXED; their knobs are then ignored; when every k <= 64, L = L_y L_b
+ *     runs one thread per row and gemm_tile_l is ignored).
  *   lu_rows_per_cta: rows of an LU held by one CTA of a problem's cluster: 0 or 512 (512
  *     threads), 256 (256 threads, twice the CTAs per problem; m and n <= 4096).
  *   umma_ctas_y, umma_ctas_c: under RLU_PREC_MIXED, CTAs of the tensor-core product Y = A G

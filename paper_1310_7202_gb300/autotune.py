@@ -84,6 +84,8 @@ def _applicable(knob: str, prec, problems: list[dict], value) -> bool:
         return value == DEFAULTS[knob]  # tensor-core products: the SIMT tile is unused
     if not mixed and knob in ("umma_ctas_y", "umma_ctas_c"):
         return value == DEFAULTS[knob]  # SIMT products: no tensor-core ring
+    if knob == "gemm_tile_l" and max(p["k"] for p in problems) <= 64:
+        return value == DEFAULTS[knob]  # L = L_y L_b runs one thread per row
     if knob == "lu_rows_per_cta":
         tallest = max(max(p["A"].shape) for p in problems)
         return tallest <= 16 * value

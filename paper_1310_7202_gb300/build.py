@@ -47,7 +47,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    headers.append(os.path.join(ROOT, "include", "rlu.h"))
+    inc = os.path.join(ROOT, "include")
+    headers += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     newest_hdr = max(os.path.getmtime(h) for h in headers)
     jobs = []
     objs = []

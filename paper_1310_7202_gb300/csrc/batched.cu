@@ -42,10 +42,14 @@ struct ProblemLayout {
 
 struct Tables {
   size_t info, gauss, gemm_y, lu_y, build, gemm_g, ldl, gemm_c, trsm, lu_b, gather, gemm_l,
-      u3y, u3c, u3y_tiles, u3c_tiles, trsm_tiles;
+      u3y, u3c, u3y_tiles, u3c_tiles, trsm_tiles, lmul_tiles;
   int n_tiles_y, n_tiles_c;  // 128-row tiles of the two tensor-core products
-  int n_tiles_t;             // 64-column blocks of the substitution B = M^{-1} C
+  int n_tiles_t;             // column blocks of the substitution B = M^{-1} C
+  int n_tiles_l;             // 256-row blocks of L = L_y L_b (small k only)
+  bool small_k;              // every k <= 64: register kernels for the solve and L
 };
+
+constexpr int kSmallK = 64;
 
 // LU group of a problem with R rows (see rlu_batch) and its rows per CTA: small problems
 // take one narrow CTA, so that several of them share an SM.
@@ -86,9 +90,15 @@ size_t plan_layout(const rlu_problem* probs, int count, int32_t prec, Tables& t,
   t.ldl = carve(cur, c * sizeof(Ldl32Job));
   t.gemm_c = carve(cur, c * sizeof(GemmArgs));
   t.trsm = carve(cur, c * sizeof(TrsmJob));
-  t.n_tiles_t = 0;
-  for (int i = 0; i < count; ++i) t.n_tiles_t += (int)ceil_div(probs[i].n, 64);
+  t.small_k = true;
+  for (int i = 0; i < count; ++i) t.small_k = t.small_k && probs[i].k <= kSmallK;
+  t.n_tiles_t = t.n_tiles_l = 0;
+  for (int i = 0; i < count; ++i) {
+    t.n_tiles_t += (int)ceil_div(probs[i].n, t.small_k ? 128 : 64);
+    if (t.small_k) t.n_tiles_l += (int)ceil_div(probs[i].m, 256);
+  }
   t.trsm_tiles = carve(cur, (size_t)t.n_tiles_t * sizeof(int2));
+  t.lmul_tiles = carve(cur, (size_t)t.n_tiles_l * sizeof(int2));
   t.lu_b = carve(cur, c * sizeof(LuArgs));
   t.gather = carve(cur, c * sizeof(GatherJob));
   t.gemm_l = carve(cur, c * sizeof(GemmArgs));
@@ -167,6 +177,7 @@ struct rlu_batch {
   int launches = 0;
   // tensor-core rings of the mixed precision (Y = A G, C = L~^T A)
   int u3y_stages = 0, u3y_stage_bytes = 0, u3c_stages = 0, u3c_stage_bytes = 0;
+  int ts_first[4] = {}, ts_count[4] = {};  // small-k substitution tiles per bucket of k
   rlu_batch_options opt{};
 };
 
@@ -364,12 +375,25 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   if (st == RLU_OK) st = up(t.lu_b, lub.data(), c * sizeof(LuArgs));
   if (st == RLU_OK) st = up(t.gather, gather.data(), c * sizeof(GatherJob));
   if (st == RLU_OK) st = up(t.gemm_l, gl.data(), c * sizeof(GemmArgs));
-  {  // substitution tile list: (problem, 64-column block), the blocks of a problem together
-    std::vector<int2> tt;
+  {  // tile lists of the substitution (problem, column block) and of L (problem, row
+     // block), the blocks of a problem next to each other
+    std::vector<int2> tt, tl;
     tt.reserve((size_t)t.n_tiles_t);
-    for (int i = 0; i < count; ++i)
-      for (int cb = 0; cb < (int)ceil_div(problems[i].n, 64); ++cb) tt.push_back(make_int2(i, cb));
+    tl.reserve((size_t)t.n_tiles_l);
+    const int cw = t.small_k ? 128 : 64;
+    // small k: the substitution's tiles grouped by the bucket of k (one launch each)
+    for (int bkt = 0; bkt < (t.small_k ? 4 : 1); ++bkt) {
+      if (t.small_k) b->ts_first[bkt] = (int)tt.size();
+      for (int i = 0; i < count; ++i) {
+        if (t.small_k && trsm_small_bucket(problems[i].k) != bkt) continue;
+        for (int cb = 0; cb < (int)ceil_div(problems[i].n, cw); ++cb) tt.push_back(make_int2(i, cb));
+      }
+      if (t.small_k) b->ts_count[bkt] = (int)tt.size() - b->ts_first[bkt];
+    }
+    for (int i = 0; i < count && t.small_k; ++i)
+      for (int rb = 0; rb < (int)ceil_div(problems[i].m, 256); ++rb) tl.push_back(make_int2(i, rb));
     if (st == RLU_OK) st = up(t.trsm_tiles, tt.data(), tt.size() * sizeof(int2));
+    if (st == RLU_OK && !tl.empty()) st = up(t.lmul_tiles, tl.data(), tl.size() * sizeof(int2));
   }
   if (mixed && st == RLU_OK) {
     // ring depth: the deepest for one CTA per SM, else a ring that lets two CTAs share an
@@ -406,7 +430,9 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   }
   int groups = 0;
   for (int g = 1; g < kLuGroups; ++g) groups += (b->count_y[g] > 0) + (b->count_b[g] > 0);
-  b->launches = 10 + groups;
+  int buckets = 0;  // the small-k substitution: one launch per nonempty bucket of k
+  for (int bkt = 0; bkt < 4; ++bkt) buckets += b->ts_count[bkt] > 0;
+  b->launches = 10 + groups + (t.small_k && buckets > 1 ? buckets - 1 : 0);
   *out = b;
   return RLU_OK;
 }
@@ -447,17 +473,26 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_c),
                                              c, b->max_k, b->max_n, true, false, true, s,
                                              b->opt.gemm_tile_c)));
-  RLU_TRY(trsm_batched(reinterpret_cast<const TrsmJob*>(ws + t.trsm),
-                       reinterpret_cast<const int2*>(ws + t.trsm_tiles), t.n_tiles_t, b->max_kp,
-                       s));
+  if (t.small_k)
+    RLU_TRY(trsm_small_batched(reinterpret_cast<const TrsmJob*>(ws + t.trsm),
+                               reinterpret_cast<const int2*>(ws + t.trsm_tiles), b->ts_first,
+                               b->ts_count, s));
+  else
+    RLU_TRY(trsm_batched(reinterpret_cast<const TrsmJob*>(ws + t.trsm),
+                         reinterpret_cast<const int2*>(ws + t.trsm_tiles), t.n_tiles_t, b->max_kp,
+                         s));
   RLU_TRY(launch_lu_reg_batched(true, b->opt.lu_rows_per_cta,
                                 reinterpret_cast<const LuArgs*>(ws + t.lu_b), b->first_b,
                                 b->count_b, s));
   RLU_TRY(gather_batched(reinterpret_cast<const GatherJob*>(ws + t.gather), c, b->max_k,
                          b->max_n, s));
-  RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_l), c,
-                                           b->max_m, b->max_k, false, true, false, s,
-                                           b->opt.gemm_tile_l)));
+  if (t.small_k)
+    RLU_TRY(lmul_batched(reinterpret_cast<const GemmArgs*>(ws + t.gemm_l),
+                         reinterpret_cast<const int2*>(ws + t.lmul_tiles), t.n_tiles_l, s));
+  else
+    RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_l), c,
+                                             b->max_m, b->max_k, false, true, false, s,
+                                             b->opt.gemm_tile_l)));
   return RLU_OK;
 }
 

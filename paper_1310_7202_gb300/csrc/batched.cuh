@@ -3,6 +3,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "gemm_simt.cuh"
 #include "small.cuh"
 
 namespace rlu {
@@ -62,5 +63,13 @@ int32_t trsm_batched(const TrsmJob* jobs_dev, const int2* tiles_dev, int ntiles,
                      cudaStream_t s);
 int32_t gather_batched(const GatherJob* jobs_dev, int count, int max_k, int64_t max_n,
                        cudaStream_t s);
+// k <= 64: the substitution one thread per column over (problem, 128-column block) tiles,
+// grouped by the bucket of k (trsm_small_bucket: 0..3 for k <= 16, 32, 48, 64; tiles of
+// bucket b at first[b] .. first[b] + count[b] - 1, one launch per nonempty bucket), and
+// L = L_y L_b one thread per row over (problem, 256-row block) tiles
+int trsm_small_bucket(int k);
+int32_t trsm_small_batched(const TrsmJob* jobs_dev, const int2* tiles_dev, const int* first,
+                           const int* count, cudaStream_t s);
+int32_t lmul_batched(const GemmArgs* jobs_dev, const int2* tiles_dev, int ntiles, cudaStream_t s);
 
 }  // namespace rlu

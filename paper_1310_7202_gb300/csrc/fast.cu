@@ -245,6 +245,9 @@ __global__ void __launch_bounds__(FFT_T) k_srft_rows(const float* __restrict__ A
 
 static constexpr int CLU_T = 512;
 static constexpr int CLU_TX = 32, CLU_TY = CLU_T / CLU_TX;
+#ifndef RLU_CLU_MIN_ROWS
+#define RLU_CLU_MIN_ROWS 8  // fewest rows per CTA (more rows: fewer CTAs meet at each step)
+#endif
 
 struct CluArgs {
   float2* Y;          // rows x cols, row-major, ld ldy; factored in place (position order)
@@ -254,7 +257,7 @@ struct CluArgs {
   int32_t* perm;      // gather form: position i holds original row perm[i]
   float2* pub_rows;   // [2][G + 1][cols]
   int* pub_idx;       // [2][G + 1]
-  unsigned long long* key;  // [3], zero before the launch
+  unsigned long long* key;  // 3 slots, 128 bytes apart (own cache lines), zero before the launch
   unsigned* bar;      // zero before the launch
   int32_t* status;
   int32_t* first_zero;
@@ -385,13 +388,13 @@ __global__ void __launch_bounds__(CLU_T, 1) k_clu_coop(CluArgs a) {
     const int* pidx = a.pub_idx + (size_t)par * (G + 1);
     if (!clu_wait(a.bar, (unsigned)G * (unsigned)(j + 1), a.status, &s_ok)) return;
     if (tid == 0) {
-      const unsigned long long kv = __ldcg(a.key + j % 3);
+      const unsigned long long kv = __ldcg(a.key + 16 * (j % 3));
       const float mag = __uint_as_float((unsigned)(kv >> 32));
       const int pos = (int)(0xFFFFFFFFu - (unsigned)(kv & 0xFFFFFFFFu));
       const bool valid = kv != 0ull && pos >= j && pos < a.rows;
       s_w = (valid && mag > 0.f) ? pos / a.rloc : -1;  // zero (or no finite) pivot: -1
       s_r = pos;
-      if (b == 0) a.key[(j + 2) % 3] = 0ull;             // the slot of step j + 2
+      if (b == 0) a.key[16 * ((j + 2) % 3)] = 0ull;             // the slot of step j + 2
     }
     __syncthreads();
     const int w = s_w, r = s_r;
@@ -402,7 +405,7 @@ __global__ void __launch_bounds__(CLU_T, 1) k_clu_coop(CluArgs a) {
     if (w < 0) {  // nothing to eliminate: the next step's candidates as they stand
       if (b == 0 && tid == 0 && a.first_zero) atomicCAS(a.first_zero, -1, j);
       if (!last) {
-        clu_candidate<CROUT>(tile, cols, nloc, base, j + 1, &s_cpos, a.key + (j + 1) % 3);
+        clu_candidate<CROUT>(tile, cols, nloc, base, j + 1, &s_cpos, a.key + 16 * ((j + 1) % 3));
         __syncthreads();
         clu_publish(tile, idx, cols, nloc, base, j + 1, s_cpos, b, G, prown, pidxn);
         clu_arrive(a.bar);
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(CLU_T, 1) k_clu_coop(CluArgs a) {
     __syncthreads();
     int ca = -1, cb = -1;  // local rows updated ahead of the others
     if (!last) {
-      clu_candidate<CROUT>(tile, cols, nloc, base, j + 1, &s_cpos, a.key + (j + 1) % 3);
+      clu_candidate<CROUT>(tile, cols, nloc, base, j + 1, &s_cpos, a.key + 16 * ((j + 1) % 3));
       __syncthreads();
       const int cpos = s_cpos;
       ca = cpos != INT_MAX ? cpos - base : -1;
@@ -481,8 +484,9 @@ static size_t clu_smem_bytes(int rloc, int cols) {
 }
 
 // Workspace of the barrier, the keys and the published rows for up to G CTAs.
+static constexpr int CLU_HDR = 512;  // barrier counter and three key slots, a line each
 static size_t clu_pub_bytes(int G, int cols) {
-  return 256 + 2 * (size_t)(G + 1) * cols * sizeof(float2) + 2 * (size_t)(G + 1) * sizeof(int);
+  return CLU_HDR + 2 * (size_t)(G + 1) * cols * sizeof(float2) + 2 * (size_t)(G + 1) * sizeof(int);
 }
 
 // CTAs and rows per CTA for a rows x cols LU; false when the rows do not fit.
@@ -492,7 +496,7 @@ static bool clu_shape(int rows, int cols, int* G, int* rloc) {
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
   if (rows < 1) return false;
-  int g = (int)ceil_div(rows, 8);
+  int g = (int)ceil_div(rows, RLU_CLU_MIN_ROWS);
   if (g > sm_count()) g = sm_count();
   if (g < 1) g = 1;
   const int r = (int)ceil_div(rows, g);
@@ -516,8 +520,8 @@ static int32_t clu_coop(bool crout, float2* Y, int64_t ldy, int rows, int cols, 
   a.rloc = rloc;
   a.perm = perm;
   a.bar = reinterpret_cast<unsigned*>(p);                      // header: barrier, 3 keys
-  a.key = reinterpret_cast<unsigned long long*>(p + 64);
-  p += 256;
+  a.key = reinterpret_cast<unsigned long long*>(p + 128);
+  p += CLU_HDR;
   a.pub_rows = reinterpret_cast<float2*>(p);
   p += 2 * (size_t)(G + 1) * cols * sizeof(float2);
   a.pub_idx = reinterpret_cast<int*>(p);
@@ -530,7 +534,7 @@ static int32_t clu_coop(bool crout, float2* Y, int64_t ldy, int rows, int cols, 
   int per_sm = 0;
   RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, CLU_T, smem));
   if (per_sm * sm_count() < G) return RLU_EUNSUPPORTED;
-  RLU_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 256, s));
+  RLU_CUDA_TRY(cudaMemsetAsync(a.bar, 0, CLU_HDR, s));
   void* args[] = {&a};
   RLU_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(CLU_T), args, smem, s));
   return last_launch_status();

@@ -1153,6 +1153,144 @@ int32_t ldl32_batched(const Ldl32Job* jobs_dev, int count, int max_k, cudaStream
   return last_launch_status();
 }
 
+// Batched form for k <= 64: one thread per column of C over a tile list of (problem,
+// 128-column block) entries. L (unit lower, from LR) sits in shared memory, zero-padded to
+// the problem's bucket KB in {16, 32, 48, 64} (padded rows and columns change nothing), and
+// the column in registers: forward substitution x_i -= sum_{j<i} L[i][j] x_j, scaling by
+// 1/D, backward substitution x_i -= sum_{j>i} L[j][i] x_j. The bucket is chosen per CTA from
+// its problem's k, so small problems do not pay for the largest k of the batch.
+static constexpr int TS_KMAX = 64;
+static constexpr int TS_LD = TS_KMAX + 4;  // 16-byte rows
+static constexpr int TS_COLS = 128;
+
+template <int KB>
+__device__ __forceinline__ void trsm_small_body(const float (*Ls)[TS_LD], const float* dv,
+                                                const float* __restrict__ C, int64_t ldc,
+                                                float* __restrict__ B, int64_t ldb, int k,
+                                                int64_t c) {
+  float x[KB];
+#pragma unroll
+  for (int i = 0; i < KB; ++i) x[i] = i < k ? C[(int64_t)i * ldc + c] : 0.f;
+#pragma unroll
+  for (int i = 1; i < KB; ++i) {
+    if (i < k) {
+      float acc = x[i];
+#pragma unroll
+      for (int j = 0; j < i; ++j) acc = fmaf(-Ls[i][j], x[j], acc);
+      x[i] = acc;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < KB; ++i) x[i] *= dv[i];
+#pragma unroll
+  for (int i = KB - 2; i >= 0; --i) {
+    if (i < k - 1) {
+      float acc = x[i];
+#pragma unroll
+      for (int j = i + 1; j < KB; ++j)
+        if (j < k) acc = fmaf(-Ls[j][i], x[j], acc);
+      x[i] = acc;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < KB; ++i)
+    if (i < k) B[(int64_t)i * ldb + c] = x[i];
+}
+
+template <int KB>
+__global__ void __launch_bounds__(TS_COLS) k_trsm_small_batched(const TrsmJob* __restrict__ jobs,
+                                                                const int2* __restrict__ tiles) {
+  __shared__ __align__(16) float Ls[TS_KMAX][TS_LD];
+  __shared__ float dv[TS_KMAX];
+  const int2 t = tiles[blockIdx.x];
+  const TrsmJob& jb = jobs[t.x];
+  const int k = jb.o.k, kp = jb.o.kp;
+  for (int e = threadIdx.x; e < KB * KB; e += TS_COLS) {
+    const int i = e / KB, j = e % KB;
+    Ls[i][j] = (i < k && j < k) ? jb.o.LR[(int64_t)i * kp + j] : 0.f;
+  }
+  for (int i = threadIdx.x; i < KB; i += TS_COLS) dv[i] = i < k ? (float)jb.o.dinv[i] : 0.f;
+  __syncthreads();
+  const int64_t c = (int64_t)t.y * TS_COLS + threadIdx.x;
+  if (c >= jb.n) return;
+  trsm_small_body<KB>(Ls, dv, jb.C, jb.ldc, jb.B, jb.ldb, k, c);
+}
+
+int trsm_small_bucket(int k) { return k <= 16 ? 0 : k <= 32 ? 1 : k <= 48 ? 2 : 3; }
+
+int32_t trsm_small_batched(const TrsmJob* jobs_dev, const int2* tiles_dev, const int* first,
+                           const int* count, cudaStream_t s) {
+  int launches = 0;
+  for (int bkt = 0; bkt < 4; ++bkt) {
+    if (count[bkt] <= 0) continue;
+    const int2* tl = tiles_dev + first[bkt];
+    const unsigned g = (unsigned)count[bkt];
+    if (bkt == 0) k_trsm_small_batched<16><<<g, TS_COLS, 0, s>>>(jobs_dev, tl);
+    else if (bkt == 1) k_trsm_small_batched<32><<<g, TS_COLS, 0, s>>>(jobs_dev, tl);
+    else if (bkt == 2) k_trsm_small_batched<48><<<g, TS_COLS, 0, s>>>(jobs_dev, tl);
+    else k_trsm_small_batched<64><<<g, TS_COLS, 0, s>>>(jobs_dev, tl);
+    ++launches;
+  }
+  return launches ? last_launch_status(launches) : RLU_OK;
+}
+
+// L (m x k, column-major) = L_y (m x k, column-major, pivot order) L_b (k x k, column-major,
+// unit lower) for k <= 64: one thread per row over a tile list of (problem, 256-row block)
+// entries, L_b (zero-padded to the problem's bucket KB) in shared memory, the row of L_y in
+// registers.
+static constexpr int LM_ROWS = 256;
+
+template <int KB>
+__device__ __forceinline__ void lmul_body(const float* Lbs, const float* __restrict__ Ly,
+                                          int64_t lda, float* __restrict__ L, int64_t ldc,
+                                          int k, int64_t i) {
+  float y[KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) y[c] = c < k ? Ly[(int64_t)c * lda + i] : 0.f;
+  for (int j = 0; j < k; ++j) {
+    const float* bcol = Lbs + j * TS_LD;  // column j of L_b
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < KB; c += 4) {
+      const float4 b4 = *reinterpret_cast<const float4*>(bcol + c);
+      acc = fmaf(y[c], b4.x, acc);
+      acc = fmaf(y[c + 1], b4.y, acc);
+      acc = fmaf(y[c + 2], b4.z, acc);
+      acc = fmaf(y[c + 3], b4.w, acc);
+    }
+    L[(int64_t)j * ldc + i] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(LM_ROWS) k_lmul_batched(const GemmArgs* __restrict__ jobs,
+                                                          const int2* __restrict__ tiles) {
+  __shared__ __align__(16) float Lbs[TS_KMAX * TS_LD];
+  const int2 t = tiles[blockIdx.x];
+  const GemmArgs& g = jobs[t.x];
+  const int k = (int)g.N;
+  const int kb = k <= 16 ? 16 : k <= 32 ? 32 : k <= 48 ? 48 : 64;
+  const float* Lb = static_cast<const float*>(g.B);
+  for (int e = threadIdx.x; e < k * kb; e += LM_ROWS) {
+    const int j = e / kb, c = e % kb;  // column j, entry c
+    Lbs[j * TS_LD + c] = c < k ? Lb[(int64_t)j * g.ldb + c] : 0.f;
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)t.y * LM_ROWS + threadIdx.x;
+  if (i >= g.M) return;
+  const float* Ly = static_cast<const float*>(g.A);
+  float* L = static_cast<float*>(g.C);
+  if (kb == 16) lmul_body<16>(Lbs, Ly, g.lda, L, g.ldc, k, i);
+  else if (kb == 32) lmul_body<32>(Lbs, Ly, g.lda, L, g.ldc, k, i);
+  else if (kb == 48) lmul_body<48>(Lbs, Ly, g.lda, L, g.ldc, k, i);
+  else lmul_body<64>(Lbs, Ly, g.lda, L, g.ldc, k, i);
+}
+
+int32_t lmul_batched(const GemmArgs* jobs_dev, const int2* tiles_dev, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return RLU_OK;
+  k_lmul_batched<<<(unsigned)ntiles, LM_ROWS, 0, s>>>(jobs_dev, tiles_dev);
+  return last_launch_status();
+}
+
 int32_t trsm_batched(const TrsmJob* jobs_dev, const int2* tiles_dev, int ntiles, int max_kp,
                      cudaStream_t s) {
   if (ntiles <= 0) return RLU_OK;

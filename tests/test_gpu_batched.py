@@ -127,6 +127,32 @@ def test_batched_kernel_choices_keep_results(prec, options):
         assert fro_g <= 1.1 * fro_o + 1e-4 * sigma[0], (m, n, k, options)
 
 
+@pytest.mark.parametrize("prec", ["f32", "mixed"])
+def test_batched_rank_above_64_takes_the_blocked_kernels(prec):
+    """A batch with one problem of k = 66 (l = 76, the register panel's width) runs the
+    blocked substitution and the SIMT product for L instead of the k <= 64 register kernels;
+    every problem still holds the oracle tolerance."""
+    shapes = [(300, 200, 66, 76), (150, 120, 20, 30), (700, 500, 40, 50)]
+    probs, mats = [], []
+    for i, (m, n, k, l) in enumerate(shapes):
+        sigma = np.exp(-np.arange(1, min(m, n) + 1) / k)
+        A = synth.prescribed_matrix(m, n, sigma, 500 + i, 600 + i, dtype=np.float32)
+        mats.append((A, sigma))
+        probs.append({"A": _padded(A), "k": k, "l": l, "seed": 90 + i})
+    b = rlu.Batch(probs, prec)
+    b.run()
+    torch.cuda.synchronize()
+    for (m, n, k, l), (A, sigma), p, o in zip(shapes, mats, probs, b.outs):
+        G = O.gaussian_f32(p["seed"], 0, n, l).astype(np.float64)
+        orc = O.rlu_factor(A.astype(np.float64), k, l, seed=p["seed"], G=G)
+        fro_o, _ = O.reconstruct_error(A, orc["P"], orc["Q"], orc["L"], orc["U"],
+                                       spectral=False)
+        fro_g, _ = O.reconstruct_error(A, *(o[x].cpu().numpy() for x in ("P", "Q", "L", "U")),
+                                       spectral=False)
+        assert fro_g <= 1.1 * fro_o + 1e-4 * sigma[0], (m, n, k, prec)
+        assert o["info"].tolist()[:3] == [0, -1, -1]
+
+
 def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     from paper_1310_7202_gb300 import autotune
     monkeypatch.setenv("RLU_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
