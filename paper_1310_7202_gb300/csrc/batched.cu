@@ -461,9 +461,11 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
                                 b->count_y, s));
   RLU_TRY(build_ly_batched(reinterpret_cast<const BuildJob*>(ws + t.build), c, b->max_m,
                            b->max_k, s));
-  // the Gram is k x k with k <= 64: one 64 x 64 tile per problem
-  RLU_TRY((gemm_simt_batched<float, double>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_g), c,
-                                            b->max_k, b->max_k, true, true, true, s, 1)));
+  if (t.small_k)  // the Gram is k x k with k <= 64: one CTA per problem
+    RLU_TRY(gram_small_batched(reinterpret_cast<const GemmArgs*>(ws + t.gemm_g), c, s));
+  else
+    RLU_TRY((gemm_simt_batched<float, double>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_g),
+                                              c, b->max_k, b->max_k, true, true, true, s, 1)));
   RLU_TRY(ldl32_batched(reinterpret_cast<const Ldl32Job*>(ws + t.ldl), c, b->max_k, s));
   if (b->prec == RLU_PREC_MIXED)
     RLU_TRY(umma3_batched(U3_MODE_C3, reinterpret_cast<const U3Job*>(ws + t.u3c),

@@ -71,5 +71,7 @@ int trsm_small_bucket(int k);
 int32_t trsm_small_batched(const TrsmJob* jobs_dev, const int2* tiles_dev, const int* first,
                            const int* count, cudaStream_t s);
 int32_t lmul_batched(const GemmArgs* jobs_dev, const int2* tiles_dev, int ntiles, cudaStream_t s);
+// k <= 64: the Gram M = L~^T L~ (FP64 out, FP32 accumulation), one CTA per problem
+int32_t gram_small_batched(const GemmArgs* jobs_dev, int count, cudaStream_t s);
 
 }  // namespace rlu

@@ -1112,18 +1112,31 @@ int32_t info_init(rlu_info* info, cudaStream_t s) {
 // ---- batched launchers --------------------------------------------------------------------
 // CTA (problem blockIdx.x, column group blockIdx.y): columns c = y, y + gridDim.y, ... of
 // L_y / L~ (m rows each) in a loop, so that the grid holds no CTAs for the rows small
-// problems do not have.
+// problems do not have. The CTA first inverts the permutation in shared memory
+// (pinv[perm[p]] = p), so that it walks the rows of L~ = P^T L_y (and of Y and the TF32
+// split) in order: only the writes of L_y in pivot order are scattered.
 __global__ void k_build_ly_batched(const BuildJob* __restrict__ jobs) {
+  extern __shared__ int bl_pinv[];  // [m]
   const BuildJob& j = jobs[blockIdx.x];
   const int64_t m = j.m;
   const int k = j.k;
+  // entries outside [0, m) (an LU that stopped early) leave -1 and are skipped
+  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) bl_pinv[r] = -1;
+  __syncthreads();
+  for (int64_t p = threadIdx.x; p < m; p += blockDim.x) {
+    const int q = j.perm[p];
+    if (q >= 0 && q < m) bl_pinv[q] = (int)p;
+  }
+  __syncthreads();
   for (int c = blockIdx.y; c < k; c += gridDim.y) {
-    for (int64_t p = threadIdx.x; p < m; p += blockDim.x) {
-      const int64_t r = j.perm[p];
+#pragma unroll 4
+    for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
+      const int p = bl_pinv[r];
+      if (p < 0) continue;
       const float v = (c < p) ? j.Y[(int64_t)c * j.ldy + r] : (c == p ? 1.f : 0.f);
-      j.Lp[(int64_t)c * j.ldl + p] = v;
       j.Lt[(int64_t)c * j.ldl + r] = v;
       if (j.Lhi) tf32_split(v, j.Lhi, j.Llo, (int64_t)c * j.ldl + r);
+      j.Lp[(int64_t)c * j.ldl + p] = v;
     }
   }
 }
@@ -1131,9 +1144,75 @@ __global__ void k_build_ly_batched(const BuildJob* __restrict__ jobs) {
 int32_t build_ly_batched(const BuildJob* jobs_dev, int count, int64_t max_m, int max_k,
                          cudaStream_t s) {
   if (count <= 0) return RLU_OK;
-  (void)max_m;
   (void)max_k;
-  k_build_ly_batched<<<dim3((unsigned)count, 8), 256, 0, s>>>(jobs_dev);
+  const size_t smem = (size_t)max_m * sizeof(int);
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_build_ly_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  k_build_ly_batched<<<dim3((unsigned)count, 8), 256, smem, s>>>(jobs_dev);
+  return last_launch_status();
+}
+
+// Gram M = L~^T L~ (k x k, FP64 out, FP32 accumulation) for k <= 64: one CTA per problem;
+// thread t holds the 4 x 4 block (4 (t / 16), 4 (t % 16)) of M; 32-row chunks of L~ are
+// staged row-major in shared memory.
+static constexpr int GS_CHUNK = 32;
+static constexpr int GS_KMAX = 64;
+__global__ void __launch_bounds__(256) k_gram_small_batched(const GemmArgs* __restrict__ jobs) {
+  __shared__ __align__(16) float S[GS_CHUNK][GS_KMAX + 4];
+  const GemmArgs& g = jobs[blockIdx.x];
+  const int k = (int)g.N;
+  const int64_t m = g.K;
+  const float* Lt = static_cast<const float*>(g.A);
+  const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;
+  const bool active = 4 * ti < k && 4 * tj < k;
+  float acc[4][4] = {};
+  constexpr int PER = GS_CHUNK * GS_KMAX / 256;  // staged values per thread and chunk
+  float nxt[PER];                                // the next chunk, loaded ahead
+  auto load_chunk = [&](int64_t r0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      const int c = e / GS_CHUNK, rr = e % GS_CHUNK;  // column c, row r0 + rr (coalesced in rr)
+      nxt[u] = (c < k && r0 + rr < m) ? Lt[(int64_t)c * g.lda + r0 + rr] : 0.f;
+    }
+  };
+  load_chunk(0);
+  for (int64_t r0 = 0; r0 < m; r0 += GS_CHUNK) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      S[e % GS_CHUNK][e / GS_CHUNK] = nxt[u];
+    }
+    __syncthreads();
+    if (r0 + GS_CHUNK < m) load_chunk(r0 + GS_CHUNK);
+    if (active) {
+#pragma unroll 8
+      for (int rr = 0; rr < GS_CHUNK; ++rr) {
+        const float4 a = *reinterpret_cast<const float4*>(&S[rr][4 * ti]);
+        const float4 b = *reinterpret_cast<const float4*>(&S[rr][4 * tj]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+      }
+    }
+  }
+  if (!active) return;
+  double* M = static_cast<double*>(g.C);
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int i = 4 * ti + x, jj = 4 * tj + y;
+      if (i < k && jj < k) M[(int64_t)i * g.ldc + jj] = (double)acc[x][y];
+    }
+}
+
+int32_t gram_small_batched(const GemmArgs* jobs_dev, int count, cudaStream_t s) {
+  if (count <= 0) return RLU_OK;
+  k_gram_small_batched<<<(unsigned)count, 256, 0, s>>>(jobs_dev);
   return last_launch_status();
 }
 
@@ -1312,6 +1391,7 @@ __global__ void k_gather_batched(const GatherJob* __restrict__ jobs) {
   const int k = j.k;
   const int64_t n = j.n;
   for (int i = 0; i < k; ++i) {
+#pragma unroll 4
     for (int64_t c = threadIdx.x; c < n; c += blockDim.x)
       j.U[(int64_t)i * j.ldu + c] = c >= i ? j.B[(int64_t)i * j.ldb + j.Q[c]] : 0.f;
     // L_b column i: rows r > i from B's row r at the pivot column Q[i]
