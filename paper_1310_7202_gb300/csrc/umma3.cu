@@ -333,14 +333,243 @@ k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtenso
   umma3_tile<MODE>(mA0, mA1, mB0, mB1, a, mt, blockIdx.y, nt);
 }
 
-// Batched form: problem blockIdx.y (one N tile, no split), 128-row tile blockIdx.x; CTAs past
-// the problem's rows return before any allocation.
+// Persistent batched form (Y2 and C3, every BN <= 128): CTA b takes the tiles b, b + G,
+// b + 2G, ... of the tile list. Setup (barriers, TMEM) happens once; the producer, the
+// converter and the MMA issuer run one ring of k-steps across the CTA's tiles, so a tile's
+// first loads are in flight while the previous tile drains; the accumulator is double
+// buffered in TMEM (columns 0 and 128), so the epilogue of one tile overlaps the MMAs of the
+// next. Ring slots are slot bytes apart (the largest slot of the batch). Every wait is
+// bounded: a wait that gives up sets RLU_ETIMEOUT in the tile's status and ends the role.
+struct U3PSmem {
+  uint64_t full[U3_MAXST];
+  uint64_t conv[U3_MAXST];
+  uint64_t empty[U3_MAXST];
+  uint64_t accf[2];  // accumulator buffer b complete (MMA commit)
+  uint64_t acce[2];  // accumulator buffer b read (4 epilogue warps)
+  uint32_t tmem_base;
+  int32_t err;
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_batched(const U3Job* __restrict__ jobs,
-                                                                 const int2* __restrict__ tiles) {
-  const int2 t = tiles[blockIdx.x];  // (problem, 128-row tile): only tiles that exist
-  const U3Job& j = jobs[t.x];
-  umma3_tile<MODE>(j.map[0], j.map[1], j.map[2], j.map[3], j.a, t.y, 0, 0);
+__global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __restrict__ jobs,
+                                                                 const int2* __restrict__ tiles,
+                                                                 int ntiles, int S,
+                                                                 uint32_t slot) {
+  using namespace u3;
+  extern __shared__ __align__(1024) unsigned char u3_smem[];
+  U3PSmem& sh = *reinterpret_cast<U3PSmem*>(u3_smem);
+  const uint32_t ring = (su32(u3_smem) + sizeof(U3PSmem) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < S; ++st) {
+      mb_init(su32(&sh.full[st]), 1);
+      mb_init(su32(&sh.conv[st]), 128);
+      mb_init(su32(&sh.empty[st]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mb_init(su32(&sh.accf[b]), 1);
+      mb_init(su32(&sh.acce[b]), 4);
+    }
+    sh.err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n"
+                 ::"r"(su32(&sh.tmem_base)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = sh.tmem_base;
+  volatile int32_t* err = &sh.err;
+  auto fail = [&](const Umma3Args& a) {
+    *err = 1;
+    if (a.status) atomicExch(a.status, RLU_ETIMEOUT);
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ------------------------------------------------------------------
+    uint32_t g = 0;
+    for (int ti = blockIdx.x; ti < ntiles && !*err; ti += gridDim.x) {
+      const int2 t = tiles[ti];
+      const U3Job& j = jobs[t.x];
+      const Umma3Args& a = j.a;
+      const U3Layout lay = u3_layout(MODE, a.BN);
+      const uint32_t tx = MODE == U3_MODE_Y2 ? U3_BM * 128 + (uint32_t)a.BN * 128
+                                             : U3_BM * 128 + 2 * (uint32_t)a.BN * 128;
+      const int m0 = t.y * U3_BM;
+      const int nk = (a.K + U3_BK - 1) / U3_BK;
+      for (int kt = 0; kt < nk; ++kt, ++g) {
+        const uint32_t st = g % (uint32_t)S;
+        if (g >= (uint32_t)S && !mb_wait(su32(&sh.empty[st]), ((g / S) - 1) & 1)) {
+          fail(a);
+          break;
+        }
+        const uint32_t base = ring + st * slot;
+        const uint32_t bar = su32(&sh.full[st]);
+        mb_expect_tx(bar, tx);
+        const int kx = kt * U3_BK;
+        if (MODE == U3_MODE_Y2) {
+          tma2d(base + lay.a0, &j.map[0], kx, m0, bar);
+          tma2d(base + lay.b0, &j.map[2], kx, 0, bar);
+        } else {
+          tma2d(base + lay.a2, &j.map[0], m0, kx, bar);  // raw A: x = n (128 wide), y = m
+          tma2d(base + lay.b0, &j.map[2], kx, 0, bar);
+          tma2d(base + lay.b1, &j.map[3], kx, 0, bar);
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer --------------------------------------------------------------------
+    uint32_t g = 0;
+    int it = 0;
+    for (int ti = blockIdx.x; ti < ntiles && !*err; ti += gridDim.x, ++it) {
+      const int2 t = tiles[ti];
+      const Umma3Args& a = jobs[t.x].a;
+      const U3Layout lay = u3_layout(MODE, a.BN);
+      const int buf = it & 1;
+      if (it >= 2 && !mb_wait(su32(&sh.acce[buf]), (uint32_t)(((it / 2) - 1) & 1))) {
+        fail(a);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t idesc = u3_idesc(U3_BM, a.BN);
+      const uint32_t acc = tmem + (uint32_t)(buf * 128);
+      const int nk = (a.K + U3_BK - 1) / U3_BK;
+      bool ok = true;
+      for (int kt = 0; kt < nk; ++kt, ++g) {
+        const uint32_t st = g % (uint32_t)S;
+        if (!mb_wait(su32(&sh.conv[st]), (g / S) & 1)) {
+          fail(a);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t base = ring + st * slot;
+#pragma unroll
+        for (int kk = 0; kk < U3_BK / 8; ++kk) {
+          const uint32_t off = kk * 32;
+          const uint64_t ah = desc_sw128(base + lay.a0 + off), al = desc_sw128(base + lay.a1 + off);
+          const uint64_t bh = desc_sw128(base + lay.b0 + off), bl = desc_sw128(base + lay.b1 + off);
+          mma_tf32(acc, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(acc, al, bh, idesc, 1u);
+          if (MODE != U3_MODE_Y2) mma_tf32(acc, ah, bl, idesc, 1u);
+        }
+        commit(su32(&sh.empty[st]));
+      }
+      if (!ok) break;
+      commit(su32(&sh.accf[buf]));
+    }
+  } else if (warp >= 2 && warp < 6) {
+    // ---- epilogue ------------------------------------------------------------------------
+    const int quarter = warp & 3;
+    int it = 0;
+    for (int ti = blockIdx.x; ti < ntiles && !*err; ti += gridDim.x, ++it) {
+      const int2 t = tiles[ti];
+      const Umma3Args& a = jobs[t.x].a;
+      const int buf = it & 1;
+      if (!mb_wait(su32(&sh.accf[buf]), (uint32_t)((it / 2) & 1))) {
+        fail(a);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int row = t.y * U3_BM + quarter * 32 + lane;
+      for (int c0 = 0; c0 < a.BN; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr =
+            tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+            "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+            "%28, %29, %30, %31}, [%32];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+              "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+              "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+              "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (row < a.M) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const int col = c0 + jj;
+            if (col < a.N) {
+              const float f = __uint_as_float(v[jj]);
+              if (a.out_colmajor)
+                a.out[(size_t)col * a.ldo + row] = f;
+              else
+                a.out[(size_t)row * a.ldo + col] = f;
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mb_arrive(su32(&sh.acce[buf]));
+    }
+  } else if (warp >= 6) {
+    // ---- converter: one thread per tile row (128 rows) ------------------------------------
+    const int r = threadIdx.x - 192;  // 0..127
+    uint32_t g = 0;
+    for (int ti = blockIdx.x; ti < ntiles && !*err; ti += gridDim.x) {
+      const int2 t = tiles[ti];
+      const Umma3Args& a = jobs[t.x].a;
+      const U3Layout lay = u3_layout(MODE, a.BN);
+      const int nk = (a.K + U3_BK - 1) / U3_BK;
+      bool ok = true;
+      for (int kt = 0; kt < nk; ++kt, ++g) {
+        const uint32_t st = g % (uint32_t)S;
+        if (!mb_wait(su32(&sh.full[st]), (g / S) & 1)) {
+          fail(a);
+          ok = false;
+          break;
+        }
+        const uint32_t base = ring + st * slot;
+        if (MODE == U3_MODE_Y2) {
+          float* hi = reinterpret_cast<float*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 32;
+          float* lo = reinterpret_cast<float*>(u3_smem + (base + lay.a1 - su32(u3_smem))) + r * 32;
+#pragma unroll
+          for (int c0 = 0; c0 < 8; ++c0) {
+            const int c = (c0 + r) & 7;
+            float4 v = *reinterpret_cast<float4*>(hi + 4 * c);
+            float4 h, l;
+            split_tf32(v.x, h.x, l.x);
+            split_tf32(v.y, h.y, l.y);
+            split_tf32(v.z, h.z, l.z);
+            split_tf32(v.w, h.w, l.w);
+            *reinterpret_cast<float4*>(hi + 4 * c) = h;
+            *reinterpret_cast<float4*>(lo + 4 * c) = l;
+          }
+        } else {
+          const float* raw = reinterpret_cast<const float*>(u3_smem + (base + lay.a2 - su32(u3_smem)));
+          float* hi = reinterpret_cast<float*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 32;
+          float* lo = reinterpret_cast<float*>(u3_smem + (base + lay.a1 - su32(u3_smem))) + r * 32;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            float4 h, l;
+            split_tf32(raw[(4 * c + 0) * U3_BM + r], h.x, l.x);
+            split_tf32(raw[(4 * c + 1) * U3_BM + r], h.y, l.y);
+            split_tf32(raw[(4 * c + 2) * U3_BM + r], h.z, l.z);
+            split_tf32(raw[(4 * c + 3) * U3_BM + r], h.w, l.w);
+            const int pc = c ^ (r & 7);
+            *reinterpret_cast<float4*>(hi + 4 * pc) = h;
+            *reinterpret_cast<float4*>(lo + 4 * pc) = l;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mb_arrive(su32(&sh.conv[st]));
+      }
+      if (!ok) break;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -505,19 +734,20 @@ int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, in
   if (ntiles <= 0) return RLU_OK;
   if (stages < 2) return RLU_EINVAL;
   const size_t smem = 2048 + (size_t)stages * max_stage_bytes;
-  const dim3 grid((unsigned)ntiles);
-  if (mode == U3_MODE_Y2) {
-    RLU_CUDA_TRY(cudaFuncSetAttribute(k_umma3_batched<U3_MODE_Y2>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_umma3_batched<U3_MODE_Y2><<<grid, U3_THREADS, smem, s>>>(jobs_dev, tiles_dev);
-  } else if (mode == U3_MODE_C3) {
-    RLU_CUDA_TRY(cudaFuncSetAttribute(k_umma3_batched<U3_MODE_C3>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_umma3_batched<U3_MODE_C3><<<grid, U3_THREADS, smem, s>>>(jobs_dev, tiles_dev);
-  } else {
-    return RLU_EINVAL;
-  }
-  return last_launch_status();
+  // persistent: as many CTAs as stay resident (one or two per SM), each walking the list
+  auto go = [&](auto kern) -> int32_t {
+    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, U3_THREADS, smem));
+    if (per_sm < 1) return RLU_EUNSUPPORTED;
+    const int grid = std::min(ntiles, per_sm * sm_count());
+    kern<<<(unsigned)grid, U3_THREADS, smem, s>>>(jobs_dev, tiles_dev, ntiles, stages,
+                                                  (uint32_t)max_stage_bytes);
+    return last_launch_status();
+  };
+  if (mode == U3_MODE_Y2) return go(k_umma3_persist<U3_MODE_Y2>);
+  if (mode == U3_MODE_C3) return go(k_umma3_persist<U3_MODE_C3>);
+  return RLU_EINVAL;
 }
 
 int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s) {
