@@ -42,7 +42,7 @@ struct ProblemLayout {
 
 struct Tables {
   size_t info, gauss, gemm_y, lu_y, build, gemm_g, ldl, gemm_c, trsm, lu_b, gather, gemm_l,
-      u3y, u3c, u3y_tiles, u3c_tiles, trsm_tiles, lmul_tiles;
+      u3y, u3c, u3y_tiles, u3c_tiles, trsm_tiles, lmul_tiles, u3_counter;
   int n_tiles_y, n_tiles_c;  // 128-row tiles of the two tensor-core products
   int n_tiles_t;             // column blocks of the substitution B = M^{-1} C
   int n_tiles_l;             // 256-row blocks of L = L_y L_b (small k only)
@@ -113,6 +113,7 @@ size_t plan_layout(const rlu_problem* probs, int count, int32_t prec, Tables& t,
     }
     t.u3y_tiles = carve(cur, (size_t)t.n_tiles_y * sizeof(int2));
     t.u3c_tiles = carve(cur, (size_t)t.n_tiles_c * sizeof(int2));
+    t.u3_counter = carve(cur, 256);  // tile counter of the persistent products
   }
   for (int i = 0; i < count; ++i) {
     const rlu_problem& p = probs[i];
@@ -451,7 +452,8 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
   if (b->prec == RLU_PREC_MIXED)
     RLU_TRY(umma3_batched(U3_MODE_Y2, reinterpret_cast<const U3Job*>(ws + t.u3y),
                           reinterpret_cast<const int2*>(ws + t.u3y_tiles), t.n_tiles_y,
-                          b->u3y_stages, b->u3y_stage_bytes, s));
+                          b->u3y_stages, b->u3y_stage_bytes,
+                          reinterpret_cast<unsigned*>(ws + t.u3_counter), s));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_y),
                                              c, b->max_m, b->max_l, true, true, false, s,
@@ -470,7 +472,8 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
   if (b->prec == RLU_PREC_MIXED)
     RLU_TRY(umma3_batched(U3_MODE_C3, reinterpret_cast<const U3Job*>(ws + t.u3c),
                           reinterpret_cast<const int2*>(ws + t.u3c_tiles), t.n_tiles_c,
-                          b->u3c_stages, b->u3c_stage_bytes, s));
+                          b->u3c_stages, b->u3c_stage_bytes,
+                          reinterpret_cast<unsigned*>(ws + t.u3_counter), s));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_c),
                                              c, b->max_k, b->max_n, true, false, true, s,

@@ -56,10 +56,11 @@ int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes
 // CTAs share an SM's shared memory (each CTA holds 256 of an SM's 512 TMEM columns).
 int32_t umma3_stages_for(int stage_bytes, int ctas_per_sm = 1);
 // One launch over a tile list (device, ntiles entries of (record, 128-row tile)), modes Y2
-// and C3, every record's BN <= 128: persistent CTAs (as many as stay resident) walk the
-// list with one ring of k-steps across their tiles and a double-buffered TMEM accumulator.
+// and C3, every record's BN <= 128: persistent CTAs (as many as stay resident) take tiles
+// from the list through counter (device, zeroed on s before the launch) and run one ring of
+// k-steps across their tiles with a double-buffered TMEM accumulator.
 int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, int ntiles,
-                      int stages, int max_stage_bytes, cudaStream_t s);
+                      int stages, int max_stage_bytes, unsigned* counter, cudaStream_t s);
 
 // BF16 products (see umma_bf16.cu), same output conventions as Umma3Op.
 // Y : A (M x K row-major BF16, lda), B0 = G^T (N x K row-major BF16, ldb), one product.

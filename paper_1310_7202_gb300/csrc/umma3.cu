@@ -333,19 +333,27 @@ k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtenso
   umma3_tile<MODE>(mA0, mA1, mB0, mB1, a, mt, blockIdx.y, nt);
 }
 
-// Persistent batched form (Y2 and C3, every BN <= 128): CTA b takes the tiles b, b + G,
-// b + 2G, ... of the tile list. Setup (barriers, TMEM) happens once; the producer, the
-// converter and the MMA issuer run one ring of k-steps across the CTA's tiles, so a tile's
-// first loads are in flight while the previous tile drains; the accumulator is double
-// buffered in TMEM (columns 0 and 128), so the epilogue of one tile overlaps the MMAs of the
-// next. Ring slots are slot bytes apart (the largest slot of the batch). Every wait is
-// bounded: a wait that gives up sets RLU_ETIMEOUT in the tile's status and ends the role.
+// Persistent batched form (Y2 and C3, every BN <= 128). The producer thread takes the next
+// tile of the list from a global counter (dynamic: CTAs that finish early take more, and
+// neighbouring tiles of one problem start at about the same time, so the operand they
+// share is read from L2) and passes its index to the other roles through a small queue in
+// shared memory. Setup (barriers, TMEM) happens once; the producer, the converter and the
+// MMA issuer run one ring of k-steps across the CTA's tiles, so a tile's first loads are in
+// flight while the previous tile drains; the accumulator is double buffered in TMEM
+// (columns 0 and 128), so the epilogue of one tile overlaps the MMAs of the next. Ring slots
+// are slot bytes apart (the largest slot of the batch). Every wait is bounded: a wait that
+// gives up sets RLU_ETIMEOUT in the tile's status (or its CTA's first tile's) and ends the
+// role.
+static constexpr int U3_QN = 4;  // tile queue depth
 struct U3PSmem {
   uint64_t full[U3_MAXST];
   uint64_t conv[U3_MAXST];
   uint64_t empty[U3_MAXST];
-  uint64_t accf[2];  // accumulator buffer b complete (MMA commit)
-  uint64_t acce[2];  // accumulator buffer b read (4 epilogue warps)
+  uint64_t accf[2];       // accumulator buffer b complete (MMA commit)
+  uint64_t acce[2];       // accumulator buffer b read (4 epilogue warps)
+  uint64_t qfull[U3_QN];  // queue entry written (producer)
+  uint64_t qempty[U3_QN]; // queue entry read (MMA 1 + converter 4 warps + epilogue 4 warps)
+  int queue[U3_QN];       // tile indices, -1 = no more tiles
   uint32_t tmem_base;
   int32_t err;
 };
@@ -354,7 +362,8 @@ template <int MODE>
 __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __restrict__ jobs,
                                                                  const int2* __restrict__ tiles,
                                                                  int ntiles, int S,
-                                                                 uint32_t slot) {
+                                                                 uint32_t slot,
+                                                                 unsigned* __restrict__ next) {
   using namespace u3;
   extern __shared__ __align__(1024) unsigned char u3_smem[];
   U3PSmem& sh = *reinterpret_cast<U3PSmem*>(u3_smem);
@@ -369,6 +378,10 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
     for (int b = 0; b < 2; ++b) {
       mb_init(su32(&sh.accf[b]), 1);
       mb_init(su32(&sh.acce[b]), 4);
+    }
+    for (int q = 0; q < U3_QN; ++q) {
+      mb_init(su32(&sh.qfull[q]), 1);
+      mb_init(su32(&sh.qempty[q]), 9);
     }
     sh.err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -387,11 +400,33 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
     *err = 1;
     if (a.status) atomicExch(a.status, RLU_ETIMEOUT);
   };
+  const Umma3Args& a_first = jobs[tiles[min((int)blockIdx.x, ntiles - 1)].x].a;
+  // the it-th tile of this CTA from the queue (-1: none left, or a wait gave up); the
+  // reader's arrival frees the entry
+  auto take = [&](int it, int arrivals) -> int {
+    const int q = it % U3_QN;
+    if (!mb_wait(su32(&sh.qfull[q]), (uint32_t)((it / U3_QN) & 1))) {
+      fail(a_first);
+      return -1;
+    }
+    const int ti = *reinterpret_cast<volatile int*>(&sh.queue[q]);
+    if (arrivals) mb_arrive(su32(&sh.qempty[q]));
+    return ti;
+  };
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer ------------------------------------------------------------------
+    // ---- TMA producer and tile scheduler -----------------------------------------------
     uint32_t g = 0;
-    for (int ti = blockIdx.x; ti < ntiles && !*err; ti += gridDim.x) {
+    for (int it = 0; !*err; ++it) {
+      const int q = it % U3_QN;
+      if (it >= U3_QN && !mb_wait(su32(&sh.qempty[q]), (uint32_t)(((it / U3_QN) - 1) & 1))) {
+        fail(a_first);
+        break;
+      }
+      const int ti = (int)atomicAdd(next, 1u);
+      sh.queue[q] = ti < ntiles ? ti : -1;
+      mb_arrive(su32(&sh.qfull[q]));
+      if (ti >= ntiles) break;
       const int2 t = tiles[ti];
       const U3Job& j = jobs[t.x];
       const Umma3Args& a = j.a;
@@ -423,8 +458,9 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer --------------------------------------------------------------------
     uint32_t g = 0;
-    int it = 0;
-    for (int ti = blockIdx.x; ti < ntiles && !*err; ti += gridDim.x, ++it) {
+    for (int it = 0; !*err; ++it) {
+      const int ti = take(it, 1);
+      if (ti < 0) break;
       const int2 t = tiles[ti];
       const Umma3Args& a = jobs[t.x].a;
       const U3Layout lay = u3_layout(MODE, a.BN);
@@ -464,8 +500,11 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
   } else if (warp >= 2 && warp < 6) {
     // ---- epilogue ------------------------------------------------------------------------
     const int quarter = warp & 3;
-    int it = 0;
-    for (int ti = blockIdx.x; ti < ntiles && !*err; ti += gridDim.x, ++it) {
+    for (int it = 0; !*err; ++it) {
+      const int ti = take(it, 0);  // every lane reads; lane 0 frees the entry for the warp
+      __syncwarp();
+      if (lane == 0) mb_arrive(su32(&sh.qempty[it % U3_QN]));
+      if (ti < 0) break;
       const int2 t = tiles[ti];
       const Umma3Args& a = jobs[t.x].a;
       const int buf = it & 1;
@@ -513,7 +552,11 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
     // ---- converter: one thread per tile row (128 rows) ------------------------------------
     const int r = threadIdx.x - 192;  // 0..127
     uint32_t g = 0;
-    for (int ti = blockIdx.x; ti < ntiles && !*err; ti += gridDim.x) {
+    for (int it = 0; !*err; ++it) {
+      const int ti = take(it, 0);
+      __syncwarp();
+      if (lane == 0) mb_arrive(su32(&sh.qempty[it % U3_QN]));
+      if (ti < 0) break;
       const int2 t = tiles[ti];
       const Umma3Args& a = jobs[t.x].a;
       const U3Layout lay = u3_layout(MODE, a.BN);
@@ -730,7 +773,7 @@ int32_t umma3_stages_for(int stage_bytes, int ctas_per_sm) {
 }
 
 int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, int ntiles,
-                      int stages, int max_stage_bytes, cudaStream_t s) {
+                      int stages, int max_stage_bytes, unsigned* counter, cudaStream_t s) {
   if (ntiles <= 0) return RLU_OK;
   if (stages < 2) return RLU_EINVAL;
   const size_t smem = 2048 + (size_t)stages * max_stage_bytes;
@@ -741,8 +784,9 @@ int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, in
     RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, U3_THREADS, smem));
     if (per_sm < 1) return RLU_EUNSUPPORTED;
     const int grid = std::min(ntiles, per_sm * sm_count());
+    RLU_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
     kern<<<(unsigned)grid, U3_THREADS, smem, s>>>(jobs_dev, tiles_dev, ntiles, stages,
-                                                  (uint32_t)max_stage_bytes);
+                                                  (uint32_t)max_stage_bytes, counter);
     return last_launch_status();
   };
   if (mode == U3_MODE_Y2) return go(k_umma3_persist<U3_MODE_Y2>);
