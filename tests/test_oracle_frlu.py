@@ -165,3 +165,18 @@ def test_frlu_error_tracks_sigma_k1():
         assert spec <= 50 * sigma[k] and spec <= bound, (k, spec, sigma[k])
         errs.append(spec)
     assert errs[0] > errs[1] > errs[2]
+
+
+def test_srft_params_are_seeded_distinct_and_in_range():
+    """The SRFT's random numbers: theta in [0, 1) (FP32), s distinct in [0, n), both fixed
+    by the seed and different for another seed."""
+    theta, s = synth.srft_params(3000, 200, seed=4)
+    assert theta.dtype == np.float32 and theta.shape == (3000,)
+    assert np.all((theta >= 0) & (theta < 1))
+    assert s.dtype == np.int32 and len(np.unique(s)) == 200 and s.min() >= 0 and s.max() < 3000
+    t2, s2 = synth.srft_params(3000, 200, seed=4)
+    assert np.array_equal(theta, t2) and np.array_equal(s, s2)
+    t3, s3 = synth.srft_params(3000, 200, seed=5)
+    assert not np.array_equal(s, s3)
+    with pytest.raises(ValueError):
+        synth.srft_params(10, 11, seed=1)
