@@ -9,7 +9,7 @@
 //        P X = [L_1; L_2] L_1^{-1}, J = P[:l], so B = M^{-1} V L_1^{-1} A(J,:) with
 //        V = L_y^H [L_1; L_2] (k x l; its first k columns are M = L_y^H L_y). V is one real
 //        product over the stacked real and imaginary planes (k_frlu_planes, FP32 products,
-//        FP64 split reduction); W = V L_1^{-1} by k_frlu_wsolve (a warp per row); C = W A(J,:)
+//        FP64 split reduction); W = V L_1^{-1} by k_frlu_wsolve (four warps per row); C = W A(J,:)
 //        is one real product of the stacked planes of W with the gathered rows A(J,:); the
 //        Hermitian system M B = C is solved through its real form [[Re M, -Im M], [Im M, Re M]]
 //        by the LDL^T factorization and blocked substitution of Algorithm 1's step 5.
