@@ -81,6 +81,11 @@ def barrier(world):
         dist.barrier()
 
 
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Replicas (weak scaling): the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def max_over_ranks(x: float, world: int, device) -> float:
     if world == 1:
         return x
@@ -410,7 +415,7 @@ def run_ours(args):
     launches = rlu.launch_count() - launches0
     ms = t_start.elapsed_time(t_stop)
     ms_max = max_over_ranks(ms, world, dev)
-    value = world * K / (ms_max / 1e3)
+    value = whole_job_rate(K, world, ms_max)
     stage_ms = {names[i]: statistics.mean(evs[s][2 * i].elapsed_time(evs[s][2 * i + 1])
                                           for s in range(K)) for i in range(ns)}
 
@@ -475,7 +480,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier(world)
         e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
-        e2e = {"value": world * K / (e2e_ms / 1e3), "unit": "LU/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": whole_job_rate(K, world, e2e_ms), "unit": "LU/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "note": "two device buffers and factorizers; the copy of the next step's A "
                        "overlaps the current factorization"}
