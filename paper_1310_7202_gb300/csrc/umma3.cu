@@ -501,14 +501,16 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
     // ---- epilogue ------------------------------------------------------------------------
     const int quarter = warp & 3;
     for (int it = 0; !*err; ++it) {
-      const int ti = take(it, 0);  // every lane reads; lane 0 frees the entry for the warp
-      __syncwarp();
+      // every lane reads; lane 0's outcome is the warp's (the tcgen05.ld below needs all 32
+      // lanes), and lane 0 frees the entry for the warp
+      const int ti = __shfl_sync(0xffffffffu, take(it, 0), 0);
       if (lane == 0) mb_arrive(su32(&sh.qempty[it % U3_QN]));
       if (ti < 0) break;
       const int2 t = tiles[ti];
       const Umma3Args& a = jobs[t.x].a;
       const int buf = it & 1;
-      if (!mb_wait(su32(&sh.accf[buf]), (uint32_t)((it / 2) & 1))) {
+      const bool done = mb_wait(su32(&sh.accf[buf]), (uint32_t)((it / 2) & 1));
+      if (!__shfl_sync(0xffffffffu, done ? 1 : 0, 0)) {
         fail(a);
         break;
       }
@@ -553,8 +555,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
     const int r = threadIdx.x - 192;  // 0..127
     uint32_t g = 0;
     for (int it = 0; !*err; ++it) {
-      const int ti = take(it, 0);
-      __syncwarp();
+      const int ti = __shfl_sync(0xffffffffu, take(it, 0), 0);  // lane 0's outcome
       if (lane == 0) mb_arrive(su32(&sh.qempty[it % U3_QN]));
       if (ti < 0) break;
       const int2 t = tiles[ti];
@@ -564,7 +565,8 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
       bool ok = true;
       for (int kt = 0; kt < nk; ++kt, ++g) {
         const uint32_t st = g % (uint32_t)S;
-        if (!mb_wait(su32(&sh.full[st]), (g / S) & 1)) {
+        const bool got = mb_wait(su32(&sh.full[st]), (g / S) & 1);
+        if (!__shfl_sync(0xffffffffu, got ? 1 : 0, 0)) {  // lane 0's outcome, warp-uniform
           fail(a);
           ok = false;
           break;
