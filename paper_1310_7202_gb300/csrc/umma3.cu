@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
   } else if (warp >= 2 && warp < 6) {
     // ---- epilogue ------------------------------------------------------------------------
     const int quarter = warp & 3;
-    for (int it = 0; !*err; ++it) {
+    for (int it = 0; !__shfl_sync(0xffffffffu, *err, 0); ++it) {  // warp-uniform test
       // every lane reads; lane 0's outcome is the warp's (the tcgen05.ld below needs all 32
       // lanes), and lane 0 frees the entry for the warp
       const int ti = __shfl_sync(0xffffffffu, take(it, 0), 0);
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
     // ---- converter: one thread per tile row (128 rows) ------------------------------------
     const int r = threadIdx.x - 192;  // 0..127
     uint32_t g = 0;
-    for (int it = 0; !*err; ++it) {
+    for (int it = 0; !__shfl_sync(0xffffffffu, *err, 0); ++it) {  // warp-uniform test
       const int ti = __shfl_sync(0xffffffffu, take(it, 0), 0);  // lane 0's outcome
       if (lane == 0) mb_arrive(su32(&sh.qempty[it % U3_QN]));
       if (ti < 0) break;
