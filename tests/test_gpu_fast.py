@@ -57,6 +57,21 @@ def test_fast_factor_against_oracle(m, n, k, l):
     assert g["info"].tolist()[:3] == [0, -1, -1]
 
 
+def test_fast_factor_paper_error_shape():
+    """The shape of the paper's error comparison of Algorithms 1 and 4 (Section 6): 3000 x 3000
+    (n = 2^3 3 5^3, a mixed-radix row transform), exponentially decaying spectrum, l = k + 3."""
+    m = n = 3000
+    k, l = 20, 23
+    sigma = synth.spectrum("paper_exp", n)
+    A = synth.prescribed_matrix(m, n, sigma, 81, 82, dtype=np.float32)
+    g, theta, s = _factor(A, k, l, seed=83)
+    o = F.frlu_factor(A.astype(np.float64), k, l, theta, s)
+    fro_o, _ = F.creconstruct_error(A, o["P"], o["Q"], o["L"], o["U"])
+    fro_g, _ = F.creconstruct_error(A, g["P"], g["Q"], g["L"], g["U"])
+    assert fro_g <= 1.1 * fro_o + 1e-4 * sigma[0], (fro_g, fro_o)
+    assert g["info"].tolist()[:3] == [0, -1, -1]
+
+
 def test_fast_factor_exact_for_rank_k():
     m, n, r, k, l = 400, 256, 8, 8, 24
     A = synth.prescribed_matrix(m, n, synth.spectrum("rank_k", r, r), 3, 4, dtype=np.float32)
