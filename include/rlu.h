@@ -169,20 +169,32 @@ int32_t rlu_factor_stages(const void* A, int32_t dtype, int64_t m, int64_t n, in
                           const rlu_stage_outputs* stages, void* stream);
 
 /* Power iterations (Section 5, "Power Iterations"): step 2 becomes
- * Y = (A A^T)^q A G, applied as q rounds of Z = A^T Y, Y = A Z (unnormalised, so q should
- * stay small: the paper's scheme for larger q normalises between rounds). The products of
- * the rounds are FP32 accurate on RLU_PREC_MIXED (three TF32 products) and RLU_PREC_BF16
- * (three BF16 products against the exact BF16 A); plain FP32 / FP64 SIMT otherwise.
- * 0 <= q <= 16 (q = 0 is rlu_factor_stages). Workspace: rlu_workspace_size_power, which
- * adds Z (n x l) and the splits of Y and Z to rlu_workspace_size. Other arguments, outputs
- * and errors as rlu_factor_stages; RLU_EINVAL also for q outside [0, 16]. */
+ * Y = (A A^T)^q A G, applied as q rounds of Z = A^T Y, Y = A Z.
+ *   normalized = 0: unnormalised rounds, as the paper states them for small q. The scale of
+ *              the top singular direction grows like sigma_1^(2q+1) against the others, so
+ *              directions below (sigma_{k+1}/sigma_1)^(2q+1) of it drown in the rounding of
+ *              the path's type (FP32: already at q = 1 for sigma_i = i^-2 and k = 200).
+ *   normalized = 1: the normalised scheme the paper refers to for larger q, read as LU
+ *              normalisation: before each product the block (Y, then Z) is factored with
+ *              partial pivoting and replaced by P^T L (its unit lower factor with the rows
+ *              put back). This multiplies the block on the right by an upper triangular
+ *              matrix, so the column space, and in exact arithmetic the pivots and factors
+ *              of steps 3-8, are those of the unnormalised rounds; each round costs two
+ *              more pivoted LUs (m x l and n x l).
+ * The products of the rounds are FP32 accurate on RLU_PREC_MIXED (three TF32 products) and
+ * RLU_PREC_BF16 (three BF16 products against the exact BF16 A); plain FP32 / FP64 SIMT
+ * otherwise. 0 <= q <= 16 (q = 0 is rlu_factor_stages). The normalisation LUs use P and Q
+ * as scratch before the factorization writes them. Workspace: rlu_workspace_size_power
+ * (either value of normalized), which adds Z (n x l), the normalised block and the splits
+ * of Y and Z to rlu_workspace_size. Other arguments, outputs and errors as
+ * rlu_factor_stages; RLU_EINVAL also for q outside [0, 16] or normalized not 0 or 1. */
 size_t rlu_workspace_size_power(int64_t m, int64_t n, int32_t k, int32_t l, int32_t prec,
                                 int32_t q);
 int32_t rlu_factor_power(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
                          int32_t k, int32_t l, uint64_t seed, int32_t prec, int32_t q,
-                         int32_t* P, int32_t* Q, void* L, int64_t ldl, void* U, int64_t ldu,
-                         rlu_info* info, void* workspace, size_t ws_bytes,
-                         const rlu_stage_outputs* stages, void* stream);
+                         int32_t normalized, int32_t* P, int32_t* Q, void* L, int64_t ldl,
+                         void* U, int64_t ldu, rlu_info* info, void* workspace,
+                         size_t ws_bytes, const rlu_stage_outputs* stages, void* stream);
 
 /* Algorithm 3 (Section 5, "Rank Deficient Least Squares"): x minimising ||A x - b|| from
  * the factors of Algorithm 1 (A ~ P^T L U Q^T): c = P b (c[i] = b[P[i]]), y = L^+ c by the
@@ -227,8 +239,12 @@ int32_t rlu_reconstruct_error(const void* A, int32_t dtype, int64_t m, int64_t n
  * framework that owns all device memory through its own pool, or a path where a cudaMalloc
  * or cudaFree would synchronise the device). Its scratch is a fixed 8 MiB array in the
  * library's device memory, present on every GPU that loads the library until the process
- * exits; it makes no allocating call. The first call on a device looks up that array's
- * address (with the device current): make it before any stream capture. Problems needing
+ * exits; it makes no allocating call. The first call in a device's CUDA context looks up
+ * that array's address (with the device current) and caches it with the context's id; a
+ * call in a new context (after cudaDeviceReset, or once the primary context was released
+ * and created again) looks it up again. No lookup is made while ``stream`` is capturing:
+ * that call returns RLU_EINVAL, so make the first call on a device, and the first after a
+ * reset, outside any stream capture. Problems needing
  * more than 8 MiB of scratch (rlu_reconstruct_workspace_size() > 8 MiB) return RLU_ENOMEM
  * before anything is enqueued. All calls share the array: calls that overlap on the GPU
  * race, so order them (one stream, or events). Other arguments, outputs and errors as in

@@ -37,6 +37,7 @@ struct U3Smem {
   uint64_t conv[U3_MAXST];
   uint64_t empty[U3_MAXST];
   uint64_t accum;
+  uint64_t drain;  // final commit of the MMA issuer when a wait gave up
   uint32_t tmem_base;
   int32_t err;
 };
@@ -154,6 +155,7 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
       mb_init(su32(&sh.empty[s]), 1);
     }
     mb_init(su32(&sh.accum), 1);
+    mb_init(su32(&sh.drain), 1);
     sh.err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -166,6 +168,7 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = sh.tmem_base;
+  int issued = 0;  // k-steps whose loads the producer started
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ------------------------------------------------------------------
@@ -201,6 +204,7 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
         tma2d(base + lay.b0, &mB0, kx, nb0, bar);
         tma2d(base + lay.b1, &mB1, kx, nb0, bar);
       }
+      issued = kt + 1;
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer --------------------------------------------------------------------
@@ -315,6 +319,20 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
+  if (sh.err) {
+    // a wait gave up: let the work already issued finish (bounded) before TMEM is freed
+    // and the CTA exits. The MMA issuer's final commit covers every MMA it issued; the
+    // producer waits for the loads of the last S k-steps it started.
+    if (warp == 1 && lane == 0) {
+      commit(su32(&sh.drain));
+      mb_wait(su32(&sh.drain), 0u);
+    }
+    if (warp == 0 && lane == 0)
+      for (int kt = issued > S ? issued - S : 0; kt < issued; ++kt)
+        mb_wait(su32(&sh.full[kt % S]), (uint32_t)((kt / S) & 1));
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+  }
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
@@ -353,6 +371,7 @@ struct U3PSmem {
   uint64_t acce[2];       // accumulator buffer b read (4 epilogue warps)
   uint64_t qfull[U3_QN];  // queue entry written (producer)
   uint64_t qempty[U3_QN]; // queue entry read (MMA 1 + converter 4 warps + epilogue 4 warps)
+  uint64_t drain;         // final commit of the MMA issuer when a wait gave up
   int queue[U3_QN];       // tile indices, -1 = no more tiles
   uint32_t tmem_base;
   int32_t err;
@@ -383,6 +402,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
       mb_init(su32(&sh.qfull[q]), 1);
       mb_init(su32(&sh.qempty[q]), 9);
     }
+    mb_init(su32(&sh.drain), 1);
     sh.err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -401,6 +421,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
     if (a.status) atomicExch(a.status, RLU_ETIMEOUT);
   };
   const Umma3Args& a_first = jobs[tiles[min((int)blockIdx.x, ntiles - 1)].x].a;
+  uint32_t issued = 0;  // ring k-steps whose loads the producer started
   // the it-th tile of this CTA from the queue (-1: none left, or a wait gave up); the
   // reader's arrival frees the entry
   auto take = [&](int it, int arrivals) -> int {
@@ -453,6 +474,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
           tma2d(base + lay.b0, &j.map[2], kx, 0, bar);
           tma2d(base + lay.b1, &j.map[3], kx, 0, bar);
         }
+        issued = g + 1;
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -611,6 +633,20 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
+  if (*err) {
+    // a wait gave up: let the work already issued finish (bounded) before TMEM is freed
+    // and the CTA exits (the MMA issuer's final commit covers every MMA it issued; the
+    // producer waits for the loads of the last S ring steps it started)
+    if (warp == 1 && lane == 0) {
+      commit(su32(&sh.drain));
+      mb_wait(su32(&sh.drain), 0u);
+    }
+    if (warp == 0 && lane == 0)
+      for (uint32_t g = issued > (uint32_t)S ? issued - S : 0; g < issued; ++g)
+        mb_wait(su32(&sh.full[g % S]), (g / S) & 1);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+  }
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");

@@ -44,6 +44,7 @@ struct UbSmem {
   uint64_t full[UB_MAXST];
   uint64_t empty[UB_MAXST];
   uint64_t accum;
+  uint64_t drain;  // final commit of the MMA issuer when a wait gave up
   uint32_t tmem_base;
   int32_t err;
 };
@@ -188,6 +189,7 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
       mb_init(su32(&sh.empty[s]), 1);
     }
     mb_init(su32(&sh.accum), 1);
+    mb_init(su32(&sh.drain), 1);
     sh.err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -200,6 +202,7 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = sh.tmem_base;
+  int issued = 0;  // k-steps whose loads the producer started
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ------------------------------------------------------------------
@@ -233,6 +236,7 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
         for (int j = 0; j < a.BN / 64; ++j)        // A: x = n (64 wide), y = m (32)
           tma2d(base + lay.b0 + (uint32_t)j * 4096u, &mA, nb0 + 64 * j, kx, bar);
       }
+      issued = kt + 1;
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: 4 MMAs of K = 16 per 64-wide slot ---------------------------------
@@ -329,6 +333,20 @@ k_ummab(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
+  if (sh.err) {
+    // a wait gave up: let the work already issued finish (bounded) before TMEM is freed
+    // and the CTA exits (the MMA issuer's final commit covers every MMA it issued; the
+    // producer waits for the loads of the last S k-steps it started)
+    if (warp == 1 && lane == 0) {
+      commit(su32(&sh.drain));
+      mb_wait(su32(&sh.drain), 0u);
+    }
+    if (warp == 0 && lane == 0)
+      for (int kt = issued > S ? issued - S : 0; kt < issued; ++kt)
+        mb_wait(su32(&sh.full[kt % S]), (uint32_t)((kt / S) & 1));
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+  }
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n"
