@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -45,6 +46,12 @@ def sources() -> list[str]:
 def build(verbose: bool = False, force: bool = False) -> str:
     """Compile and link librlu.so; returns its path. Skips work when up to date."""
     os.makedirs(BUILD, exist_ok=True)
+    # objects built on another host architecture (x86 container vs Arm GPU host) are never
+    # reused: the stamp names the machine that built what is under _build/
+    stamp = os.path.join(BUILD, "HOST_ARCH")
+    host = platform.machine()
+    if not os.path.exists(stamp) or open(stamp).read().strip() != host:
+        force = True
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     inc = os.path.join(ROOT, "include")
@@ -67,6 +74,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link of librlu.so failed:\n" + res.stderr[-6000:])
+    with open(stamp, "w") as f:
+        f.write(host + "\n")
     if verbose:
         print(f"built {LIB} ({len(jobs)} of {len(srcs)} sources compiled)")
     return LIB
