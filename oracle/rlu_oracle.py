@@ -357,30 +357,54 @@ def check_dims(m: int, n: int, k: int, l: int) -> None:
         raise ValueError(f"need 1 <= k <= l <= min(m, n); got m={m} n={n} k={k} l={l}")
 
 
-def project(A: np.ndarray, G: np.ndarray, q: int = 0) -> np.ndarray:
+def lu_normalize(X: np.ndarray) -> np.ndarray:
+    """The normalisation between power-iteration rounds (the normalised scheme that the
+    power-iteration subsection of Section 5 refers to for larger q), read here as: replace
+    the block X (r x l) by the lower factor of its partial-pivot LU, with the rows put back
+    in X's order, Lt = P^T L (so X = Lt U and range(Lt) = range(X) when U is invertible).
+    Its entries are bounded by 1, so a following product with A or A^T starts from
+    well-scaled columns instead of ones that all lean towards the top singular vector."""
+    X_lu, perm, _, _ = lu_partial_pivot(X)
+    r, l = X.shape
+    L = np.tril(X_lu[:, :l], -1) + np.eye(r, l)
+    Lt = np.empty_like(L)
+    Lt[perm] = L
+    return Lt
+
+
+def project(A: np.ndarray, G: np.ndarray, q: int = 0, normalized: bool = False) -> np.ndarray:
     """Step 2, Y = A G, or with the power iterations of Section 5 ("Power Iterations"):
-    Y = (A A^*)^q A G for a small integer q, unnormalised, applied as q rounds of
-    Y <- A (A^T Y) (A real, so A^* = A^T)."""
+    Y = (A A^*)^q A G for a small integer q, applied as q rounds of Y <- A (A^T Y) (A real,
+    so A^* = A^T). ``normalized``: every round first replaces Y by lu_normalize(Y) and
+    A^T Y by lu_normalize(A^T Y). Each normalisation multiplies the block on the right by
+    the inverse of an upper triangular U, so the result is (A A^T)^q A G T with T upper
+    triangular: the same column space, and (exact arithmetic) the same pivots and L_y in
+    step 3, since P (Y T) = L_y (U_y T)."""
     if q < 0:
         raise ValueError("q must be >= 0")
     Y = A @ G
     for _ in range(q):
-        Y = A @ (A.T @ Y)
+        if normalized:
+            Y = lu_normalize(Y)
+            Y = A @ lu_normalize(A.T @ Y)
+        else:
+            Y = A @ (A.T @ Y)
     return Y
 
 
 def rlu_factor(A: np.ndarray, k: int, l: int, seed: int, stream_id: int = 0,
-               G: np.ndarray | None = None, q: int = 0) -> dict:
+               G: np.ndarray | None = None, q: int = 0, normalized: bool = False) -> dict:
     """Algorithm 1, steps 1-8, in FP64. A is upcast exactly. Returns P, Q (gather form),
     L (m x k, unit lower trapezoidal), U (k x n, upper trapezoidal) and the intermediates
-    G, Y (A G, or (A A^T)^q A G with q power iterations), Y_lu (factored Y), L_y, B, plus
-    zero-pivot steps and per-step pivot gaps."""
+    G, Y (A G, or (A A^T)^q A G with q power iterations, LU-normalised between products
+    when ``normalized``), Y_lu (factored Y), L_y, B, plus zero-pivot steps and per-step
+    pivot gaps."""
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     check_dims(m, n, k, l)
     if G is None:
         G = gaussian(seed, stream_id, n, l)                 # step 1
-    Y = project(A, G, q)                                    # step 2
+    Y = project(A, G, q, normalized)                        # step 2
     Y_lu, P, zero_y, gaps_y = lu_partial_pivot(Y)           # step 3
     Ly = np.tril(Y_lu[:, :k], -1) + np.eye(m, k)            # step 4: first k columns
     B = pinv_apply(Ly, A[P, :])                             # step 5
@@ -416,9 +440,10 @@ def rdls_apply(P, Q, L, U, b: np.ndarray) -> np.ndarray:
     return X[:, 0] if vec else X
 
 
-def rdls_solve(A: np.ndarray, b: np.ndarray, k: int, l: int, seed: int, q: int = 0) -> dict:
+def rdls_solve(A: np.ndarray, b: np.ndarray, k: int, l: int, seed: int, q: int = 0,
+               normalized: bool = False) -> dict:
     """Algorithm 3: step 1 is Algorithm 1 on A; returns x and the factors."""
-    res = rlu_factor(A, k, l, seed, q=q)
+    res = rlu_factor(A, k, l, seed, q=q, normalized=normalized)
     res["x"] = rdls_apply(res["P"], res["Q"], res["L"], res["U"], b)
     return res
 

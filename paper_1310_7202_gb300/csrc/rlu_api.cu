@@ -109,7 +109,9 @@ struct Plan {
   int64_t ldg = 0, ldy = 0, ldl = 0, ldb = 0, ldu12 = 0;
   int split_y = 1, split_g = 1, split_c = 1;
   int q = 0;                      // power iterations (Section 5)
+  bool normalized = false;        // LU-normalised rounds
   int split_z = 1, split_y3 = 1;  // their products Z = A^T Y and Y = A Z
+  size_t off_Ln = 0;              // the normalised block (FP64 / plain FP32 paths)
   size_t off_Z = 0, off_Yh = 0, off_Yl = 0, off_Zh = 0, off_Zl = 0, off_Yb[3] = {0, 0, 0},
          off_Zb[3] = {0, 0, 0};
   size_t off_Lbh = 0, off_Lbl = 0;  // TF32 split of L_b (k x k, ld round_up(k, 4))
@@ -125,10 +127,12 @@ static size_t carve(size_t& cur, size_t bytes) {
   return at;
 }
 
-static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p, int q = 0) {
+static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p, int q = 0,
+                      bool normalized = false) {
   p.prec = prec;
   if (q < 0 || q > 16) return false;
   p.q = q;
+  p.normalized = normalized && q > 0;
   if (prec == RLU_PREC_F64) {
     p.dt = RLU_F64;
     p.esz = 8;
@@ -210,6 +214,9 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p,
   }
   if (q > 0) {  // Z (n x l, ld ldg) and the splits of Y and Z for the accurate products
     p.off_Z = carve(cur, (size_t)p.ldg * l * e);
+    // the normalised block P^T L of the LU of Y (ld ldy) or of Z (ld ldg), read by the
+    // SIMT products (the tensor-core paths read its splits instead)
+    p.off_Ln = carve(cur, (size_t)(p.ldy > p.ldg ? p.ldy : p.ldg) * l * e);
     if (prec == RLU_PREC_MIXED) {
       p.off_Yh = carve(cur, (size_t)p.ldy * l * 4);
       p.off_Yl = carve(cur, (size_t)p.ldy * l * 4);
@@ -307,8 +314,27 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
   }
   // power iterations (Section 5): Y <- A (A^T Y), q times, with FP32-accurate products on
   // the reduced-precision paths (Z and Y are not random matrices whose rounding is harmless)
+  // LU normalisation of a block X (rows x l, column-major, ld): X is factored in place with
+  // partial pivoting (its permutation into perm, an output buffer overwritten later) and
+  // replaced, for the next product, by P^T L (unit lower factor, rows put back): in FP32 /
+  // FP64 into Ln, or straight into the splits the tensor-core products read.
+  auto normalize = [&](T* X, int64_t ld, int64_t rows, int32_t* perm, T* Ln, T* hi, T* lo,
+                       Bf16Parts parts) -> int32_t {
+    LuArgs a{};
+    a.X = X; a.ldx = ld; a.R = (int)rows; a.C = l; a.perm = perm;
+    a.zero_step = nullptr;  // a zero pivot of a round is not one of the factorization's
+    a.nonfinite = info ? &info->nonfinite : nullptr;
+    a.status = info ? &info->status : nullptr;
+    a.posg = reinterpret_cast<int32_t*>(ws + p.off_pos);
+    a.psg = reinterpret_cast<int32_t*>(ws + p.off_ps);
+    a.u12 = ws + p.off_u12;
+    a.ldu = p.ldu12;
+    RLU_TRY(launch_cluster_lu(p.dt, false, a, s));
+    return build_ly<T>(X, ld, rows, l, perm, Ln, nullptr, ld, s, hi, lo, parts);
+  };
   for (int it = 0; it < p.q; ++it) {
     T* Z = reinterpret_cast<T*>(ws + p.off_Z);  // n x l, column-major, ld ldg
+    T* Ln = reinterpret_cast<T*>(ws + p.off_Ln);
     if (bf16) {
       Bf16Parts yp{}, zp{};
       yp.hi = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Yb[0]);
@@ -317,7 +343,10 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
       zp.hi = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Zb[0]);
       zp.mid = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Zb[1]);
       zp.lo = reinterpret_cast<__nv_bfloat16*>(ws + p.off_Zb[2]);
-      RLU_TRY(split_parts(reinterpret_cast<const float*>(Y), p.ldy, m, l, nullptr, nullptr, yp, s));
+      if (p.normalized)
+        RLU_TRY(normalize(Y, p.ldy, m, P, nullptr, nullptr, nullptr, yp));
+      else
+        RLU_TRY(split_parts(reinterpret_cast<const float*>(Y), p.ldy, m, l, nullptr, nullptr, yp, s));
       UmmaBf16Op zo{};  // Z^T (l x n, row-major = Z column-major) = Y^T A
       zo.A = Av;
       zo.lda = lda;
@@ -335,7 +364,10 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
       zo.partial = reinterpret_cast<float*>(part);
       zo.status = info ? &info->status : nullptr;
       RLU_TRY(umma_bf16_gemm(UB_MODE_C3, zo, s));
-      RLU_TRY(split_parts(reinterpret_cast<const float*>(Z), p.ldg, n, l, nullptr, nullptr, zp, s));
+      if (p.normalized)
+        RLU_TRY(normalize(Z, p.ldg, n, Q, nullptr, nullptr, nullptr, zp));
+      else
+        RLU_TRY(split_parts(reinterpret_cast<const float*>(Z), p.ldg, n, l, nullptr, nullptr, zp, s));
       UmmaBf16Op yo{};  // Y = A Z, Z in three BF16 parts
       yo.A = Av;
       yo.lda = lda;
@@ -358,7 +390,11 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
       float* Yl = reinterpret_cast<float*>(ws + p.off_Yl);
       float* Zh = reinterpret_cast<float*>(ws + p.off_Zh);
       float* Zl = reinterpret_cast<float*>(ws + p.off_Zl);
-      RLU_TRY(split_parts(reinterpret_cast<const float*>(Y), p.ldy, m, l, Yh, Yl, Bf16Parts{}, s));
+      if (p.normalized)
+        RLU_TRY(normalize(Y, p.ldy, m, P, nullptr, reinterpret_cast<T*>(Yh),
+                          reinterpret_cast<T*>(Yl), Bf16Parts{}));
+      else
+        RLU_TRY(split_parts(reinterpret_cast<const float*>(Y), p.ldy, m, l, Yh, Yl, Bf16Parts{}, s));
       Umma3Op zo{};  // Z (n x l, column-major) = A^T Y, three TF32 products
       zo.A0 = reinterpret_cast<const float*>(A);
       zo.lda = lda;
@@ -375,7 +411,11 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
       zo.partial = reinterpret_cast<float*>(part);
       zo.status = info ? &info->status : nullptr;
       RLU_TRY(umma3_gemm(U3_MODE_C3, zo, s));
-      RLU_TRY(split_parts(reinterpret_cast<const float*>(Z), p.ldg, n, l, Zh, Zl, Bf16Parts{}, s));
+      if (p.normalized)
+        RLU_TRY(normalize(Z, p.ldg, n, Q, nullptr, reinterpret_cast<T*>(Zh),
+                          reinterpret_cast<T*>(Zl), Bf16Parts{}));
+      else
+        RLU_TRY(split_parts(reinterpret_cast<const float*>(Z), p.ldg, n, l, Zh, Zl, Bf16Parts{}, s));
       Umma3Op yo{};  // Y = A Z, three TF32 products
       yo.A0 = reinterpret_cast<const float*>(A);
       yo.lda = lda;
@@ -393,9 +433,19 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
       yo.status = info ? &info->status : nullptr;
       RLU_TRY(umma3_gemm(U3_MODE_Y3, yo, s));
     } else {
-      GemmOp zo{Y, p.ldy, true, A, lda, false, Z, p.ldg, true, l, n, m, p.split_z, part, false};
+      const T* Yin = Y;
+      if (p.normalized) {
+        RLU_TRY(normalize(Y, p.ldy, m, P, Ln, nullptr, nullptr, Bf16Parts{}));
+        Yin = Ln;
+      }
+      GemmOp zo{Yin, p.ldy, true, A, lda, false, Z, p.ldg, true, l, n, m, p.split_z, part, false};
       RLU_TRY((gemm_simt<T, T>(zo, s)));
-      GemmOp yo{A, lda, true, Z, p.ldg, true, Y, p.ldy, false, m, l, n, p.split_y3, part, false};
+      const T* Zin = Z;
+      if (p.normalized) {
+        RLU_TRY(normalize(Z, p.ldg, n, Q, Ln, nullptr, nullptr, Bf16Parts{}));
+        Zin = Ln;
+      }
+      GemmOp yo{A, lda, true, Zin, p.ldg, true, Y, p.ldy, false, m, l, n, p.split_y3, part, false};
       RLU_TRY((gemm_simt<T, T>(yo, s)));
     }
   }
@@ -624,13 +674,14 @@ extern "C" size_t rlu_workspace_size_power(int64_t m, int64_t n, int32_t k, int3
 
 extern "C" int32_t rlu_factor_power(const void* A, int32_t dtype, int64_t m, int64_t n,
                                     int64_t lda, int32_t k, int32_t l, uint64_t seed,
-                                    int32_t prec, int32_t q, int32_t* P, int32_t* Q, void* L,
-                                    int64_t ldl, void* U, int64_t ldu, rlu_info* info,
-                                    void* workspace, size_t ws_bytes,
+                                    int32_t prec, int32_t q, int32_t normalized, int32_t* P,
+                                    int32_t* Q, void* L, int64_t ldl, void* U, int64_t ldu,
+                                    rlu_info* info, void* workspace, size_t ws_bytes,
                                     const rlu_stage_outputs* stages, void* stream) {
   RLU_TRY(validate(A, dtype, m, n, lda, k, l, prec, P, Q, L, ldl, U, ldu));
+  if (normalized != 0 && normalized != 1) return RLU_EINVAL;
   Plan p;
-  if (!make_plan(m, n, k, l, prec, p, q)) return RLU_EINVAL;
+  if (!make_plan(m, n, k, l, prec, p, q, normalized != 0)) return RLU_EINVAL;
   if (workspace == nullptr || ws_bytes < p.total) return RLU_ENOMEM;
   if (((uintptr_t)workspace & 255u) != 0) return RLU_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -647,8 +698,8 @@ extern "C" int32_t rlu_factor_stages(const void* A, int32_t dtype, int64_t m, in
                                      void* U, int64_t ldu, rlu_info* info, void* workspace,
                                      size_t ws_bytes, const rlu_stage_outputs* stages,
                                      void* stream) {
-  return rlu_factor_power(A, dtype, m, n, lda, k, l, seed, prec, 0, P, Q, L, ldl, U, ldu, info,
-                          workspace, ws_bytes, stages, stream);
+  return rlu_factor_power(A, dtype, m, n, lda, k, l, seed, prec, 0, 0, P, Q, L, ldl, U, ldu,
+                          info, workspace, ws_bytes, stages, stream);
 }
 
 extern "C" int32_t rlu_factor(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,

@@ -116,7 +116,7 @@ def load_library(require_cuda: bool = True) -> ctypes.CDLL:
     lib.rlu_workspace_size_power.restype = sz
     lib.rlu_workspace_size_power.argtypes = [i64, i64, i32, i32, i32, i32]
     lib.rlu_factor_power.restype = i32
-    lib.rlu_factor_power.argtypes = fac[:9] + [i32] + fac[9:] + [ctypes.POINTER(_StageOutputs),
+    lib.rlu_factor_power.argtypes = fac[:9] + [i32, i32] + fac[9:] + [ctypes.POINTER(_StageOutputs),
                                                                 vp]
     lib.rlu_timed_step_name.restype = ctypes.c_char_p
     lib.rlu_timed_step_name.argtypes = [i32]
@@ -214,10 +214,11 @@ class Factorizer:
     size and precision."""
 
     def __init__(self, m: int, n: int, k: int, l: int, prec: int | str = RLU_PREC_F32,
-                 q: int = 0):
+                 q: int = 0, normalized: bool = False):
         self.lib = load_library()
         self.prec = PREC_BY_NAME[prec] if isinstance(prec, str) else int(prec)
         self.m, self.n, self.k, self.l, self.q = m, n, k, l, q
+        self.normalized = 1 if normalized else 0  # LU-normalised power-iteration rounds
         dt = _TORCH_OF_PREC[self.prec]
         self.dtype = dt
         ws = self.lib.rlu_workspace_size_power(m, n, k, l, self.prec, q)
@@ -243,7 +244,7 @@ class Factorizer:
         if stages is None and self.q == 0:
             st = self.lib.rlu_factor(*args, _stream_ptr(stream))
         elif stages is None:
-            st = self.lib.rlu_factor_power(*args[:9], self.q, *args[9:], None,
+            st = self.lib.rlu_factor_power(*args[:9], self.q, self.normalized, *args[9:], None,
                                            _stream_ptr(stream))
         else:
             ev = stages.get("events")
@@ -258,8 +259,8 @@ class Factorizer:
                                _dev_ptr(stages.get("Ly")), _dev_ptr(stages.get("B")),
                                ctypes.cast(ev_arr, ctypes.POINTER(ctypes.c_void_p))
                                if ev_arr is not None else None, n_ev)
-            st = self.lib.rlu_factor_power(*args[:9], self.q, *args[9:], ctypes.byref(so),
-                                           _stream_ptr(stream))
+            st = self.lib.rlu_factor_power(*args[:9], self.q, self.normalized, *args[9:],
+                                           ctypes.byref(so), _stream_ptr(stream))
         _check(st, "rlu_factor")
         return self.P, self.Q, self.L, self.U, self.info
 
@@ -272,13 +273,13 @@ class Factorizer:
 
 
 def factor(A: torch.Tensor, k: int, l: int, seed: int, prec: int | str | None = None,
-           stages: bool = False, q: int = 0) -> dict:
+           stages: bool = False, q: int = 0, normalized: bool = False) -> dict:
     """One randomized LU of A (CUDA tensor, row-major). Returns P, Q, L, U, info (device
     tensors) and, with ``stages=True``, the intermediates G, Y, Ly, B."""
     if prec is None:
         prec = {torch.float64: RLU_PREC_F64, torch.bfloat16: RLU_PREC_BF16}.get(A.dtype,
                                                                                RLU_PREC_F32)
-    f = Factorizer(A.shape[0], A.shape[1], k, l, prec, q)
+    f = Factorizer(A.shape[0], A.shape[1], k, l, prec, q, normalized)
     st = f.stage_buffers() if stages else None
     P, Q, L, U, info = f(A, seed, stages=st)
     out = {"P": P, "Q": Q, "L": L, "U": U, "info": info}

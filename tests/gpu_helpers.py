@@ -7,11 +7,12 @@ import oracle as O
 from paper_1310_7202_gb300 import rlu
 
 
-def run_gpu(A: np.ndarray, k: int, l: int, seed: int, prec: str, q: int = 0):
-    """Factor A on the GPU through rlu_factor_power (q power iterations) with the stage
-    outputs; returns numpy copies."""
+def run_gpu(A: np.ndarray, k: int, l: int, seed: int, prec: str, q: int = 0,
+            normalized: bool = False):
+    """Factor A on the GPU through rlu_factor_power (q power iterations, LU-normalised when
+    ``normalized``) with the stage outputs; returns numpy copies."""
     At = torch.from_numpy(np.ascontiguousarray(A)).cuda()
-    f = rlu.Factorizer(A.shape[0], A.shape[1], k, l, prec, q)
+    f = rlu.Factorizer(A.shape[0], A.shape[1], k, l, prec, q, normalized)
     st = f.stage_buffers()
     P, Q, L, U, info = f(At, seed, stages=st)
     torch.cuda.synchronize()
@@ -23,15 +24,22 @@ def run_gpu(A: np.ndarray, k: int, l: int, seed: int, prec: str, q: int = 0):
     return out
 
 
-def oracle_for(A: np.ndarray, k: int, l: int, seed: int, prec: str, q: int = 0):
+def oracle_for(A: np.ndarray, k: int, l: int, seed: int, prec: str, q: int = 0,
+               normalized: bool = False):
     """The oracle on the same stored A; the FP32 path's G definition for prec 'f32'."""
     G = None
     if prec == "f32":
         G = O.gaussian_f32(seed, 0, A.shape[1], l).astype(np.float64)
-    return O.rlu_factor(np.asarray(A, dtype=np.float64), k, l, seed=seed, G=G, q=q)
+    return O.rlu_factor(np.asarray(A, dtype=np.float64), k, l, seed=seed, G=G, q=q,
+                        normalized=normalized)
 
 
 def rel_max(a, b) -> float:
+    """max |a - b| / max |b|: the normwise (max-norm) relative difference. Entries of L and
+    U that are small because of cancellation carry absolute rounding errors of the size of
+    the terms that cancelled, so two correct implementations with different summation
+    orders agree entrywise only to that absolute level; the bound that backward-error
+    analysis gives, and the one tested, is relative to the largest entry."""
     b = np.asarray(b, dtype=np.float64)
     scale = np.max(np.abs(b))
     return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / (scale if scale > 0 else 1.0))

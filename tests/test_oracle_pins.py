@@ -288,11 +288,79 @@ def test_power_iteration_lowers_the_error(spec):
     assert np.median(e1) < np.median(e0), (e0, e1)
 
 
+def test_lu_normalize_is_scipys_permuted_lower_factor():
+    """The normalisation between rounds: the lower factor of the partial-pivot LU with the
+    rows put back (X = Lt U) is scipy's lu(X, permute_l=True) lower factor (LAPACK getrf)."""
+    import scipy.linalg as sl
+    rng = np.random.default_rng(8)
+    for r, l in ((50, 8), (37, 37), (200, 31)):
+        X = rng.standard_normal((r, l))
+        Lt = O.rlu_oracle.lu_normalize(X)
+        PL, Uf = sl.lu(X, permute_l=True)
+        assert np.abs(Lt - PL).max() <= 1e-13
+        assert np.abs(Lt @ Uf - X).max() <= 1e-12 * np.abs(X).max()
+        assert np.abs(Lt).max() <= 1.0 + 1e-15
+
+
+def test_normalized_power_is_an_upper_triangular_change_of_basis():
+    """Normalised rounds give (A A^T)^q A G T with T upper triangular (each normalisation
+    multiplies by the inverse of an upper triangular U factor): a least-squares fit of the
+    normalised Y on the unnormalised one recovers an upper triangular T, exactly (to
+    rounding) fitting. A normalisation that reordered or mixed columns would leave a lower
+    part; one that lost a round would not fit."""
+    rng = np.random.default_rng(4)
+    m, n, l = 60, 45, 7
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (U * np.linspace(1.4, 0.3, n)) @ V.T
+    G = rng.standard_normal((n, l))
+    for q in (1, 2):
+        Yu = O.project(A, G, q)
+        Yn = O.project(A, G, q, normalized=True)
+        T = np.linalg.lstsq(Yu, Yn, rcond=None)[0]
+        assert np.abs(Yu @ T - Yn).max() <= 1e-11 * np.abs(Yn).max()
+        assert np.abs(np.tril(T, -1)).max() <= 1e-9 * np.abs(T).max(), q
+
+
+def test_normalized_power_gives_the_same_factors():
+    """Y T with T upper triangular has the same partial-pivot pivots and lower factor as Y,
+    so in exact arithmetic normalised and unnormalised rounds give the same P, Q, L, U;
+    in FP64 on a well-resolved case they agree to rounding."""
+    m, n, k, l = 300, 260, 20, 30
+    A = synth.prescribed_matrix(m, n, synth.spectrum("paper_slow", n), 3, 4)
+    for q in (1, 2):
+        a = O.rlu_factor(A, k, l, seed=2, q=q)
+        b = O.rlu_factor(A, k, l, seed=2, q=q, normalized=True)
+        assert np.array_equal(a["P"], b["P"]) and np.array_equal(a["Q"], b["Q"])
+        assert np.abs(a["L"] - b["L"]).max() <= 1e-8 * np.abs(a["L"]).max()
+        assert np.abs(a["U"] - b["U"]).max() <= 1e-8 * np.abs(a["U"]).max()
+
+
+def test_normalized_power_keeps_directions_that_unnormalized_rounds_lose():
+    """Why the paper points to a normalised scheme for larger q: with sigma_i = i^-2 and
+    q = 4, (sigma_{k+1} / sigma_1)^(2q+1) = 441^-9 ~ 1e-24 is far below FP64's unit, so
+    the unnormalised product has lost the directions beyond the first few and the error
+    grows past the q = 0 error, while the normalised rounds keep improving on it. Both stay
+    at or above the optimum sigma_{k+1} (spectral norm)."""
+    m = n = 300
+    k, l = 20, 30
+    sigma = synth.spectrum("inv_square", n)
+    A = synth.prescribed_matrix(m, n, sigma, 3, 4)
+    e = {}
+    for q, norm in ((0, False), (4, False), (4, True)):
+        r = O.rlu_factor(A, k, l, seed=2, q=q, normalized=norm)
+        _, e[(q, norm)] = O.reconstruct_error(A, r["P"], r["Q"], r["L"], r["U"])
+        assert e[(q, norm)] >= sigma[k] * (1 - 1e-9)
+    assert e[(4, False)] > e[(0, False)]
+    assert e[(4, True)] < 0.5 * e[(0, False)]
+    assert e[(4, True)] < 0.25 * e[(4, False)]
+
+
 def test_power_iteration_keeps_exact_rank():
     m, n, k, l = 120, 90, 10, 14
     A = synth.prescribed_matrix(m, n, synth.spectrum("rank_k", min(m, n), k), 3, 4)
-    for q in (1, 2):
-        res = O.rlu_factor(A, k, l, seed=5, q=q)
+    for q, norm in ((1, False), (2, False), (1, True), (3, True)):
+        res = O.rlu_factor(A, k, l, seed=5, q=q, normalized=norm)
         _check_structure(res, m, n, k)
         fro, _ = O.reconstruct_error(A, res["P"], res["Q"], res["L"], res["U"], spectral=False)
         assert fro / np.linalg.norm(A) < 1e-12
