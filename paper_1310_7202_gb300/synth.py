@@ -60,6 +60,40 @@ def prescribed_matrix(m: int, n: int, sigma: np.ndarray, seed_u: int, seed_v: in
     return np.ascontiguousarray(A.astype(dtype))
 
 
+def round_to_bf16_bits(x: np.ndarray) -> np.ndarray:
+    """BF16 bit patterns (uint16) of the FP64 values x, rounded to nearest, ties to even, in
+    one step (no intermediate FP32 rounding). Finite values in BF16's normal range."""
+    u = np.ascontiguousarray(x, dtype=np.float64).view(np.uint64)
+    drop = np.uint64(45)                      # 52 - 7 mantissa bits
+    lsb = (u >> drop) & np.uint64(1)
+    u = (u + (np.uint64((1 << 44) - 1) + lsb)) >> drop << drop
+    return (u.view(np.float64).astype(np.float32).view(np.uint32) >> np.uint32(16)).astype(np.uint16)
+
+
+def bf16_bits_to_f64(bits: np.ndarray) -> np.ndarray:
+    """FP64 values (exact) of BF16 bit patterns."""
+    return (np.asarray(bits, dtype=np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+
+
+def prescribed_matrix_bf16(m: int, n: int, sigma: np.ndarray, seed_u: int, seed_v: int,
+                           rank: int) -> np.ndarray:
+    """BF16 bit patterns (uint16, m x n row-major) of A = U diag(sigma) V^T with the first
+    ``rank`` singular triplets, built on the CPU in FP64 (U: m x rank and V: n x rank from
+    the QR of seeded N(0,1) matrices, as in prescribed_matrix) and rounded to BF16 in one
+    step. Dropping sigma_i for i > rank changes A by at most sqrt(sum_{i>rank} sigma_i^2)
+    in Frobenius norm; the precision workload takes rank = 2048 for sigma_i = 0.99^i
+    (sigma_2049 = 1.1e-9), far below BF16's rounding of A."""
+    r = min(rank, len(sigma), m, n)
+    U = _haar_like_q(np.random.default_rng(seed_u), m, r)
+    V = _haar_like_q(np.random.default_rng(seed_v), n, r)
+    U *= sigma[:r]
+    out = np.empty((m, n), dtype=np.uint16)
+    for i0 in range(0, m, 4096):            # in row blocks: the FP64 product of the whole
+        i1 = min(m, i0 + 4096)               # matrix would hold 4 GB at the workload size
+        out[i0:i1] = round_to_bf16_bits(U[i0:i1] @ V.T)
+    return out
+
+
 def prescribed_matrix_torch(m: int, n: int, sigma: np.ndarray, seed_u: int, seed_v: int,
                             dtype, device: str = "cuda"):
     """Same construction with torch on ``device`` (for sizes where CPU QR is slow). The
@@ -103,8 +137,10 @@ WORKLOADS = {
                      seed_u=11, seed_v=12, seed_g=1),
     "fp32_8192": dict(m=8192, n=8192, k=200, l=210, spectrum="inv_square", dtype="f32",
                       seed_u=21, seed_v=22, seed_g=2),
+    # A built on the CPU from its 2048 leading singular triplets, rounded to BF16 in one step
+    # (prescribed_matrix_bf16), so that the stored FP64 oracle result of this matrix applies
     "bf16_32768x16384": dict(m=32768, n=16384, k=512, l=532, spectrum="geometric_099",
-                             dtype="bf16", seed_u=31, seed_v=32, seed_g=3),
+                             dtype="bf16", seed_u=31, seed_v=32, seed_g=3, rank=2048),
     # batched form: 4096 problems, sizes from batch_shapes, sigma_i = exp(-i/k), FP32
     "batch4096": dict(kind="batch", count=4096, spectrum="exp_k", dtype="f32", seed_shapes=4,
                       seed_u=41, seed_g=5000),
