@@ -12,9 +12,11 @@ from paper_1310_7202_gb300 import rlu, synth
 pytestmark = pytest.mark.gpu
 
 
-def _mix(seed=5, count=10):
+def _mix(seed=5, count=12):
     """Request shapes drawn like the serving workload (log-uniform m, n; k uniform;
-    l = k + 10, k resampled while l > min(m, n)), at sizes the oracle handles quickly."""
+    l = k + 10, k resampled while l > min(m, n)), at sizes the oracle handles quickly. The
+    classes cycle through the FP32-accuracy path (mixed), plain FP32, FP64 and the
+    BF16-accuracy class (BF16-stored A, the precision form)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
@@ -24,22 +26,33 @@ def _mix(seed=5, count=10):
             k = int(rng.integers(16, 65))
             if k + 10 <= min(m, n):
                 break
-        prec = ["mixed", "f32", "f64"][i % 3]
+        prec = ["mixed", "f32", "f64", "bf16"][i % 4]
         out.append((m, n, k, k + 10, prec, 100 + i))
     return out
 
 
 def _matrix(m, n, prec, seed):
+    """(the stored values in FP64, the device tensor, sigma); BF16 requests store A in
+    BF16 (the FP32 values rounded to nearest even, rows 16-byte aligned) and the oracle
+    factors those values."""
     sigma = synth.spectrum("inv_1p5", min(m, n))
     dt = np.float64 if prec == "f64" else np.float32
-    return synth.prescribed_matrix(m, n, sigma, seed, seed + 1, dtype=dt), sigma
+    A = synth.prescribed_matrix(m, n, sigma, seed, seed + 1, dtype=dt)
+    At = torch.from_numpy(A)
+    if prec != "bf16":
+        return A.astype(np.float64), At.cuda(), sigma
+    # the BF16 products read A with TMA: rows padded to a multiple of 8 elements
+    buf = torch.zeros((m, (n + 7) // 8 * 8), dtype=torch.bfloat16, device="cuda")
+    buf[:, :n] = At.to(torch.bfloat16).cuda()
+    Ad = buf[:, :n]
+    return Ad.double().cpu().numpy(), Ad, sigma
 
 
 @pytest.fixture(scope="module")
 def served():
     cases = _mix()
     mats = [_matrix(m, n, p, s) for (m, n, k, l, p, s) in cases]
-    dev = [torch.from_numpy(A).cuda() for A, _ in mats]
+    dev = [At for _, At, _ in mats]
     alone = []
     for (m, n, k, l, p, s), A in zip(cases, dev):
         r = rlu.factor(A, k, l, s, p)
@@ -74,10 +87,17 @@ def test_results_same_alone_and_in_mix(served):
         assert torch.equal(a["info"], b["info"]), c
 
 
+def test_every_class_is_served(served):
+    cases, mats, alone, mixed, states, stats = served
+    assert {c[4] for c in cases} == {"mixed", "f32", "f64", "bf16"}
+
+
 def test_mixed_results_within_tolerance_of_oracle(served):
     cases, mats, alone, mixed, states, stats = served
-    for (m, n, k, l, p, s), (A, sigma), b in zip(cases, mats, mixed):
-        G = None if p == "f64" else O.gaussian_f32(s, 0, n, l).astype(np.float64)
+    for (m, n, k, l, p, s), (A, _, sigma), b in zip(cases, mats, mixed):
+        # the oracle draws its own G: FP64 for the FP64 and BF16 classes (the BF16 path's
+        # rounding of G counts as error), the FP32 transform for the FP32 classes
+        G = None if p in ("f64", "bf16") else O.gaussian_f32(s, 0, n, l).astype(np.float64)
         o = O.rlu_factor(A.astype(np.float64), k, l, seed=s, G=G)
         fro_o, _ = O.reconstruct_error(A, o["P"], o["Q"], o["L"], o["U"], spectral=False)
         fro_g, _ = O.reconstruct_error(A, b["P"].cpu().numpy(), b["Q"].cpu().numpy(),
