@@ -46,7 +46,7 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
-    ap.add_argument("--prec", choices=["f32", "mixed", "f64", "bf16"], default=None,
+    ap.add_argument("--prec", choices=["f32", "mixed", "f64", "bf16", "fp8"], default=None,
                     help="arithmetic of the path (default: the workload's storage type)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-power", action="store_true",
@@ -580,7 +580,7 @@ def run_ours(args):
 
     # ---- the plain FP32 path on the same input, for the "vs plain FP32" comparison -----
     plain = None
-    if prec in ("mixed", "bf16"):
+    if prec in ("mixed", "bf16", "fp8"):
         A32 = A if A.dtype == torch.float32 else A.float()   # the same values in FP32
         fp = rlu.Factorizer(m, n, k, l, "f32")
         pe = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * ns)]
@@ -610,7 +610,7 @@ def run_ours(args):
     # ---- two factorizations in flight (two streams, own buffers): the LU latency of one
     # overlaps the products of the other ---------------------------------------------
     two = None
-    if prec in ("mixed", "bf16"):
+    if prec in ("mixed", "bf16", "fp8"):
         fzb = rlu.Factorizer(m, n, k, l, prec)
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
         fzs = [fz, fzb]
@@ -729,6 +729,8 @@ def run_ours(args):
                             "bf16": "tcgen05 BF16 GEMMs (Y: BF16 x BF16; C: 3-part split "
                                     "BF16 L~), TF32-split Gram, cluster register LUs, "
                                     "LDL^T + blocked triangular solves",
+                            "fp8": "Y: e4m3 A and G with per-tile UE8M0 scales on the "
+                                   "block-scaled tcgen05 MMA; the rest as the BF16 form",
                             "f32": "SIMT GEMMs, cluster register LUs",
                             "f64": "FP64 SIMT GEMMs, cluster register LUs"}[prec],
                    "l2": f"inputs larger than L2 (A = {A.numel() * A.element_size() / 1e6:.0f} MB)",
@@ -1010,6 +1012,35 @@ def single_config(wname: str, K: int, W: int, peaks: dict, peak_kind: str) -> di
         plain = {"value": 1e3 / pms, "unit": "LU/s", "ms_per_step": pms, "fro": fro_p.item(),
                  "speedup": pms / ms, "speedup_of": prec}
         del A32, fp
+    fp8 = None
+    if prec == "bf16":  # the FP8 variant of the projection on the same stored A
+        f8 = rlu.Factorizer(m, n, k, l, "fp8")
+        e8 = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * ns)]
+              for _ in range(max(3, K // 2))]
+        for _ in range(2):
+            f8(A, w["seed_g"])
+        torch.cuda.synchronize()
+        for ev in e8:
+            f8(A, w["seed_g"], stages={"events": ev})
+        torch.cuda.synchronize()
+        st8 = {names[i]: statistics.mean(ev[2 * i].elapsed_time(ev[2 * i + 1]) for ev in e8)
+               for i in range(ns)}
+        ms8 = statistics.median(ev[0].elapsed_time(ev[2 * ns - 1]) for ev in e8)
+        P8, Q8, L8, U8, i8 = f8(A, w["seed_g"])
+        fro8, _ = rlu.reconstruct_error(A, P8, Q8, L8, U8)
+        torch.cuda.synchronize()
+        fl = 2.0 * m * n * l
+        fp8 = {"value": 1e3 / ms8, "unit": "LU/s", "ms_per_step": ms8,
+               "gemm_Y_ms": st8["gemm_Y"], "gaussian_ms": st8["gaussian"],
+               "gemm_Y_note": "quantisation of A (1 x 128 tiles) plus the block-scaled e4m3 "
+                              "product",
+               "gemm_Y_tflops": fl / (st8["gemm_Y"] / 1e3) / 1e12,
+               "fro": fro8.item(), "info": i8.cpu().tolist()}
+        if "oracle_fro" in err:
+            fp8["oracle_fro"] = err["oracle_fro"]
+            fp8["within_tolerance"] = bool(fro8.item() <= 1.1 * err["oracle_fro"]
+                                           + 1e-4 * sigma[0])
+        del f8
     res = {"workload": f"{wname}: m={m} n={n} k={k} l={l}, sigma_i={w['spectrum']}, "
                        f"{w['dtype']} storage, {prec} path",
            "value": 1e3 / ms, "unit": "LU/s", "ms_per_step": ms, "steps": K, "warmup": W,
@@ -1019,7 +1050,7 @@ def single_config(wname: str, K: int, W: int, peaks: dict, peak_kind: str) -> di
            "setup_s": round(setup_s, 1), "stages_ms": {x: round(v, 4) for x, v in stage_ms.items()},
            "roofline": roof, "gemms": gemms,
            "gemm_tflops": 2.0 * m * n * (l + k) / ((stage_ms["gemm_Y"] + stage_ms["gemm_C"]) / 1e3) / 1e12,
-           "error": err, "plain_fp32": plain}
+           "error": err, "plain_fp32": plain, "fp8_projection": fp8}
     del fz, A, flush
     torch.cuda.empty_cache()
     return res

@@ -63,12 +63,23 @@ typedef enum { RLU_F64 = 0, RLU_F32 = 1, RLU_BF16 = 2 } rlu_dtype;
  *                 Y = A G runs on the BF16 tensor cores with FP32 accumulation; C = L~^T A
  *                 takes L~ in three BF16 parts (hi + mid + lo, FP32 accurate) against the
  *                 exact BF16 A; Y, L~, the Gram matrix (TF32 splits as in RLU_PREC_MIXED), the
- *                 LUs, L and U are FP32 (L and U are returned in FP32). */
+ *                 LUs, L and U are FP32 (L and U are returned in FP32).
+ *   RLU_PREC_FP8: as RLU_PREC_BF16, but Y = A G runs in FP8 e4m3 with per-tile power-of-two
+ *                 (UE8M0) scales: A is quantised with one scale per row and 128-column
+ *                 block (1 x 128 tiles), G with one scale per 128 x 128 block, each scale the
+ *                 smallest power of two that keeps the tile's largest magnitude within e4m3's
+ *                 448 (round to nearest even); the tensor cores apply the scales
+ *                 (block-scaled MMA) and accumulate in FP32. The workspace adds the e4m3 A
+ *                 (m x 128*ceil(n/128) bytes), G and the scales. E4m3 keeps 4 significant
+ *                 bits, so A's quantisation adds about 3% relative noise to every entry: the
+ *                 range finder tolerates it only while that noise stays well below
+ *                 sigma_{k+1} (it does not at 32768 x 16384 with sigma_i = 0.99^i, k = 512). */
 typedef enum {
   RLU_PREC_F64 = 0,
   RLU_PREC_F32 = 1,
   RLU_PREC_MIXED = 2,
-  RLU_PREC_BF16 = 3
+  RLU_PREC_BF16 = 3,
+  RLU_PREC_FP8 = 4
 } rlu_precision;
 
 /* Device-resident status written by rlu_factor (the caller reads it after the stream

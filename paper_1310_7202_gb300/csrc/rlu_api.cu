@@ -112,6 +112,9 @@ struct Plan {
   bool normalized = false;        // LU-normalised rounds
   int split_z = 1, split_y3 = 1;  // their products Z = A^T Y and Y = A Z
   size_t off_Ln = 0;              // the normalised block (FP64 / plain FP32 paths)
+  // FP8 projection: e4m3 A and G with their UE8M0 scales
+  size_t off_A8 = 0, off_SA = 0, off_G8 = 0, off_SG = 0;
+  int64_t ld8 = 0, lds = 0, lsg = 0;
   size_t off_Z = 0, off_Yh = 0, off_Yl = 0, off_Zh = 0, off_Zl = 0, off_Yb[3] = {0, 0, 0},
          off_Zb[3] = {0, 0, 0};
   size_t off_Lbh = 0, off_Lbl = 0;  // TF32 split of L_b (k x k, ld round_up(k, 4))
@@ -136,7 +139,8 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p,
   if (prec == RLU_PREC_F64) {
     p.dt = RLU_F64;
     p.esz = 8;
-  } else if (prec == RLU_PREC_F32 || prec == RLU_PREC_MIXED || prec == RLU_PREC_BF16) {
+  } else if (prec == RLU_PREC_F32 || prec == RLU_PREC_MIXED || prec == RLU_PREC_BF16 ||
+             prec == RLU_PREC_FP8) {
     p.dt = RLU_F32;  // the path's type: Y, L~, the LUs, L and U (A may be BF16)
     p.esz = 4;
   } else {
@@ -155,19 +159,21 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p,
     p.split_y = umma3_splits(m, n, l);
   }
   if (prec == RLU_PREC_BF16) p.split_y = umma_bf16_splits(m, n, l, 256);
+  if (prec == RLU_PREC_FP8) p.split_y = umma_fp8_splits(m, n, l);
+  const bool bf16_like = prec == RLU_PREC_BF16 || prec == RLU_PREC_FP8;
   p.split_g = split_for(k, k, m, bm, bn);
   if (p.dt == RLU_F32 && p.split_g < 2) p.split_g = 2;  // FP32 partials, FP64 reduction
   p.split_c = split_for(k, n, m, bm, bn);
-  if (prec == RLU_PREC_MIXED || prec == RLU_PREC_BF16) {
+  if (prec == RLU_PREC_MIXED || bf16_like) {
     p.split_g = umma3_splits(k, m, k);
     p.split_c = umma3_splits(n, m, k);
   }
-  if (prec == RLU_PREC_BF16) p.split_c = umma_bf16_splits(k, m, n, 256);
+  if (bf16_like) p.split_c = umma_bf16_splits(k, m, n, 256);
   // power iterations: Z = A^T Y (as C, with l columns of Y) and Y = A Z (as Y)
   p.split_z = split_for(l, n, m, bm, bn);
   p.split_y3 = p.split_y;
   if (prec == RLU_PREC_MIXED) p.split_z = umma3_splits(n, m, l);
-  if (prec == RLU_PREC_BF16) {
+  if (bf16_like) {
     p.split_z = umma_bf16_splits(l, m, n, 256);
     p.split_y3 = umma_bf16_splits(m, n, l, 128);
   }
@@ -201,13 +207,13 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p,
   p.off_ps = carve(cur, (size_t)l * sizeof(int32_t));
   p.ldu12 = round_up(l, 4);  // the LUs' solved pivot rows, dense (<= 96 rows of <= l columns)
   p.off_u12 = carve(cur, (size_t)96 * p.ldu12 * e);
-  if (prec == RLU_PREC_MIXED || prec == RLU_PREC_BF16) {
+  if (prec == RLU_PREC_MIXED || bf16_like) {
     p.off_Lhi = carve(cur, (size_t)p.ldl * k * e);
     p.off_Llo = carve(cur, (size_t)p.ldl * k * e);
     p.off_Lbh = carve(cur, (size_t)round_up(k, 4) * k * 4);
     p.off_Lbl = carve(cur, (size_t)round_up(k, 4) * k * 4);
   }
-  if (prec == RLU_PREC_BF16) {  // L~ in three BF16 parts for the products with BF16 A
+  if (bf16_like) {  // L~ in three BF16 parts for the products with BF16 A
     p.off_Bh = carve(cur, (size_t)p.ldl * k * 2);
     p.off_Bm = carve(cur, (size_t)p.ldl * k * 2);
     p.off_Bl = carve(cur, (size_t)p.ldl * k * 2);
@@ -223,11 +229,20 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p,
       p.off_Zh = carve(cur, (size_t)p.ldg * l * 4);
       p.off_Zl = carve(cur, (size_t)p.ldg * l * 4);
     }
-    if (prec == RLU_PREC_BF16)
+    if (bf16_like)
       for (int t = 0; t < 3; ++t) {
         p.off_Yb[t] = carve(cur, (size_t)p.ldy * l * 2);
         p.off_Zb[t] = carve(cur, (size_t)p.ldg * l * 2);
       }
+  }
+  if (prec == RLU_PREC_FP8) {  // e4m3 A (m rows) and G (l rows) with their scales
+    p.ld8 = fp8_ld(n);
+    p.lds = ceil_div(n, 128);
+    p.lsg = ceil_div(l, 128);
+    p.off_A8 = carve(cur, (size_t)m * p.ld8);
+    p.off_SA = carve(cur, (size_t)m * p.lds);
+    p.off_G8 = carve(cur, (size_t)l * p.ld8);
+    p.off_SG = carve(cur, (size_t)p.lds * p.lsg);
   }
   p.total = cur;
   return true;
@@ -255,7 +270,9 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
   T* Lb = reinterpret_cast<T*>(ws + p.off_Lb);
   void* part = ws + p.off_part;
   const T* A = static_cast<const T*>(Av);  // FP32/FP64 storage (BF16: only Av is read)
-  const bool bf16 = p.prec == RLU_PREC_BF16;
+  // the FP8 form shares the BF16 form's products after step 2
+  const bool fp8 = p.prec == RLU_PREC_FP8;
+  const bool bf16 = p.prec == RLU_PREC_BF16 || fp8;
   const int64_t m = p.m, n = p.n;
   const int k = p.k, l = p.l;
 
@@ -263,10 +280,14 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
   if (info) RLU_TRY(info_init(info, s));
   // step 1
   RLU_TRY(tm.rec(0, false, s));
-  RLU_TRY(launch_gaussian(seed, 0, n, l, bf16 ? RLU_BF16 : p.dt, G, p.ldg, s));
+  RLU_TRY(launch_gaussian(seed, 0, n, l, (bf16 && !fp8) ? RLU_BF16 : p.dt, G, p.ldg, s));
+  if (fp8)  // e4m3 G with one scale per 128 x 128 block
+    RLU_TRY(fp8_quantize_g(reinterpret_cast<const float*>(G), p.ldg, n, l,
+                           reinterpret_cast<uint8_t*>(ws + p.off_G8), p.ld8,
+                           reinterpret_cast<uint8_t*>(ws + p.off_SG), p.lsg, s));
   RLU_TRY(tm.rec(0, true, s));
   if (st && st->G) {
-    if (bf16)
+    if (bf16 && !fp8)
       RLU_TRY(copy_cm<__nv_bfloat16>(reinterpret_cast<const __nv_bfloat16*>(G), p.ldg,
                                      static_cast<__nv_bfloat16*>(st->G), n, n, l, s));
     else
@@ -276,7 +297,30 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
   RLU_TRY(tm.rec(1, false, s));
   // the tensor-core projection reads A with TMA: rows must start on 16-byte boundaries
   const bool tma_ok = ((uintptr_t)A & 15u) == 0 && (lda * (int64_t)sizeof(T)) % 16 == 0;
-  if (bf16) {  // BF16 A and G, FP32 accumulation (validated: A rows 16-byte aligned)
+  if (fp8) {  // e4m3 A (one scale per row and 128 columns) times e4m3 G, FP32 accumulation
+    uint8_t* A8 = reinterpret_cast<uint8_t*>(ws + p.off_A8);
+    uint8_t* SA = reinterpret_cast<uint8_t*>(ws + p.off_SA);
+    RLU_TRY(fp8_quantize_a(Av, lda, m, n, A8, p.ld8, SA, p.lds, s));
+    Fp8Op op{};
+    op.A8 = A8;
+    op.lda8 = p.ld8;
+    op.SA = SA;
+    op.lds = p.lds;
+    op.G8 = reinterpret_cast<const uint8_t*>(ws + p.off_G8);
+    op.ldg8 = p.ld8;
+    op.SG = reinterpret_cast<const uint8_t*>(ws + p.off_SG);
+    op.lsg = p.lsg;
+    op.M = m;
+    op.N = l;
+    op.K = n;
+    op.out = reinterpret_cast<float*>(Y);
+    op.ldo = p.ldy;
+    op.out_colmajor = true;
+    op.splits = p.split_y;
+    op.partial = reinterpret_cast<float*>(part);
+    op.status = info ? &info->status : nullptr;
+    RLU_TRY(umma_fp8_y(op, s));
+  } else if (bf16) {  // BF16 A and G, FP32 accumulation (validated: A rows 16-byte aligned)
     UmmaBf16Op op{};
     op.A = Av;
     op.lda = lda;
@@ -624,13 +668,13 @@ int32_t validate(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda
   if (prec == RLU_PREC_F64 && dtype != RLU_F64) return RLU_EUNSUPPORTED;
   if ((prec == RLU_PREC_F32 || prec == RLU_PREC_MIXED) && dtype != RLU_F32)
     return RLU_EUNSUPPORTED;
-  if (prec == RLU_PREC_BF16) {
+  if (prec == RLU_PREC_BF16 || prec == RLU_PREC_FP8) {
     if (dtype != RLU_BF16) return RLU_EUNSUPPORTED;
     // the BF16 products read A with TMA: rows on 16-byte boundaries
     if (((uintptr_t)A & 15u) != 0 || lda % 8 != 0) return RLU_EINVAL;
   }
   if (prec != RLU_PREC_F64 && prec != RLU_PREC_F32 && prec != RLU_PREC_MIXED &&
-      prec != RLU_PREC_BF16)
+      prec != RLU_PREC_BF16 && prec != RLU_PREC_FP8)
     return RLU_EUNSUPPORTED;
   return RLU_OK;
 }

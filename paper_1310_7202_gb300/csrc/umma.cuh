@@ -84,6 +84,35 @@ struct UmmaBf16Op {
   int32_t* status;
 };
 int32_t umma_bf16_gemm(int mode, const UmmaBf16Op& op, cudaStream_t s);
+// FP8 e4m3 projection with per-tile power-of-two scales (see umma_fp8.cu).
+// A8: M x K e4m3 (lda8 bytes per row, K zero-padded to a multiple of 128), SA: one UE8M0
+// byte per row and 128-column block (lds per row); G8: N x K e4m3 (row j = column j of G,
+// ldg8 bytes), SG: one byte per 128 x 128 block (lsg per K block). out = A8 G8^T, FP32.
+struct Fp8Op {
+  const uint8_t* A8;
+  int64_t lda8;
+  const uint8_t* SA;
+  int64_t lds;
+  const uint8_t* G8;
+  int64_t ldg8;
+  const uint8_t* SG;
+  int64_t lsg;
+  int64_t M, N, K;
+  float* out;
+  int64_t ldo;
+  bool out_colmajor;
+  int splits;
+  float* partial;
+  int32_t* status;
+};
+int64_t fp8_ld(int64_t K);  // bytes per row of an e4m3 operand with K columns
+int32_t fp8_quantize_a(const void* A, int64_t lda, int64_t M, int64_t K, uint8_t* A8,
+                       int64_t ld8, uint8_t* SA, int64_t lds, cudaStream_t s);
+int32_t fp8_quantize_g(const float* G, int64_t ldg, int64_t K, int64_t N, uint8_t* G8,
+                       int64_t ld8, uint8_t* SG, int64_t lsg, cudaStream_t s);
+int32_t umma_fp8_y(const Fp8Op& op, cudaStream_t s);
+int umma_fp8_splits(int64_t M, int64_t K, int64_t N);
+
 // split-K factor that fills the SMs for an M x N output (N tiles of bn columns)
 int umma_bf16_splits(int64_t M, int64_t K, int64_t N, int bn);
 int umma3_splits(int64_t M, int64_t K, int64_t N);

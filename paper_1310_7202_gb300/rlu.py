@@ -18,13 +18,14 @@ LIB_PATH = os.path.join(_PKG, "librlu.so")
 
 RLU_OK, RLU_EINVAL, RLU_ENOMEM, RLU_EUNSUPPORTED, RLU_ECUDA = 0, 1, 2, 3, 4
 RLU_F64, RLU_F32, RLU_BF16 = 0, 1, 2
-RLU_PREC_F64, RLU_PREC_F32, RLU_PREC_MIXED, RLU_PREC_BF16 = 0, 1, 2, 3
+RLU_PREC_F64, RLU_PREC_F32, RLU_PREC_MIXED, RLU_PREC_BF16, RLU_PREC_FP8 = 0, 1, 2, 3, 4
 
 PREC_BY_NAME = {"f64": RLU_PREC_F64, "f32": RLU_PREC_F32, "mixed": RLU_PREC_MIXED,
-                "bf16": RLU_PREC_BF16}
+                "bf16": RLU_PREC_BF16, "fp8": RLU_PREC_FP8}
 _DT_OF_TORCH = {torch.float64: RLU_F64, torch.float32: RLU_F32, torch.bfloat16: RLU_BF16}
 _TORCH_OF_PREC = {RLU_PREC_F64: torch.float64, RLU_PREC_F32: torch.float32,
-                  RLU_PREC_MIXED: torch.float32, RLU_PREC_BF16: torch.float32}
+                  RLU_PREC_MIXED: torch.float32, RLU_PREC_BF16: torch.float32,
+                  RLU_PREC_FP8: torch.float32}
 
 # Every symbol include/*.h declares.
 EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian",
