@@ -1,6 +1,7 @@
 """FP64 CPU oracle for the randomized LU decomposition (Shabat, Shmueli, Aizenbud,
 Averbuch, "Randomized LU Decomposition", Algorithm 1, with power iterations and the
-rank-deficient least squares of Algorithm 3) and its fast variant (Algorithm 4, complex128).
+rank-deficient least squares of Algorithm 3), its fast variant (Algorithm 4, complex128)
+and the orthogonal-basis range finder of Algorithm 2, the comparator of Section 5.
 
 TEST INFRASTRUCTURE ONLY. Nothing in the product path imports this package: only
 ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
@@ -18,6 +19,7 @@ from .rlu_oracle import (  # noqa: F401
     box_muller_f32, gaussian_f32,
     lu_partial_pivot, lu_column_pivot, pinv_apply, project,
     rlu_factor, reconstruct_error, spectral_norm, rdls_apply, rdls_solve,
+    lu_normalize, randomized_orth, orth_error, halko_bound,
     theorem1_constant, theorem1_success_probability, theorem1_failure_terms,
     check_dims,
 )

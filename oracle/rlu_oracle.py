@@ -482,6 +482,51 @@ def reconstruct_error(A, P, Q, L, U, spectral: bool = True):
 
 
 # ---------------------------------------------------------------------------------------
+# Algorithm 2 (alg:randomized_orth, Section 4.3): the randomized range finder with an
+# orthogonal basis, the comparator of the error experiment of Section 5.
+# ---------------------------------------------------------------------------------------
+
+def randomized_orth(A: np.ndarray, k: int, l: int, seed: int, stream_id: int = 0,
+                    G: np.ndarray | None = None) -> dict:
+    """Algorithm 2: G (n x l) Gaussian (step 1, the same generator as Algorithm 1), Y = A G
+    (step 2), U = the left singular vectors of Y (step 3, LAPACK SVD as a library step),
+    Q = its first k columns (step 4), so that Q^T Q = I and ||Q Q^T A - A|| is bounded.
+    Also returns B = Q^T A (A ~ Q B, the rank-k approximation whose error Section 5
+    compares with the randomized LU's) and the singular values of Y."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    check_dims(m, n, k, l)
+    if G is None:
+        G = gaussian(seed, stream_id, n, l)                 # step 1
+    Y = A @ G                                               # step 2
+    Uy, sy, _ = np.linalg.svd(Y, full_matrices=False)       # step 3
+    Q = Uy[:, :k]                                           # step 4
+    return dict(Q=Q, B=Q.T @ A, sigma_y=sy, G=G, Y=Y)
+
+
+def orth_error(A: np.ndarray, Q: np.ndarray, B: np.ndarray | None = None, spectral=True):
+    """(||Q B - A||_F, ||Q B - A||_2) with B = Q^T A unless given: ||Q Q^* A - A||."""
+    A = np.asarray(A, dtype=np.float64)
+    if B is None:
+        B = Q.T @ A
+    R = Q @ B - A
+    fro = float(np.linalg.norm(R))
+    return fro, (spectral_norm(R) if spectral else float("nan"))
+
+
+def halko_bound(sigma: np.ndarray, k: int, l: int) -> float:
+    """The bound of Corollary 10.9 of Halko, Martinsson and Tropp that Section 4.3 quotes
+    for Algorithm 2 (p = l - k >= 4, failure probability at most 6 e^{-p}):
+    (1 + 17 sqrt(1 + k/p)) sigma_{k+1} + 8 sqrt(k + p) / (p + 1) (sum_{j>k} sigma_j^2)^{1/2}."""
+    p = l - k
+    if p < 4:
+        raise ValueError("the bound needs p = l - k >= 4")
+    s = np.asarray(sigma, dtype=np.float64)
+    return float((1.0 + 17.0 * math.sqrt(1.0 + k / p)) * s[k]
+                 + 8.0 * math.sqrt(k + p) / (p + 1.0) * math.sqrt(float(np.sum(s[k:] ** 2))))
+
+
+# ---------------------------------------------------------------------------------------
 # the error theorem of Section 4 (trm:rand_lu_err): error constant and success probability xi.
 # ---------------------------------------------------------------------------------------
 

@@ -531,3 +531,67 @@ def test_gaussian_f32_distribution_and_layout():
     # same uniforms, up to the FP32 uniform's 24-bit resolution)
     G64 = O.gaussian(77, 0, 1000, 1000)
     assert np.median(np.abs(G - G64)) < 1e-5
+
+
+# ----------------------------------------------------------------------------------------
+# Algorithm 2 (randomized range finder with an orthogonal basis), the comparator of the
+# error experiment of Section 5.
+# ----------------------------------------------------------------------------------------
+
+def test_randomized_orth_closed_form():
+    """A = U diag(sigma) V^T and G = V[:, :l] (a fixed test matrix in place of the Gaussian)
+    give Y = U[:, :l] diag(sigma_1..l): the top-k left singular vectors of Y are U[:, :k], so
+    Q Q^T = U_k U_k^T and the errors are the optimal rank-k ones, sqrt(sum_{i>k} sigma_i^2)
+    (Frobenius) and sigma_{k+1} (spectral). Taking the last k columns, A^T for A, or a G
+    of the wrong side breaks each equality."""
+    rng = np.random.default_rng(11)
+    m, n, k, l = 60, 45, 6, 10
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sigma = np.sort(rng.uniform(0.1, 2.0, n))[::-1]
+    A = (U * sigma) @ V.T
+    r = O.randomized_orth(A, k, l, seed=0, G=V[:, :l].copy())
+    assert np.abs(r["Q"] @ r["Q"].T - U[:, :k] @ U[:, :k].T).max() <= 1e-12
+    assert np.abs(r["sigma_y"] - sigma[:l]).max() <= 1e-12
+    fro, spec = O.orth_error(A, r["Q"])
+    assert abs(fro - np.sqrt(np.sum(sigma[k:] ** 2))) <= 1e-12
+    assert abs(spec - sigma[k]) <= 1e-12
+
+
+def test_randomized_orth_exact_rank_and_orthonormal_basis():
+    m, n, k, l = 120, 90, 10, 16
+    A = synth.prescribed_matrix(m, n, synth.spectrum("rank_k", min(m, n), k), 3, 4)
+    r = O.randomized_orth(A, k, l, seed=5)
+    assert np.abs(r["Q"].T @ r["Q"] - np.eye(k)).max() <= 1e-13
+    assert np.abs(r["B"] - r["Q"].T @ A).max() <= 1e-13
+    fro, _ = O.orth_error(A, r["Q"], spectral=False)
+    assert fro / np.linalg.norm(A) < 1e-13
+
+
+@pytest.mark.parametrize("spec", ["paper_exp", "paper_slow", "inv_square"])
+def test_randomized_orth_bounds(spec):
+    """Eckart-Young: no rank-k Q reaches below sigma_{k+1}; the bound of Corollary 10.9 of
+    Halko et al. quoted in Section 4.3 holds (failure probability 6 e^{-10} < 3e-4 per
+    draw at p = 10)."""
+    m = n = 200
+    sigma = synth.spectrum(spec, n)
+    for seed in range(3):
+        A = synth.prescribed_matrix(m, n, sigma, 30 + seed, 40 + seed)
+        for k in (8, 25):
+            r = O.randomized_orth(A, k, k + 10, seed=seed)
+            _, spec2 = O.orth_error(A, r["Q"])
+            assert sigma[k] * (1 - 1e-9) <= spec2 <= O.halko_bound(sigma, k, k + 10)
+
+
+def test_randomized_lu_error_close_to_randomized_orth():
+    """Section 5 reports the randomized LU and the randomized SVD errors as almost identical
+    on an exponentially decaying spectrum; here their ratio stays within [1/3, 3]."""
+    m = n = 300
+    sigma = synth.spectrum("paper_exp", n)
+    A = synth.prescribed_matrix(m, n, sigma, 7, 8)
+    for k in (10, 20, 40):
+        r = O.randomized_orth(A, k, k + 3, seed=2)
+        _, e_svd = O.orth_error(A, r["Q"])
+        lu = O.rlu_factor(A, k, k + 3, seed=2)
+        _, e_lu = O.reconstruct_error(A, lu["P"], lu["Q"], lu["L"], lu["U"])
+        assert 1 / 3 <= e_lu / e_svd <= 3, (k, e_lu, e_svd)
