@@ -229,6 +229,32 @@ int32_t rlu_lstsq(int32_t dtype, int64_t m, int64_t n, int32_t k, const int32_t*
                   const void* b, int64_t ldb, int32_t nrhs, void* x, int64_t ldx,
                   rlu_info* info, void* workspace, size_t ws_bytes, void* stream);
 
+/* Algorithm 2 (alg:randomized_orth, Section 4.3): the randomized range finder with an
+ * orthogonal basis, the accuracy comparator ("randomized SVD") of the error experiment of
+ * Section 5. Step 1 draws G (n x l) as step 1 of Algorithm 1 does (FP64 transform, stream
+ * id 0), step 2 forms Y = A G, step 3 takes the left singular vectors of Y from the
+ * eigenpairs of the FP64 Gram matrix Y^T Y (parallel cyclic Jacobi: U_y = Y V diag(lambda)^-1/2),
+ * step 4 keeps the k with the largest singular values: Q (m x k, column-major, ldq >= m,
+ * orthonormal columns). Also returns B = Q^T A (k x n, row-major, ldb >= n), so that
+ * ||Q B - A|| = ||Q Q^T A - A|| is the comparator's rank-k error (rlu_reconstruct_error
+ * with identity permutations, L = Q, U = B), and sigma (l doubles, may be NULL): the
+ * singular values of Y in decreasing order.
+ *   dtype: RLU_F64 only (the comparison runs in double precision, as the paper's does).
+ *   1 <= k <= l <= min(m, n), l <= 4096.
+ *   info: device rlu_info (may be NULL): status RLU_EINVAL when Y has fewer than k singular
+ *         values above the resolution of the Gram route (an eigenvalue of Y^T Y at or below
+ *         64 eps lambda_max, i.e. sigma_j(Y) below about 1e-7 sigma_1(Y), is rounding noise:
+ *         its sigma is returned as 0 and its column of Q is zero); RLU_ETIMEOUT when a grid
+ *         barrier of the eigensolver gave up.
+ *   workspace: rlu_rsvd_workspace_size bytes, 256-byte aligned.
+ * Errors: RLU_EINVAL (dimensions, NULL pointers, strides), RLU_EUNSUPPORTED (dtype),
+ * RLU_ENOMEM, RLU_ECUDA. Asynchronous on stream. */
+size_t rlu_rsvd_workspace_size(int64_t m, int64_t n, int32_t k, int32_t l);
+int32_t rlu_rsvd(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
+                 int32_t l, uint64_t seed, void* Q, int64_t ldq, void* B, int64_t ldb,
+                 double* sigma, rlu_info* info, void* workspace, size_t ws_bytes,
+                 void* stream);
+
 /* Bytes of workspace rlu_reconstruct_error needs. */
 size_t rlu_reconstruct_workspace_size(int64_t m, int64_t n, int32_t k);
 

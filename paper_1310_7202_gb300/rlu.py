@@ -31,7 +31,8 @@ _TORCH_OF_PREC = {RLU_PREC_F64: torch.float64, RLU_PREC_F32: torch.float32,
 EXPORTED = ("rlu_version", "rlu_status_string", "rlu_philox_u32", "rlu_gaussian",
             "rlu_workspace_size", "rlu_factor", "rlu_factor_stages", "rlu_timed_step_name",
             "rlu_launch_count", "rlu_reconstruct_workspace_size", "rlu_reconstruct_error",
-            "rlu_reconstruct_error_static", "rlu_server_create", "rlu_server_submit",
+            "rlu_reconstruct_error_static", "rlu_rsvd_workspace_size", "rlu_rsvd",
+            "rlu_server_create", "rlu_server_submit",
             "rlu_server_poll", "rlu_server_wait_all", "rlu_server_stats", "rlu_server_destroy",
             "rlu_batch_workspace_size", "rlu_batch_create", "rlu_factor_batched",
             "rlu_batch_launches", "rlu_batch_destroy", "rlu_workspace_size_power",
@@ -131,6 +132,11 @@ def load_library(require_cuda: bool = True) -> ctypes.CDLL:
     lib.rlu_reconstruct_error_static.restype = i32
     lib.rlu_reconstruct_error_static.argtypes = [vp, i32, i64, i64, i64, i32, vp, vp, vp, i64,
                                                  vp, i64, i32, vp, vp, i32, vp]
+    lib.rlu_rsvd_workspace_size.restype = sz
+    lib.rlu_rsvd_workspace_size.argtypes = [i64, i64, i32, i32]
+    lib.rlu_rsvd.restype = i32
+    lib.rlu_rsvd.argtypes = [vp, i32, i64, i64, i64, i32, i32, u64, vp, i64, vp, i64, vp, vp,
+                             vp, sz, vp]
     lib.rlu_server_create.restype = i32
     lib.rlu_server_create.argtypes = [sz, i32, ctypes.POINTER(vp)]
     lib.rlu_server_submit.restype = i32
@@ -408,6 +414,28 @@ def reconstruct_error(A: torch.Tensor, P: torch.Tensor, Q: torch.Tensor, L: torc
                                      ws.numel(), _stream_ptr(stream)),
            "rlu_reconstruct_error")
     return out[0], (out[1] if power_iters > 0 else None)
+
+
+def rsvd(A: torch.Tensor, k: int, l: int, seed: int, stream=None) -> dict:
+    """Algorithm 2 (the comparator of Section 5) on an FP64 row-major CUDA tensor A: Q
+    (m x k, column-major, orthonormal), B = Q^T A (k x n), sigma (the l singular values of
+    Y = A G, decreasing) and info (device tensors)."""
+    lib = load_library()
+    m, n = A.shape
+    if A.dtype != torch.float64 or A.stride(1) != 1 or A.device.type != "cuda":
+        raise RluError("A must be a row-major FP64 CUDA tensor")
+    ws_n = lib.rlu_rsvd_workspace_size(m, n, k, l)
+    if ws_n == 0:
+        raise RluError(f"invalid sizes m={m} n={n} k={k} l={l}")
+    ws = torch.empty(ws_n, dtype=torch.uint8, device="cuda")
+    Q = _colmajor(m, k, torch.float64)
+    B = torch.empty((k, n), dtype=torch.float64, device="cuda")
+    sigma = torch.empty(l, dtype=torch.float64, device="cuda")
+    info = torch.empty(4, dtype=torch.int32, device="cuda")
+    _check(lib.rlu_rsvd(_dev_ptr(A), RLU_F64, m, n, A.stride(0), k, l, seed, _dev_ptr(Q),
+                        Q.stride(1), _dev_ptr(B), B.stride(0), _dev_ptr(sigma), _dev_ptr(info),
+                        _dev_ptr(ws), ws_n, _stream_ptr(stream)), "rlu_rsvd")
+    return {"Q": Q, "B": B, "sigma": sigma, "info": info, "_ws": ws}
 
 
 def reconstruct_error_static(A: torch.Tensor, P: torch.Tensor, Q: torch.Tensor,
