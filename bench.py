@@ -760,6 +760,7 @@ def run_ours(args):
             "c4_batch4096": batched_measure("batch4096", ["mixed", "f32"], K, W,
                                             oracle_sample=8),
         }
+        line["error_comparison"] = error_comparison()
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -890,6 +891,51 @@ def batched_measure(wname: str, precs, K: int, W: int, oracle_sample: int = 0) -
     del probs
     torch.cuda.empty_cache()
     return line
+
+
+def error_comparison(ks=(10, 20, 40, 60, 100), reps: int = 5) -> dict:
+    """The error experiment of Section 5: 3000 x 3000 with exponentially decaying singular
+    values (sigma_i = e^{-(i-1)/10}), l = k + 3; the randomized LU (FP64 path) against
+    Algorithm 2 (the orthogonal-basis range finder, FP64) in the spectral norm (200 power
+    iterations of the error measure) and in time, with sigma_{k+1} beside them."""
+    from paper_1310_7202_gb300 import rlu
+
+    m = n = 3000
+    sigma = synth.spectrum("paper_exp", n)
+    A = synth.prescribed_matrix_torch(m, n, sigma, 51, 52, torch.float64)
+    ident_m = torch.arange(m, dtype=torch.int32, device="cuda")
+    ident_n = torch.arange(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for k in ks:
+        l = k + 3
+        fz = rlu.Factorizer(m, n, k, l, "f64")
+        fz(A, 7)
+        rlu.rsvd(A, k, l, 7)
+        torch.cuda.synchronize()
+        t = {}
+        for name, fn in (("lu", lambda: fz(A, 7)), ("svd", lambda: rlu.rsvd(A, k, l, 7))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t[name] = e0.elapsed_time(e1) / reps
+        P, Q, L, U, _ = fz(A, 7)
+        r = rlu.rsvd(A, k, l, 7)
+        _, e_lu = rlu.reconstruct_error(A, P, Q, L, U, power_iters=200)
+        _, e_svd = rlu.reconstruct_error(A, ident_m, ident_n, r["Q"], r["B"], power_iters=200)
+        torch.cuda.synchronize()
+        rows.append({"k": k, "l": l, "sigma_k1": float(sigma[k]), "rlu_spec": e_lu.item(),
+                     "rsvd_spec": e_svd.item(), "ratio": e_lu.item() / e_svd.item(),
+                     "rlu_ms": t["lu"], "rsvd_ms": t["svd"], "rsvd_info": r["info"].cpu().tolist()})
+        del fz, r
+    torch.cuda.empty_cache()
+    return {"workload": "3000 x 3000, sigma_i = e^{-(i-1)/10}, l = k + 3, FP64 (the error "
+                        "experiment of Section 5)", "rows": rows,
+            "note": "errors ||PAQ - LU||_2 and ||Q Q^T A - A||_2 (power-iteration estimates "
+                    "on the GPU); times per factorization, CUDA events"}
 
 
 def run_batched(args):
