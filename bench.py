@@ -54,6 +54,9 @@ def parse_args():
     ap.add_argument("--serve-lambdas", default="300,1000,3000",
                     help="Poisson arrival rates (requests/s) of the serving measurement")
     ap.add_argument("--serve-secs", type=float, default=2.0, help="arrival window per rate")
+    ap.add_argument("--streams", type=int, default=2,
+                    help="factorizations in flight in the timed throughput pass (each on its "
+                         "own stream with its own workspace and input buffer)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads' sub-keys of the default line (the FP64 "
                          "512^2, BF16 32768x16384 and 4096-problem batched workloads)")
@@ -440,31 +443,59 @@ def run_ours(args):
         fz(A, w["seed_g"])
     torch.cuda.synchronize()
     barrier(world)
-    launches0 = rlu.launch_count()
+    # ---- one factorization at a time (latency, and the per-step events of the roofline) --
     t_start = torch.cuda.Event(enable_timing=True)
     t_stop = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(K):
+        fz(A, w["seed_g"], stages={"events": evs[i]})
+    t_stop.record(stream)
+    torch.cuda.synchronize()
+    lat_ms = t_start.elapsed_time(t_stop) / K
+    stage_ms = {names[i]: statistics.mean(evs[s][2 * i].elapsed_time(evs[s][2 * i + 1])
+                                          for s in range(K)) for i in range(ns)}
+
+    # ---- the timed throughput pass: K factorizations, S in flight -------------------------
+    # A caller with a stream of matrices keeps several factorizations in flight: while one
+    # runs its latency-bound pivoted LUs on one thread-block cluster, another's products
+    # fill the other SMs. Step i runs on stream i % S with its own factorizer (workspace,
+    # outputs) and its own input buffer (a copy of the workload's matrix).
+    S = max(1, args.streams)
+    fzs = [fz] + [rlu.Factorizer(m, n, k, l, prec) for _ in range(S - 1)]
+    As = [A] + [A.clone() for _ in range(S - 1)]
+    streams = [stream] + [torch.cuda.Stream() for _ in range(S - 1)]
+    for i in range(2 * S):
+        fzs[i % S](As[i % S], w["seed_g"], stream=streams[i % S])
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = rlu.launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_ends = [torch.cuda.Event(enable_timing=True) for _ in range(S)]
     with ClockSampler(local) as clocks:
         torch.cuda.synchronize()
         barrier(world)
         t_start.record(stream)
+        for st_ in streams[1:]:
+            st_.wait_event(t_start)
         for i in range(K):
-            fz(A, w["seed_g"], stages={"events": evs[i]})
-        t_stop.record(stream)
+            fzs[i % S](As[i % S], w["seed_g"], stream=streams[i % S])
+        for j in range(S):
+            t_ends[j].record(streams[j])
         torch.cuda.synchronize()
         barrier(world)
     launches = rlu.launch_count() - launches0
-    ms = t_start.elapsed_time(t_stop)
+    ms = max(t_start.elapsed_time(e) for e in t_ends)
     ms_max = max_over_ranks(ms, world, dev)
     value = whole_job_rate(K, world, ms_max)
-    stage_ms = {names[i]: statistics.mean(evs[s][2 * i].elapsed_time(evs[s][2 * i + 1])
-                                          for s in range(K)) for i in range(ns)}
+    del fzs[1:], As[1:]
 
     # ---- end to end through the public API: host input in, host factors out ----------
     # Every step copies its A from pinned host memory and its factors back. Steps are
-    # pipelined as a user streaming matrices would run them: two device buffers and two
-    # factorizers alternate, the copy of step i + 1's A (its own stream) overlaps the
-    # factorization of step i, and each step's factors are copied back right after it.
-    nbuf = 2
+    # pipelined as a user streaming matrices would run them: S device buffers and S
+    # factorizers on S compute streams alternate (as in the throughput pass), the copy of
+    # step i + 1's A (its own stream) overlaps the factorizations in flight, and each step's
+    # factors are copied back on its compute stream right after it.
+    nbuf = S
     A_pin = [torch.empty((m, n), dtype=A.dtype, pin_memory=True) for _ in range(nbuf)]
     for ap_ in A_pin:
         ap_.copy_(A)
@@ -477,6 +508,7 @@ def run_ours(args):
     h2d = A.numel() * A.element_size()
     d2h = sum(t.numel() * t.element_size() for t in outs[0].values())
     copy_stream = torch.cuda.Stream()
+    cstreams = [stream] + [torch.cuda.Stream() for _ in range(nbuf - 1)]
     copied = [torch.cuda.Event() for _ in range(nbuf)]
     consumed = [torch.cuda.Event() for _ in range(nbuf)]
     for e in consumed:
@@ -491,16 +523,18 @@ def run_ours(args):
 
     def e2e_step(i, last):
         b = i % nbuf
+        cs = cstreams[b]
         if not last:
             e2e_issue_copy(i + 1)
-        stream.wait_event(copied[b])
-        P, Q, L, U, info = fze[b](A_dev[b], w["seed_g"])
-        consumed[b].record(stream)
+        cs.wait_event(copied[b])
+        P, Q, L, U, info = fze[b](A_dev[b], w["seed_g"], stream=cs)
+        consumed[b].record(cs)
         o = outs[b]
-        o["P"].copy_(P, non_blocking=True)
-        o["Q"].copy_(Q, non_blocking=True)
-        o["L"].copy_(L, non_blocking=True)
-        o["U"].copy_(U, non_blocking=True)
+        with torch.cuda.stream(cs):
+            o["P"].copy_(P, non_blocking=True)
+            o["Q"].copy_(Q, non_blocking=True)
+            o["L"].copy_(L, non_blocking=True)
+            o["U"].copy_(U, non_blocking=True)
 
     e2e = None
     if not args.no_e2e:
@@ -510,20 +544,24 @@ def run_ours(args):
             e2e_step(i, i == nw - 1)
         torch.cuda.synchronize()
         barrier(world)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1s = [torch.cuda.Event(enable_timing=True) for _ in range(nbuf)]
         e0.record(stream)
         copy_stream.wait_event(e0)            # the first copy is inside the timed region
+        for cs in cstreams[1:]:
+            cs.wait_event(e0)
         e2e_issue_copy(0)
         for i in range(K):
             e2e_step(i, i == K - 1)
-        e1.record(stream)
+        for j in range(nbuf):
+            e1s[j].record(cstreams[j])
         torch.cuda.synchronize()
         barrier(world)
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e_ms = max_over_ranks(max(e0.elapsed_time(e) for e in e1s), world, dev)
         e2e = {"value": whole_job_rate(K, world, e2e_ms), "unit": "LU/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
-               "note": "two device buffers and factorizers; the copy of the next step's A "
-                       "overlaps the current factorization"}
+               "note": f"{nbuf} device buffers, factorizers and compute streams; the copy of "
+                       "the next step's A overlaps the factorizations in flight"}
     del fze[1:]
 
     # ---- accuracy of the last factorization (outside the timed region) -----------------
@@ -600,38 +638,35 @@ def run_ours(args):
         Pp, Qp, Lp, Up, _ = fp(A32, w["seed_g"])
         fro_p, _ = rlu.reconstruct_error(A, Pp, Qp, Lp, Up)
         torch.cuda.synchronize()
-        del A32
-        plain = {"value": 1e3 / pms, "unit": "LU/s", "ms_per_step": pms,
+        # the plain path with the same S factorizations in flight, as the headline pass
+        fps = [fp] + [rlu.Factorizer(m, n, k, l, "f32") for _ in range(S - 1)]
+        A32s = [A32] + [A32.clone() for _ in range(S - 1)]
+        reps = max(2 * S, K // 2)
+        for i in range(S):
+            fps[i](A32s[i], w["seed_g"], stream=streams[i])
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1s = [torch.cuda.Event(enable_timing=True) for _ in range(S)]
+        q0.record(stream)
+        for st_ in streams[1:]:
+            st_.wait_event(q0)
+        for i in range(reps):
+            fps[i % S](A32s[i % S], w["seed_g"], stream=streams[i % S])
+        for j in range(S):
+            q1s[j].record(streams[j])
+        torch.cuda.synchronize()
+        pms_s = max(q0.elapsed_time(e) for e in q1s) / reps
+        del A32, A32s, fps
+        plain = {"value": 1e3 / pms_s, "unit": "LU/s", "ms_per_step": pms_s,
+                 "in_flight": S, "single_stream": {"value": 1e3 / pms, "ms_per_step": pms},
                  "gemm_tflops": 2.0 * m * n * (l + k) / (pg / 1e3) / 1e12,
-                 "fro": fro_p.item(), "speedup": (1e3 / (ms_max / K)) / (1e3 / pms),
-                 "speedup_of": prec}
+                 "fro": fro_p.item(), "speedup": (1e3 / (ms_max / K)) / (1e3 / pms_s),
+                 "speedup_single_stream": pms / lat_ms, "speedup_of": prec}
         del fp
 
-    # ---- two factorizations in flight (two streams, own buffers): the LU latency of one
-    # overlaps the products of the other ---------------------------------------------
-    two = None
-    if prec in ("mixed", "bf16", "fp8"):
-        fzb = rlu.Factorizer(m, n, k, l, prec)
-        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-        fzs = [fz, fzb]
-        for i in range(4):
-            with torch.cuda.stream(streams[i % 2]):
-                fzs[i % 2](A, w["seed_g"], stream=streams[i % 2])
-        torch.cuda.synchronize()
-        t0e = torch.cuda.Event(enable_timing=True)
-        t1e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        t0e.record(streams[0])
-        streams[1].wait_event(t0e)
-        for i in range(K):
-            fzs[i % 2](A, w["seed_g"], stream=streams[i % 2])
-        for j in range(2):
-            t1e[j].record(streams[j])
-        torch.cuda.synchronize()
-        span = max(t0e.elapsed_time(t1e[0]), t0e.elapsed_time(t1e[1]))
-        two = {"value": K / (span / 1e3), "unit": "LU/s", "ms_per_step": span / K,
-               "note": "K factorizations alternating over two streams, each with its own "
-                       "workspace and outputs; the same input"}
-        del fzb
+    # ---- one factorization at a time (the latency of one step) -------------------------
+    single = {"value": 1e3 / lat_ms, "unit": "LU/s", "ms_per_step": lat_ms,
+              "note": "K factorizations one after another on one stream: each one's latency"}
 
     # ---- Algorithm 3 (rank-deficient least squares) on the factors of the last run ----
     lstsq = None
@@ -734,10 +769,12 @@ def run_ours(args):
                             "f32": "SIMT GEMMs, cluster register LUs",
                             "f64": "FP64 SIMT GEMMs, cluster register LUs"}[prec],
                    "l2": f"inputs larger than L2 (A = {A.numel() * A.element_size() / 1e6:.0f} MB)",
-                   "parallelism": f"{world} independent replica(s)"},
+                   "parallelism": f"{world} independent replica(s)",
+                   "in_flight": f"{S} factorizations in flight (stream i % {S}, own workspace "
+                                "and input buffer each)"},
         "gemm_tflops": gemm_tflops,
         "plain_fp32": plain,
-        "two_in_flight": two,
+        "single_stream": single,
         "power": power,
         "lstsq": lstsq,
         "serve": serve,
@@ -945,6 +982,30 @@ def run_batched(args):
                                      oracle_sample=8)))
 
 
+def in_flight_rate(make, A: torch.Tensor, seed: int, reps: int, S: int = 2) -> float:
+    """Milliseconds per factorization with S in flight: factorization i on stream i % S with
+    its own factorizer (from make()) and its own copy of A."""
+    fzs = [make() for _ in range(S)]
+    As = [A] + [A.clone() for _ in range(S - 1)]
+    streams = [torch.cuda.current_stream()] + [torch.cuda.Stream() for _ in range(S - 1)]
+    for i in range(2 * S):
+        fzs[i % S](As[i % S], seed, stream=streams[i % S])
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = [torch.cuda.Event(enable_timing=True) for _ in range(S)]
+    t0.record(streams[0])
+    for st_ in streams[1:]:
+        st_.wait_event(t0)
+    for i in range(reps):
+        fzs[i % S](As[i % S], seed, stream=streams[i % S])
+    for j in range(S):
+        t1[j].record(streams[j])
+    torch.cuda.synchronize()
+    ms = max(t0.elapsed_time(e) for e in t1) / reps
+    del fzs, As
+    return ms
+
+
 def single_config(wname: str, K: int, W: int, peaks: dict, peak_kind: str) -> dict:
     """One single-matrix workload as a sub-key of the default line: factorizations/s on its
     default path, stage times, the dominant kernel's roofline, the GEMMs against their
@@ -1004,6 +1065,8 @@ def single_config(wname: str, K: int, W: int, peaks: dict, peak_kind: str) -> di
         if prec == "bf16":
             e["tensor_frac_of_bf16_peak"] = fl / t / 1e12 / peaks["bf16_tflops"]
         gemms[g_] = e
+    ms2 = in_flight_rate(lambda: rlu.Factorizer(m, n, k, l, prec), A, w["seed_g"],
+                         max(4, K))
     P, Q, L, U, info = fz(A, w["seed_g"])
     fro_d, spec_d = rlu.reconstruct_error(A, P, Q, L, U, power_iters=100)
     torch.cuda.synchronize()
@@ -1055,8 +1118,12 @@ def single_config(wname: str, K: int, W: int, peaks: dict, peak_kind: str) -> di
         Pp, Qp, Lp, Up, _ = fp(A32, w["seed_g"])
         fro_p, _ = rlu.reconstruct_error(A, Pp, Qp, Lp, Up)
         torch.cuda.synchronize()
-        plain = {"value": 1e3 / pms, "unit": "LU/s", "ms_per_step": pms, "fro": fro_p.item(),
-                 "speedup": pms / ms, "speedup_of": prec}
+        pms2 = in_flight_rate(lambda: rlu.Factorizer(m, n, k, l, "f32"), A32, w["seed_g"],
+                              max(4, reps))
+        plain = {"value": 1e3 / pms2, "unit": "LU/s", "ms_per_step": pms2, "in_flight": 2,
+                 "single_stream": {"value": 1e3 / pms, "ms_per_step": pms},
+                 "fro": fro_p.item(), "speedup": pms2 / ms2, "speedup_single_stream": pms / ms,
+                 "speedup_of": prec}
         del A32, fp
     fp8 = None
     if prec == "bf16":  # the FP8 variant of the projection on the same stored A
@@ -1089,7 +1156,8 @@ def single_config(wname: str, K: int, W: int, peaks: dict, peak_kind: str) -> di
         del f8
     res = {"workload": f"{wname}: m={m} n={n} k={k} l={l}, sigma_i={w['spectrum']}, "
                        f"{w['dtype']} storage, {prec} path",
-           "value": 1e3 / ms, "unit": "LU/s", "ms_per_step": ms, "steps": K, "warmup": W,
+           "value": 1e3 / ms2, "unit": "LU/s", "ms_per_step": ms2, "in_flight": 2,
+           "single_stream": {"value": 1e3 / ms, "ms_per_step": ms}, "steps": K, "warmup": W,
            "dtype": prec, "gpu_launches": launches, "clocks": csum,
            "l2": ("L2 flushed before every step" if small else
                   f"inputs larger than L2 (A = {A.numel() * A.element_size() / 1e6:.0f} MB)"),

@@ -36,6 +36,7 @@ struct U3Smem {
   uint64_t full[U3_MAXST];
   uint64_t conv[U3_MAXST];
   uint64_t empty[U3_MAXST];
+  uint64_t lofree[2];  // Y2 / Y3: lo buffer b no longer read by the MMAs
   uint64_t accum;
   uint64_t drain;  // final commit of the MMA issuer when a wait gave up
   uint32_t tmem_base;
@@ -128,6 +129,25 @@ __host__ __device__ inline U3Layout u3_layout(int mode, int BN) {
   return L;
 }
 
+// Ring slot of the one-tile kernel. For Y2 / Y3 the converter's lo tiles do not live in the
+// ring but in two buffers after it (lo of k-step kt in buffer kt % 2, freed by the MMAs'
+// commit), so the ring holds only what TMA brings: 4 slots of A and G instead of 3 of A, its
+// lo part and G, more bytes in flight to cover the load latency.
+__host__ __device__ inline U3Layout u3_tile_layout(int mode, int BN) {
+  U3Layout L = u3_layout(mode, BN);
+  const uint32_t at = U3_BM * 128, bt = (uint32_t)BN * 128;
+  if (mode == U3_MODE_Y2) {
+    L.a0 = 0; L.a1 = 0; L.b0 = at; L.b1 = at; L.a2 = 0; L.stage = at + bt;
+  } else if (mode == U3_MODE_Y3) {
+    L.a0 = 0; L.a1 = 0; L.b0 = at; L.b1 = at + bt; L.a2 = 0; L.stage = at + 2 * bt;
+  }
+  L.stage = (L.stage + 1023u) & ~1023u;
+  return L;
+}
+__host__ __device__ constexpr bool u3_lo_ring(int mode) {
+  return mode == U3_MODE_Y2 || mode == U3_MODE_Y3;
+}
+
 // One 128-row tile (mt) of N tile nt over K slice kz; the tensor maps are read by address
 // (kernel parameters or, for the batched form, records in global memory).
 template <int MODE>
@@ -138,8 +158,10 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
   extern __shared__ __align__(1024) unsigned char u3_smem[];
   U3Smem& sh = *reinterpret_cast<U3Smem*>(u3_smem);
   const uint32_t tiles = (su32(u3_smem) + sizeof(U3Smem) + 1023u) & ~1023u;
-  const U3Layout lay = u3_layout(MODE, a.BN);
+  const U3Layout lay = u3_tile_layout(MODE, a.BN);
   const int S = a.stages;
+  constexpr bool LORING = u3_lo_ring(MODE);
+  const uint32_t lo_base = tiles + (uint32_t)S * lay.stage;  // LORING: two lo tiles
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = mt * U3_BM;
   const int nb0 = nt * a.BN;  // first column of this CTA's N tile
@@ -156,6 +178,8 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
     }
     mb_init(su32(&sh.accum), 1);
     mb_init(su32(&sh.drain), 1);
+    mb_init(su32(&sh.lofree[0]), 1);
+    mb_init(su32(&sh.lofree[1]), 1);
     sh.err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -218,16 +242,18 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t base = tiles + s * lay.stage;
+      const uint32_t lo_at = LORING ? lo_base + (uint32_t)(kt & 1) * (U3_BM * 128) : base + lay.a1;
 #pragma unroll
       for (int kk = 0; kk < U3_BK / 8; ++kk) {
         const uint32_t off = kk * 32;
-        const uint64_t ah = desc_sw128(base + lay.a0 + off), al = desc_sw128(base + lay.a1 + off);
+        const uint64_t ah = desc_sw128(base + lay.a0 + off), al = desc_sw128(lo_at + off);
         const uint64_t bh = desc_sw128(base + lay.b0 + off), bl = desc_sw128(base + lay.b1 + off);
         mma_tf32(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
         mma_tf32(tmem, al, bh, idesc, 1u);
         if (MODE != U3_MODE_Y2) mma_tf32(tmem, ah, bl, idesc, 1u);
       }
       commit(su32(&sh.empty[s]));
+      if (LORING) commit(su32(&sh.lofree[kt & 1]));
     }
     commit(su32(&sh.accum));
   } else if (warp >= 2 && warp < 6) {
@@ -276,11 +302,18 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
         sh.err = 1;
         break;
       }
+      // the lo buffer of this k-step is free once the MMAs of k-step kt - 2 completed
+      if (LORING && kt >= 2 &&
+          !mb_wait(su32(&sh.lofree[kt & 1]), (uint32_t)(((kt >> 1) - 1) & 1))) {
+        sh.err = 1;
+        break;
+      }
       const uint32_t base = tiles + s * lay.stage;
       if (MODE == U3_MODE_Y2 || MODE == U3_MODE_Y3) {
         // row r of the swizzled A tile: 8 chunks of 16 bytes, position-preserving split
+        const uint32_t lo_at = lo_base + (uint32_t)(kt & 1) * (U3_BM * 128);
         float* hi = reinterpret_cast<float*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 32;
-        float* lo = reinterpret_cast<float*>(u3_smem + (base + lay.a1 - su32(u3_smem))) + r * 32;
+        float* lo = reinterpret_cast<float*>(u3_smem + (lo_at - su32(u3_smem))) + r * 32;
         // chunks visited in a row-rotated order so that each 8-thread phase of a warp
         // touches 8 different 16-byte bank groups
 #pragma unroll
@@ -689,16 +722,17 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
   // N tiles of up to 256 columns (one TMEM accumulator each), one per grid z index
   const int BN = op.N > 256 ? 256 : (int)round_up(op.N, 16);
   const int ntiles = (int)ceil_div(op.N, BN);
-  const U3Layout lay = u3_layout(MODE, BN);
+  const U3Layout lay = u3_tile_layout(MODE, BN);
   int dev = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
   int optin = 0;
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const int ctrl = 2048;
-  int stages = (int)((optin - ctrl) / (int)lay.stage);
+  const int lo_bytes = u3_lo_ring(MODE) ? 2 * U3_BM * 128 : 0;  // the two lo tiles
+  int stages = (int)((optin - ctrl - lo_bytes) / (int)lay.stage);
   if (stages > U3_MAXST) stages = U3_MAXST;
   if (stages < 2) return RLU_EUNSUPPORTED;
-  const size_t smem = (size_t)ctrl + (size_t)stages * lay.stage;
+  const size_t smem = (size_t)ctrl + (size_t)stages * lay.stage + (size_t)lo_bytes;
   CUtensorMap m0{}, m1{}, n0{}, n1{};
   if (MODE == U3_MODE_Y2) {
     RLU_TRY(map2d(&m0, op.A0, op.M, op.K, op.lda, U3_BK, U3_BM, true));
