@@ -54,7 +54,7 @@ def parse_args():
     ap.add_argument("--serve-lambdas", default="300,1000,3000",
                     help="Poisson arrival rates (requests/s) of the serving measurement")
     ap.add_argument("--serve-secs", type=float, default=2.0, help="arrival window per rate")
-    ap.add_argument("--streams", type=int, default=2,
+    ap.add_argument("--streams", type=int, default=4,
                     help="factorizations in flight in the timed throughput pass (each on its "
                          "own stream with its own workspace and input buffer)")
     ap.add_argument("--no-configs", action="store_true",
