@@ -176,6 +176,30 @@ __global__ void k_splitk_reduce(const T* __restrict__ part, int splits, int64_t 
   }
 }
 
+// The same sum for a column-major output (out(i, j) at out[j * ldo + i]): 32 x 32 tiles
+// staged in shared memory, so that the partial slices are read along their rows and the
+// output is written along its columns (both coalesced); z ascending as above.
+template <typename T, typename OutT>
+__global__ void __launch_bounds__(256) k_splitk_reduce_t(const T* __restrict__ part, int splits,
+                                                         int64_t M, int64_t N, int64_t slice,
+                                                         OutT* __restrict__ out, int64_t ldo) {
+  __shared__ OutT tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r, j = j0 + tx;
+    OutT s = OutT(0);
+    if (i < M && j < N)
+      for (int z = 0; z < splits; ++z) s += (OutT)part[z * slice + i * N + j];
+    tile[r][tx] = s;
+  }
+  __syncthreads();
+  for (int c = ty; c < 32; c += 8) {
+    const int64_t j = j0 + c, i = i0 + tx;
+    if (i < M && j < N) out[j * ldo + i] = tile[tx][c];
+  }
+}
+
 template <typename T>
 static void launch_variant(const GemmArgs& a, bool AK, bool BKM, bool CR, dim3 grid,
                            cudaStream_t s) {
@@ -265,6 +289,13 @@ int32_t gemm_simt(const GemmOp& op, cudaStream_t s) {
   a.C = op.partial; a.ldc = op.N; a.split_stride = op.M * op.N;
   launch_variant<T>(a, op.a_kmajor, op.b_kmajor, true, grid, s);
   RLU_TRY(last_launch_status());  // the split-K product
+  if (!op.c_rowmajor && ceil_div(op.M, 32) <= 65535) {
+    const dim3 tgrid((unsigned)ceil_div(op.N, 32), (unsigned)ceil_div(op.M, 32));
+    k_splitk_reduce_t<T, OutT><<<tgrid, 256, 0, s>>>(static_cast<const T*>(op.partial), splits,
+                                                     op.M, op.N, op.M * op.N,
+                                                     static_cast<OutT*>(op.C), op.ldc);
+    return last_launch_status();
+  }
   const int threads = 256;
   int64_t blocks = ceil_div(op.M * op.N, threads);
   if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
@@ -282,6 +313,12 @@ template size_t gemm_partial_bytes<double>(int64_t, int64_t, int);
 
 int32_t splitk_reduce_f32(const float* part, int splits, int64_t M, int64_t N, float* out,
                           int64_t ldo, bool out_rowmajor, cudaStream_t s) {
+  if (!out_rowmajor) {
+    if (ceil_div(M, 32) > 65535) return RLU_EUNSUPPORTED;
+    const dim3 grid((unsigned)ceil_div(N, 32), (unsigned)ceil_div(M, 32));
+    k_splitk_reduce_t<float, float><<<grid, 256, 0, s>>>(part, splits, M, N, M * N, out, ldo);
+    return last_launch_status();
+  }
   const int threads = 256;
   int64_t blocks = ceil_div(M * N, threads);
   if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
