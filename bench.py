@@ -51,9 +51,11 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-power", action="store_true",
                     help="skip the power-iteration (q = 1) measurement")
-    ap.add_argument("--serve-lambdas", default="300,1000,3000",
+    ap.add_argument("--serve-lambdas", default="300,1000,3000,5000",
                     help="Poisson arrival rates (requests/s) of the serving measurement")
     ap.add_argument("--serve-secs", type=float, default=2.0, help="arrival window per rate")
+    ap.add_argument("--serve-inflight", type=int, default=16,
+                    help="requests the server runs at once (slots, one stream each)")
     ap.add_argument("--streams", type=int, default=4,
                     help="factorizations in flight in the timed throughput pass (each on its "
                          "own stream with its own workspace and input buffer)")
@@ -316,7 +318,7 @@ def serve_requests(lam: float, secs: float, rng: np.random.Generator):
         out.append((t, m, n, k, k + 10))
 
 
-def serve_run(lams, secs: float, seed: int = 7):
+def serve_run(lams, secs: float, seed: int = 7, inflight: int = 16):
     """The serving form: requests arrive by a Poisson process and are submitted to the
     server at their arrival times; latency = arrival -> completion (host clock). Half the
     requests are FP32-accuracy (mixed path, FP32 A), half BF16-accuracy (BF16 A, the
@@ -331,7 +333,7 @@ def serve_run(lams, secs: float, seed: int = 7):
     torch.cuda.synchronize()
     rng = np.random.default_rng(seed)
     res = {}
-    srv = rlu.Server(budget_bytes=24 << 30, max_inflight=16)
+    srv = rlu.Server(budget_bytes=24 << 30, max_inflight=inflight)
     try:
         # warm-up: one request per pool size and class
         for sz in SERVE_POOL:
@@ -396,7 +398,7 @@ def serve_run(lams, secs: float, seed: int = 7):
     return {"lambdas": res, "arrival_window_s": secs,
             "classes": "half FP32-accuracy (mixed path, FP32 A), half BF16-accuracy (BF16 A, "
                        "precision form), drawn at random",
-            "max_inflight": 16, "budget_GB": 24, "peak_running": stats["peak_running"],
+            "max_inflight": inflight, "budget_GB": 24, "peak_running": stats["peak_running"],
             "peak_arena_GB": round(stats["peak_arena_bytes"] / 2 ** 30, 2),
             "bypassed_admissions": stats["bypassed_admissions"],
             "inputs": "top-left m x n blocks of resident prescribed-spectrum matrices "
@@ -407,7 +409,7 @@ def run_serve(args):
     """Serving form alone: the full arrival-rate sweep of the serving workload."""
     lams = [float(x) for x in args.serve_lambdas.split(",") if x]
     with ClockSampler(0) as clocks:
-        r = serve_run(lams, args.serve_secs)
+        r = serve_run(lams, args.serve_secs, inflight=args.serve_inflight)
     top = r["lambdas"][str(int(max(lams)))]
     line = {"metric": METRIC, "value": top["throughput_req_s"], "unit": "req/s", "n_gpus": 1,
             "steps": len(lams), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
@@ -729,7 +731,8 @@ def run_ours(args):
 
     serve = None
     if not args.no_serve and args.workload == WORKLOAD:
-        serve = serve_run([float(x) for x in args.serve_lambdas.split(",") if x], args.serve_secs)
+        serve = serve_run([float(x) for x in args.serve_lambdas.split(",") if x], args.serve_secs,
+                          inflight=args.serve_inflight)
 
     cpu = None
     gold = stored_oracle(args.workload)
