@@ -310,12 +310,17 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
         }
       }
     }
-    // ---- meanwhile: the deferred part of the previous step's update (live columns only) ---
+    // ---- meanwhile: the deferred part of the previous step's update --------------------------
     if (jj > 0) {
       const T* P1 = sh.prow[warp][par ^ 1];  // P1[c] = previous pivot row at offset c + 1
+      // FP32: every block of the panel, also those past the live columns (their registers
+      // are never read again): skipping them behind a branch costs more instructions
+      // (register moves at the join) than their multiply-adds. FP64 multiply-adds are slow
+      // enough that the blocks past the live columns are skipped.
+      constexpr bool kAllBlocks = sizeof(T) == 4;
 #pragma unroll
       for (int b0 = 0; b0 < NB - 1; b0 += 16) {
-        if (b0 < live) {  // uniform: skip whole blocks past the panel's live columns
+        if (kAllBlocks || b0 < live) {
 #pragma unroll
           for (int c0 = b0; c0 < b0 + 16 && c0 < NB - 1; c0 += 4) {
             T pv[4];
