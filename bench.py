@@ -318,11 +318,12 @@ def serve_requests(lam: float, secs: float, rng: np.random.Generator):
         out.append((t, m, n, k, k + 10))
 
 
-def serve_run(lams, secs: float, seed: int = 7, inflight: int = 16):
+def serve_run(lams, secs: float, seed: int = 7, inflight: int = 16, plain: bool = False):
     """The serving form: requests arrive by a Poisson process and are submitted to the
     server at their arrival times; latency = arrival -> completion (host clock). Half the
     requests are FP32-accuracy (mixed path, FP32 A), half BF16-accuracy (BF16 A, the
-    precision form), drawn at random."""
+    precision form), drawn at random. plain: the same arrivals (same seed) with every
+    request on the plain FP32 path (FP32 A), the comparison the served form must beat."""
     from paper_1310_7202_gb300 import rlu
 
     pool, pool_bf = {}, {}
@@ -331,16 +332,20 @@ def serve_run(lams, secs: float, seed: int = 7, inflight: int = 16):
         pool[sz] = synth.prescribed_matrix_torch(sz, sz, sigma, 31 + sz, 32 + sz, torch.float32)
         pool_bf[sz] = pool[sz].to(torch.bfloat16)
     torch.cuda.synchronize()
-    rng = np.random.default_rng(seed)
     res = {}
     srv = rlu.Server(budget_bytes=24 << 30, max_inflight=inflight)
     try:
-        # warm-up: one request per pool size and class
+        # warm-up: the smallest and the largest k per pool size and class, so that the
+        # output buffers of any request later come from memory the allocator already holds
         for sz in SERVE_POOL:
-            srv.submit(pool[sz], 16, 26, 1, "mixed", m=sz, n=sz)
-            srv.submit(pool_bf[sz], 16, 26, 1, "bf16", m=sz, n=sz)
-        srv.wait_all()
+            for kk in (16, 256):
+                cls_ = ("f32", "f32") if plain else ("mixed", "bf16")
+                srv.submit(pool[sz], kk, kk + 10, 1, cls_[0], m=sz, n=sz)
+                srv.submit(pool[sz] if plain else pool_bf[sz], kk, kk + 10, 1, cls_[1],
+                           m=sz, n=sz)
+            srv.wait_all()
         for lam in lams:
+            rng = np.random.default_rng((seed, int(lam)))  # the same arrivals for every run
             reqs = serve_requests(lam, secs, rng)
             classes = rng.random(len(reqs)) < 0.5
             ids, t_arr, cls = [], [], []
@@ -351,7 +356,9 @@ def serve_run(lams, secs: float, seed: int = 7, inflight: int = 16):
                 while time.perf_counter_ns() < target:
                     pass
                 sz = next(s for s in SERVE_POOL if s >= max(m, n))
-                if bf:
+                if plain:
+                    rid = srv.submit(pool[sz], k, l, len(ids) + 1, "f32", m=m, n=n)
+                elif bf:
                     rid = srv.submit(pool_bf[sz], k, l, len(ids) + 1, "bf16", m=m, n=n)
                 else:
                     rid = srv.submit(pool[sz], k, l, len(ids) + 1, "mixed", m=m, n=n)
@@ -396,8 +403,9 @@ def serve_run(lams, secs: float, seed: int = 7, inflight: int = 16):
     finally:
         srv.close()
     return {"lambdas": res, "arrival_window_s": secs,
-            "classes": "half FP32-accuracy (mixed path, FP32 A), half BF16-accuracy (BF16 A, "
-                       "precision form), drawn at random",
+            "classes": ("every request on the plain FP32 path (FP32 A)" if plain else
+                        "half FP32-accuracy (mixed path, FP32 A), half BF16-accuracy (BF16 A, "
+                        "precision form), drawn at random"),
             "max_inflight": inflight, "budget_GB": 24, "peak_running": stats["peak_running"],
             "peak_arena_GB": round(stats["peak_arena_bytes"] / 2 ** 30, 2),
             "bypassed_admissions": stats["bypassed_admissions"],
@@ -731,8 +739,11 @@ def run_ours(args):
 
     serve = None
     if not args.no_serve and args.workload == WORKLOAD:
-        serve = serve_run([float(x) for x in args.serve_lambdas.split(",") if x], args.serve_secs,
-                          inflight=args.serve_inflight)
+        lams_ = [float(x) for x in args.serve_lambdas.split(",") if x]
+        serve = serve_run(lams_, args.serve_secs, inflight=args.serve_inflight)
+        # the same arrival sequence with every request on the plain FP32 path
+        serve["plain_fp32"] = serve_run(lams_[-2:], args.serve_secs,
+                                        inflight=args.serve_inflight, plain=True)["lambdas"]
 
     cpu = None
     gold = stored_oracle(args.workload)
