@@ -327,6 +327,28 @@ int32_t splitk_reduce_f32(const float* part, int splits, int64_t M, int64_t N, f
   return last_launch_status();
 }
 
+__global__ void __launch_bounds__(256) k_splitk_reduce_cm(const float* __restrict__ part,
+                                                          int splits, int64_t M, int64_t N,
+                                                          float* __restrict__ out,
+                                                          int64_t ldo) {
+  const int64_t total = M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int z = 0; z < splits; ++z) s += part[z * total + e];
+    const int64_t j = e / M, i = e - j * M;
+    out[j * ldo + i] = s;
+  }
+}
+
+int32_t splitk_reduce_cm_f32(const float* part, int splits, int64_t M, int64_t N, float* out,
+                             int64_t ldo, cudaStream_t s) {
+  int64_t blocks = ceil_div(M * N, 256);
+  if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+  k_splitk_reduce_cm<<<(unsigned)blocks, 256, 0, s>>>(part, splits, M, N, out, ldo);
+  return last_launch_status();
+}
+
 int32_t splitk_reduce_f64(const float* part, int splits, int64_t M, int64_t N, double* out,
                           int64_t ldo, cudaStream_t s) {
   const int threads = 256;

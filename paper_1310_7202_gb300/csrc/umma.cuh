@@ -121,6 +121,11 @@ int umma3_splits(int64_t M, int64_t K, int64_t N);
 int32_t splitk_reduce_f32(const float* part, int splits, int64_t M, int64_t N, float* out,
                           int64_t ldo, bool out_rowmajor, cudaStream_t s);
 
+// Fixed-order sum of column-major FP32 partial slices (M x N, ld M each, slice stride M N)
+// into a column-major output (ldo).
+int32_t splitk_reduce_cm_f32(const float* part, int splits, int64_t M, int64_t N, float* out,
+                             int64_t ldo, cudaStream_t s);
+
 // Fixed-order FP64 sum of row-major FP32 partial slices into a row-major FP64 matrix.
 int32_t splitk_reduce_f64(const float* part, int splits, int64_t M, int64_t N, double* out,
                           int64_t ldo, cudaStream_t s);

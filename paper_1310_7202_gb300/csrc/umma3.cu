@@ -774,9 +774,13 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
     a.out_colmajor = op.out_colmajor;
   } else {
     if (!op.partial) return RLU_ENOMEM;
+    // partial slices in the output's layout: for a column-major output the epilogue's
+    // thread-per-row stores are then coalesced (row-major slices scatter every warp store
+    // over 32 rows), and the reduction is an element-wise sum
+    const bool cm = op.out != nullptr && op.out_colmajor;
     a.out = op.partial;
-    a.ldo = op.N;
-    a.out_colmajor = false;
+    a.ldo = cm ? op.M : op.N;
+    a.out_colmajor = cm;
     a.split_stride = (size_t)op.M * op.N;
   }
   auto kern = k_umma3<MODE>;
@@ -785,8 +789,11 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
   dim3 grid((unsigned)(ceil_div(op.M, U3_BM) * ntiles), (unsigned)splits);
   kern<<<grid, U3_THREADS, smem, s>>>(m0, m1, n0, n1, a);
   RLU_TRY(last_launch_status());
-  if (a.out == op.partial && op.out)
+  if (a.out == op.partial && op.out) {
+    if (a.out_colmajor)
+      return splitk_reduce_cm_f32(op.partial, splits, op.M, op.N, op.out, op.ldo, s);
     return splitk_reduce_f32(op.partial, splits, op.M, op.N, op.out, op.ldo, !op.out_colmajor, s);
+  }
   return RLU_OK;
 }
 
