@@ -357,8 +357,9 @@ __device__ __forceinline__ bool ldl_diag_block(float* BJJ, float* dJ, float* W, 
   return bad;
 }
 
-// C (32 x 32 block) -= A B^T for 32 x 32 blocks A, B (padded rows), one 4 x 4 register tile
-// (tile 0..63) per call.
+// C (32 x 32 block) -= A B^T (kSub) or C = A B^T for 32 x 32 blocks A, B (padded rows), one
+// 4 x 4 register tile (tile 0..63) per call.
+template <bool kSub = true>
 __device__ __forceinline__ void gemm_nt_tile(float* C, const float* A, const float* B, int tile) {
   const int r0 = (tile / 8) * 4, c0 = (tile % 8) * 4;
   float acc[4][4] = {};
@@ -378,7 +379,10 @@ __device__ __forceinline__ void gemm_nt_tile(float* C, const float* A, const flo
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) C[(r0 + x) * LBP + c0 + y] -= acc[x][y];
+    for (int y = 0; y < 4; ++y) {
+      if (kSub) C[(r0 + x) * LBP + c0 + y] -= acc[x][y];
+      else C[(r0 + x) * LBP + c0 + y] = acc[x][y];
+    }
 }
 
 template <int NT>
@@ -417,45 +421,20 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
   }
   __syncthreads();
   for (int J = 0; J < nb; ++J) {
-    float* BJJ = Bk + (size_t)tri_blk(J, J) * LB * LBP;
     if (warp == 0) {
-      float a[LB];
-#pragma unroll
-      for (int c = 0; c < LB; ++c) a[c] = BJJ[lane * LBP + c];
-      bool bad = false;
-      ldl_cols(a, lane, dd + J * LB, bad, std::make_integer_sequence<int, LB>{});
-#pragma unroll
-      for (int c = 0; c < LB; ++c) BJJ[lane * LBP + c] = (c < lane) ? a[c] : (c == lane ? 1.f : 0.f);
-      __syncwarp();
-      // W = L^{-1}: lane i holds row i; row t is final at step t
-      float w[LB];
-#pragma unroll
-      for (int c = 0; c < LB; ++c) w[c] = (c == lane) ? 1.f : 0.f;
-#pragma unroll
-      for (int t = 0; t < LB; ++t) {
-        const float lit = (lane > t) ? BJJ[lane * LBP + t] : 0.f;
-#pragma unroll
-        for (int c = 0; c <= t; ++c) {
-          const float wtc = __shfl_sync(0xffffffffu, w[c], t);
-          w[c] = fmaf(-lit, wtc, w[c]);
-        }
-      }
-      float* W = Wb + (size_t)J * LB * LBP;
-#pragma unroll
-      for (int c = 0; c < LB; ++c) W[lane * LBP + c] = (c <= lane) ? w[c] : 0.f;
+      const bool bad = ldl_diag_block(Bk + (size_t)tri_blk(J, J) * LB * LBP, dd + J * LB,
+                                      Wb + (size_t)J * LB * LBP, lane);
       if (bad && J * LB + lane < k) s_bad = 1;
     }
     __syncthreads();
-    // U_IJ = M_IJ W_J^T, then L_IJ = U_IJ D_J^{-1} in place
+    // U_IJ = M_IJ W_J^T in 4 x 4 register tiles (16 independent sums per thread), then
+    // L_IJ = U_IJ D_J^{-1} in place once every tile of the block column has read M_IJ
     const int rest = nb - 1 - J;
     const float* W = Wb + (size_t)J * LB * LBP;
-    for (int e = tid; e < rest * LB * LB; e += NT) {
-      const int I = J + 1 + e / (LB * LB), r = (e / LB) % LB, c = e % LB;
-      const float* Mr = Bk + (size_t)tri_blk(I, J) * LB * LBP + r * LBP;
-      float acc = 0.f;
-#pragma unroll
-      for (int t = 0; t < LB; ++t) acc = fmaf(Mr[t], W[c * LBP + t], acc);
-      Ub[(size_t)(I - J - 1) * LB * LBP + r * LBP + c] = acc;
+    for (int q = tid; q < rest * 64; q += NT) {
+      const int I = J + 1 + q / 64;
+      gemm_nt_tile<false>(Ub + (size_t)(I - J - 1) * LB * LBP,
+                          Bk + (size_t)tri_blk(I, J) * LB * LBP, W, q % 64);
     }
     __syncthreads();
     for (int e = tid; e < rest * LB * LB; e += NT) {
@@ -472,28 +451,8 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
       while ((ii + 1) * (ii + 2) / 2 <= pb) ++ii;
       const int kk = pb - ii * (ii + 1) / 2;
       const int I = J + 1 + ii, K = J + 1 + kk;
-      const int r0 = (tile / 8) * 4, c0 = (tile % 8) * 4;
-      const float* Lr = Bk + (size_t)tri_blk(I, J) * LB * LBP;
-      const float* Ur = Ub + (size_t)(K - J - 1) * LB * LBP;
-      float acc[4][4] = {};
-#pragma unroll 8
-      for (int t = 0; t < LB; ++t) {
-        float lv[4], uv[4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x) {
-          lv[x] = Lr[(r0 + x) * LBP + t];
-          uv[x] = Ur[(c0 + x) * LBP + t];
-        }
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(lv[x], uv[y], acc[x][y]);
-      }
-      float* Mt = Bk + (size_t)tri_blk(I, K) * LB * LBP;
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) Mt[(r0 + x) * LBP + c0 + y] -= acc[x][y];
+      gemm_nt_tile(Bk + (size_t)tri_blk(I, K) * LB * LBP, Bk + (size_t)tri_blk(I, J) * LB * LBP,
+                   Ub + (size_t)(K - J - 1) * LB * LBP, tile);
     }
     __syncthreads();
   }
@@ -665,16 +624,9 @@ __global__ void __launch_bounds__(LC_NT, 1) k_ldl32c(const double* __restrict__ 
     __syncthreads();
     // U_IJ = M_IJ W_J^T for the owned rows I > J
     const int q0 = (J < me) ? 0 : (J - me) / nc + 1;  // first owned row below J
-    for (int q = q0; q < mine; ++q) {
-      const float* Mr = blk(q, J);
-      float* U = Ub + (size_t)q * LC_BS;
-      for (int e = tid; e < LB * LB; e += LC_NT) {
-        const int r = e / LB, c = e % LB;
-        float acc = 0.f;
-#pragma unroll
-        for (int t = 0; t < LB; ++t) acc = fmaf(Mr[r * LBP + t], Wf[c * LBP + t], acc);
-        U[r * LBP + c] = acc;
-      }
+    for (int t = tid; t < (mine - q0) * 64; t += LC_NT) {
+      const int q = q0 + t / 64;
+      gemm_nt_tile<false>(Ub + (size_t)q * LC_BS, blk(q, J), Wf, t % 64);
     }
     __syncthreads();
     for (int q = q0; q < mine; ++q) {  // L_IJ = U_IJ D_J^{-1} in place
