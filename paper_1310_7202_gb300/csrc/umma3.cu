@@ -14,9 +14,13 @@
 //
 // Warp roles: warp 0 TMA producer (ring of STAGES slots, full/empty mbarriers), warp 1
 // TMEM allocation and MMA issue, warps 2..5 epilogue (tcgen05.ld), warps 6..9 converter
-// (MODE_Y2 / MODE_C3): one thread per tile row, writes the 128-byte-swizzled K-major hi/lo
-// tiles, fences them to the async proxy and arrives on a per-slot mbarrier. Every wait is
-// bounded (~1 s) and records an error instead of hanging.
+// (MODE_Y2 / MODE_Y3 / MODE_C3): one thread per tile row. In the one-tile kernel the
+// converter stores the row's hi and lo parts into tensor memory (tcgen05.st, the thread's
+// own TMEM lane) and the MMAs take A from there, so shared memory carries only what TMA
+// brings and what the MMAs read of B; in the persistent batched kernel it writes
+// 128-byte-swizzled K-major hi/lo tiles to shared memory and fences them to the async
+// proxy. Either way it arrives on a per-slot mbarrier. Every wait is bounded (~1 s) and
+// records an error instead of hanging.
 #include <algorithm>
 
 #include <cuda.h>
@@ -30,13 +34,19 @@ namespace rlu {
 static constexpr int U3_BM = 128;
 static constexpr int U3_BK = 32;
 static constexpr int U3_THREADS = 320;
-static constexpr int U3_MAXST = 4;
+static constexpr int U3_MAXST = 4;       // ring slots of the persistent batched kernel
+static constexpr int U3_MAXST_TILE = 6;  // ring slots of the one-tile kernel
+// TMEM of the one-tile kernel: the FP32 accumulator in columns 0..255; for the modes that
+// split A on chip, U3_NA buffers of 64 columns (hi(A) in 32, lo(A) in 32; lane = tile row,
+// column = K index) at 256 + 64 b
+static constexpr int U3_NA = 4;
+static constexpr uint32_t U3_ACOL = 256;
 
 struct U3Smem {
-  uint64_t full[U3_MAXST];
-  uint64_t conv[U3_MAXST];
-  uint64_t empty[U3_MAXST];
-  uint64_t lofree[2];  // Y2 / Y3: lo buffer b no longer read by the MMAs
+  uint64_t full[U3_MAXST_TILE];
+  uint64_t conv[U3_MAXST_TILE];
+  uint64_t empty[U3_MAXST_TILE];
+  uint64_t afree[U3_NA];  // TMEM A buffer b no longer read by the MMAs
   uint64_t accum;
   uint64_t drain;  // final commit of the MMA issuer when a wait gave up
   uint32_t tmem_base;
@@ -94,6 +104,27 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db
                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
                ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
 }
+// A from tensor memory (M rows in lanes 0..M-1, the 8 K values of this MMA in 8 columns
+// from tmem_a), B from shared memory
+__device__ __forceinline__ void mma_tf32_ts(uint32_t tmem, uint32_t tmem_a, uint64_t db,
+                                            uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+               ::"r"(tmem), "r"(tmem_a), "l"(db), "r"(idesc), "r"(acc) : "memory");
+}
+// 32 consecutive columns of this thread's TMEM lane (the warp's 32-lane quarter)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31, %32};\n"
+      ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+        "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]),
+        "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]),
+        "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]),
+        "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
 __device__ __forceinline__ void commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                ::"r"(bar) : "memory");
@@ -129,10 +160,9 @@ __host__ __device__ inline U3Layout u3_layout(int mode, int BN) {
   return L;
 }
 
-// Ring slot of the one-tile kernel. For Y2 / Y3 the converter's lo tiles do not live in the
-// ring but in two buffers after it (lo of k-step kt in buffer kt % 2, freed by the MMAs'
-// commit), so the ring holds only what TMA brings: 4 slots of A and G instead of 3 of A, its
-// lo part and G, more bytes in flight to cover the load latency.
+// Ring slot of the one-tile kernel: only what TMA brings, since the converter's hi / lo
+// parts of A go to tensor memory. Y2: A (a0), G (b0); Y3: A (a0), Zhi (b0), Zlo (b1); C3:
+// raw n-contiguous A (a2), Lhi (b0), Llo (b1); G3 as in the batched layout.
 __host__ __device__ inline U3Layout u3_tile_layout(int mode, int BN) {
   U3Layout L = u3_layout(mode, BN);
   const uint32_t at = U3_BM * 128, bt = (uint32_t)BN * 128;
@@ -140,12 +170,11 @@ __host__ __device__ inline U3Layout u3_tile_layout(int mode, int BN) {
     L.a0 = 0; L.a1 = 0; L.b0 = at; L.b1 = at; L.a2 = 0; L.stage = at + bt;
   } else if (mode == U3_MODE_Y3) {
     L.a0 = 0; L.a1 = 0; L.b0 = at; L.b1 = at + bt; L.a2 = 0; L.stage = at + 2 * bt;
+  } else if (mode == U3_MODE_C3) {
+    L.a2 = 0; L.a0 = 0; L.a1 = 0; L.b0 = at; L.b1 = at + bt; L.stage = at + 2 * bt;
   }
   L.stage = (L.stage + 1023u) & ~1023u;
   return L;
-}
-__host__ __device__ constexpr bool u3_lo_ring(int mode) {
-  return mode == U3_MODE_Y2 || mode == U3_MODE_Y3;
 }
 
 // One 128-row tile (mt) of N tile nt over K slice kz; the tensor maps are read by address
@@ -160,8 +189,6 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
   const uint32_t tiles = (su32(u3_smem) + sizeof(U3Smem) + 1023u) & ~1023u;
   const U3Layout lay = u3_tile_layout(MODE, a.BN);
   const int S = a.stages;
-  constexpr bool LORING = u3_lo_ring(MODE);
-  const uint32_t lo_base = tiles + (uint32_t)S * lay.stage;  // LORING: two lo tiles
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = mt * U3_BM;
   const int nb0 = nt * a.BN;  // first column of this CTA's N tile
@@ -169,6 +196,7 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
   const int k_end = min(a.K, k_begin + a.kchunk);
   const int nk = (k_end - k_begin + U3_BK - 1) / U3_BK;
   constexpr bool CONV = (MODE != U3_MODE_G3);
+  constexpr uint32_t TCOLS = CONV ? 512u : 256u;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -178,14 +206,13 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
     }
     mb_init(su32(&sh.accum), 1);
     mb_init(su32(&sh.drain), 1);
-    mb_init(su32(&sh.lofree[0]), 1);
-    mb_init(su32(&sh.lofree[1]), 1);
+    for (int b = 0; b < U3_NA; ++b) mb_init(su32(&sh.afree[b]), 1);
     sh.err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n"
-                 ::"r"(su32(&sh.tmem_base)) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 ::"r"(su32(&sh.tmem_base)), "r"(TCOLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -242,18 +269,32 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t base = tiles + s * lay.stage;
-      const uint32_t lo_at = LORING ? lo_base + (uint32_t)(kt & 1) * (U3_BM * 128) : base + lay.a1;
+      if (CONV) {
+        // A's hi / lo parts of this k-step in TMEM buffer kt % U3_NA
+        const uint32_t abuf = tmem + U3_ACOL + (uint32_t)(kt % U3_NA) * 64u;
 #pragma unroll
-      for (int kk = 0; kk < U3_BK / 8; ++kk) {
-        const uint32_t off = kk * 32;
-        const uint64_t ah = desc_sw128(base + lay.a0 + off), al = desc_sw128(lo_at + off);
-        const uint64_t bh = desc_sw128(base + lay.b0 + off), bl = desc_sw128(base + lay.b1 + off);
-        mma_tf32(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, al, bh, idesc, 1u);
-        if (MODE != U3_MODE_Y2) mma_tf32(tmem, ah, bl, idesc, 1u);
+        for (int kk = 0; kk < U3_BK / 8; ++kk) {
+          const uint32_t off = kk * 32;
+          const uint64_t bh = desc_sw128(base + lay.b0 + off), bl = desc_sw128(base + lay.b1 + off);
+          const uint32_t ah = abuf + (uint32_t)kk * 8u, al = ah + 32u;
+          mma_tf32_ts(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32_ts(tmem, al, bh, idesc, 1u);
+          if (MODE != U3_MODE_Y2) mma_tf32_ts(tmem, ah, bl, idesc, 1u);
+        }
+        commit(su32(&sh.empty[s]));
+        commit(su32(&sh.afree[kt % U3_NA]));
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < U3_BK / 8; ++kk) {
+          const uint32_t off = kk * 32;
+          const uint64_t ah = desc_sw128(base + lay.a0 + off), al = desc_sw128(base + lay.a1 + off);
+          const uint64_t bh = desc_sw128(base + lay.b0 + off), bl = desc_sw128(base + lay.b1 + off);
+          mma_tf32(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(tmem, al, bh, idesc, 1u);
+          mma_tf32(tmem, ah, bl, idesc, 1u);
+        }
+        commit(su32(&sh.empty[s]));
       }
-      commit(su32(&sh.empty[s]));
-      if (LORING) commit(su32(&sh.lofree[kt & 1]));
     }
     commit(su32(&sh.accum));
   } else if (warp >= 2 && warp < 6) {
@@ -294,59 +335,62 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
       }
     }
   } else if (CONV && warp >= 6) {
-    // ---- converter: one thread per tile row (128 rows) ------------------------------------
-    const int r = threadIdx.x - 192;  // 0..127
+    // ---- converter: one thread per tile row; row r = TMEM lane r, so warp w serves the
+    // rows of its lane quarter w % 4 ------------------------------------------------------
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % S;
       if (!mb_wait(su32(&sh.full[s]), (uint32_t)((kt / S) & 1))) {
         sh.err = 1;
         break;
       }
-      // the lo buffer of this k-step is free once the MMAs of k-step kt - 2 completed
-      if (LORING && kt >= 2 &&
-          !mb_wait(su32(&sh.lofree[kt & 1]), (uint32_t)(((kt >> 1) - 1) & 1))) {
+      // TMEM buffer kt % U3_NA is free once the MMAs of k-step kt - U3_NA completed
+      if (kt >= U3_NA &&
+          !mb_wait(su32(&sh.afree[kt % U3_NA]), (uint32_t)(((kt / U3_NA) - 1) & 1))) {
         sh.err = 1;
         break;
       }
       const uint32_t base = tiles + s * lay.stage;
+      uint32_t h[32], l[32];
       if (MODE == U3_MODE_Y2 || MODE == U3_MODE_Y3) {
-        // row r of the swizzled A tile: 8 chunks of 16 bytes, position-preserving split
-        const uint32_t lo_at = lo_base + (uint32_t)(kt & 1) * (U3_BM * 128);
-        float* hi = reinterpret_cast<float*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 32;
-        float* lo = reinterpret_cast<float*>(u3_smem + (lo_at - su32(u3_smem))) + r * 32;
-        // chunks visited in a row-rotated order so that each 8-thread phase of a warp
-        // touches 8 different 16-byte bank groups
-#pragma unroll
-        for (int c0 = 0; c0 < 8; ++c0) {
-          const int c = (c0 + r) & 7;
-          float4 v = *reinterpret_cast<float4*>(hi + 4 * c);
-          float4 h, l;
-          split_tf32(v.x, h.x, l.x);
-          split_tf32(v.y, h.y, l.y);
-          split_tf32(v.z, h.z, l.z);
-          split_tf32(v.w, h.w, l.w);
-          *reinterpret_cast<float4*>(hi + 4 * c) = h;
-          *reinterpret_cast<float4*>(lo + 4 * c) = l;
-        }
-      } else {
-        // raw tile: 32 rows (K) x 128 floats (M), row-major; output row r (M index r):
-        // its 32 K values, 16-byte chunk c stored at chunk position c ^ (r & 7)
-        const float* raw = reinterpret_cast<const float*>(u3_smem + (base + lay.a2 - su32(u3_smem)));
-        float* hi = reinterpret_cast<float*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 32;
-        float* lo = reinterpret_cast<float*>(u3_smem + (base + lay.a1 - su32(u3_smem))) + r * 32;
+        // row r of the 128-byte-swizzled A tile: logical 16-byte chunk c sits at chunk
+        // c ^ (r & 7), so the 8 threads of each quarter warp hit 8 different bank groups
+        const float4* row =
+            reinterpret_cast<const float4*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 8;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          float4 h, l;
-          split_tf32(raw[(4 * c + 0) * U3_BM + r], h.x, l.x);
-          split_tf32(raw[(4 * c + 1) * U3_BM + r], h.y, l.y);
-          split_tf32(raw[(4 * c + 2) * U3_BM + r], h.z, l.z);
-          split_tf32(raw[(4 * c + 3) * U3_BM + r], h.w, l.w);
-          const int pc = c ^ (r & 7);
-          *reinterpret_cast<float4*>(hi + 4 * pc) = h;
-          *reinterpret_cast<float4*>(lo + 4 * pc) = l;
+          const float4 v = row[c ^ (r & 7)];
+          float hx, lx;
+          split_tf32(v.x, hx, lx);
+          h[4 * c + 0] = __float_as_uint(hx);
+          l[4 * c + 0] = __float_as_uint(lx);
+          split_tf32(v.y, hx, lx);
+          h[4 * c + 1] = __float_as_uint(hx);
+          l[4 * c + 1] = __float_as_uint(lx);
+          split_tf32(v.z, hx, lx);
+          h[4 * c + 2] = __float_as_uint(hx);
+          l[4 * c + 2] = __float_as_uint(lx);
+          split_tf32(v.w, hx, lx);
+          h[4 * c + 3] = __float_as_uint(hx);
+          l[4 * c + 3] = __float_as_uint(lx);
+        }
+      } else {
+        // raw tile: 32 rows (K) x 128 floats (M), row-major; tile row r is its column r
+        const float* raw = reinterpret_cast<const float*>(u3_smem + (base + lay.a2 - su32(u3_smem)));
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float hx, lx;
+          split_tf32(raw[j * U3_BM + r], hx, lx);
+          h[j] = __float_as_uint(hx);
+          l[j] = __float_as_uint(lx);
         }
       }
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + U3_ACOL + (uint32_t)(kt % U3_NA) * 64u;
+      tmem_st32(taddr, h);
+      tmem_st32(taddr + 32u, l);
+      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       mb_arrive(su32(&sh.conv[s]));
     }
   }
@@ -368,7 +412,8 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
   }
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n"
+                 ::"r"(tmem), "r"(TCOLS) : "memory");
   }
   if (threadIdx.x == 0 && sh.err && a.status) atomicExch(a.status, RLU_ETIMEOUT);
 }
@@ -728,11 +773,10 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
   int optin = 0;
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const int ctrl = 2048;
-  const int lo_bytes = u3_lo_ring(MODE) ? 2 * U3_BM * 128 : 0;  // the two lo tiles
-  int stages = (int)((optin - ctrl - lo_bytes) / (int)lay.stage);
-  if (stages > U3_MAXST) stages = U3_MAXST;
+  int stages = (int)((optin - ctrl) / (int)lay.stage);
+  if (stages > U3_MAXST_TILE) stages = U3_MAXST_TILE;
   if (stages < 2) return RLU_EUNSUPPORTED;
-  const size_t smem = (size_t)ctrl + (size_t)stages * lay.stage + (size_t)lo_bytes;
+  const size_t smem = (size_t)ctrl + (size_t)stages * lay.stage;
   CUtensorMap m0{}, m1{}, n0{}, n1{};
   if (MODE == U3_MODE_Y2) {
     RLU_TRY(map2d(&m0, op.A0, op.M, op.K, op.lda, U3_BK, U3_BM, true));
