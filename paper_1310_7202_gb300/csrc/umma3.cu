@@ -94,6 +94,21 @@ __device__ __forceinline__ void tma2d(uint32_t dst, const CUtensorMap* map, int 
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+// the same load with an L2 eviction-priority policy (from evict_first_policy)
+__device__ __forceinline__ void tma2d_hint(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                           uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;\n"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+      : "memory");
+}
+// L2 policy for data read once (A streamed past operands that other tiles read again)
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
          ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
@@ -516,6 +531,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
   if (warp == 0 && lane == 0) {
     // ---- TMA producer and tile scheduler -----------------------------------------------
     uint32_t g = 0;
+    const uint64_t pol_a = evict_first_policy();
     for (int it = 0; !*err; ++it) {
       const int q = it % U3_QN;
       if (it >= U3_QN && !mb_wait(su32(&sh.qempty[q]), (uint32_t)(((it / U3_QN) - 1) & 1))) {
@@ -544,11 +560,13 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
         const uint32_t bar = su32(&sh.full[st]);
         mb_expect_tx(bar, tx);
         const int kx = kt * U3_BK;
+        // A is read once per tile; G (Y2) and L~'s parts (C3) are read by every row tile
+        // of the problem, so A goes first when L2 evicts
         if (MODE == U3_MODE_Y2) {
-          tma2d(base + lay.a0, &j.map[0], kx, m0, bar);
+          tma2d_hint(base + lay.a0, &j.map[0], kx, m0, bar, pol_a);
           tma2d(base + lay.b0, &j.map[2], kx, 0, bar);
         } else {
-          tma2d(base + lay.a2, &j.map[0], m0, kx, bar);  // raw A: x = n (128 wide), y = m
+          tma2d_hint(base + lay.a2, &j.map[0], m0, kx, bar, pol_a);  // raw A: x = n, y = m
           tma2d(base + lay.b0, &j.map[2], kx, 0, bar);
           tma2d(base + lay.b1, &j.map[3], kx, 0, bar);
         }
