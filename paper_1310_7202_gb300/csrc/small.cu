@@ -303,56 +303,75 @@ static constexpr int L32_MAXB = 8;  // k <= 256
 
 __device__ __forceinline__ int tri_blk(int I, int J) { return I * (I + 1) / 2 + J; }
 
+// Reciprocal of a pivot: the hardware approximation refined by one Newton-Raphson step
+// (y' = y + y (1 - d y)), within an ulp or so of 1/d.
+__device__ __forceinline__ float rcp_nr(float d) {
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(d));
+  return isfinite(y) ? fmaf(y, fmaf(-d, y, 1.0f), y) : y;
+}
+
 // Column t of the register-resident LDL^T of a 32 x 32 block (lane i holds row i):
 // d = M[t][t]; rows below get L[i][t] = M[i][t] / d and the rank-1 update of columns > t.
+// Column t (= row t, by symmetry) is broadcast through the 32-float shared row bc: one
+// store per lane, then 16-byte broadcast loads, cheaper than one shuffle per column.
 template <int t>
-__device__ __forceinline__ void ldl_col(float (&a)[LB], int lane, float* d_out, bool& bad) {
-  const float d = __shfl_sync(0xffffffffu, a[t], t);
-  const float rd = __frcp_rn(d);
+__device__ __forceinline__ void ldl_col(float (&a)[LB], float* bc, int lane, float* d_out,
+                                        bool& bad) {
+  __syncwarp();
+  bc[lane] = a[t];  // M[lane][t], the unscaled column
+  __syncwarp();
+  const float d = bc[t];
+  const float rd = rcp_nr(d);
   bad |= !(d > 0.f) || !(d < INFINITY);
-  const float u = a[t];  // M[lane][t], the unscaled column
-  const float l = u * rd;
+  const float l = a[t] * rd;
 #pragma unroll
-  for (int c = t + 1; c < LB; ++c) {
-    const float uc = __shfl_sync(0xffffffffu, u, c);
-    if (lane > t) a[c] = fmaf(-l, uc, a[c]);
+  for (int c0 = (t + 1) / 4 * 4; c0 < LB; c0 += 4) {
+    const float4 u = *reinterpret_cast<const float4*>(bc + c0);
+    const float uc[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (c0 + q > t && lane > t) a[c0 + q] = fmaf(-l, uc[q], a[c0 + q]);
   }
   if (lane == t) d_out[t] = d;
   if (lane > t) a[t] = l;
 }
 template <int... ts>
-__device__ __forceinline__ void ldl_cols(float (&a)[LB], int lane, float* d_out, bool& bad,
-                                         std::integer_sequence<int, ts...>) {
-  (ldl_col<ts>(a, lane, d_out, bad), ...);
+__device__ __forceinline__ void ldl_cols(float (&a)[LB], float* bc, int lane, float* d_out,
+                                         bool& bad, std::integer_sequence<int, ts...>) {
+  (ldl_col<ts>(a, bc, lane, d_out, bad), ...);
 }
 
 // One warp: LDL^T of the 32 x 32 block BJJ in place (L unit lower, zero above), D into dJ
-// and W = L^{-1} (row-major, padded rows) into W, as in ldl32_body. Returns true in the
-// lanes whose pivot was not positive and finite.
+// and W = L^{-1} (row-major, padded rows) into W. Returns true in the lanes whose pivot was
+// not positive and finite.
 __device__ __forceinline__ bool ldl_diag_block(float* BJJ, float* dJ, float* W, int lane) {
+  __shared__ __align__(16) float bc[LB];
   float a[LB];
 #pragma unroll
   for (int c = 0; c < LB; ++c) a[c] = BJJ[lane * LBP + c];
   bool bad = false;
-  ldl_cols(a, lane, dJ, bad, std::make_integer_sequence<int, LB>{});
+  ldl_cols(a, bc, lane, dJ, bad, std::make_integer_sequence<int, LB>{});
 #pragma unroll
   for (int c = 0; c < LB; ++c) BJJ[lane * LBP + c] = (c < lane) ? a[c] : (c == lane ? 1.f : 0.f);
   __syncwarp();
-  // W = L^{-1}: lane i holds row i; row t is final at step t
+  // W = L^{-1} by forward substitution, lane c computing column c:
+  // W[i][c] = [i == c] - sum_{j < i} L[i][j] W[j][c] (zero above the diagonal by itself);
+  // L[i][j] is the same for every lane, a broadcast load. Two partial sums per entry.
   float w[LB];
 #pragma unroll
-  for (int c = 0; c < LB; ++c) w[c] = (c == lane) ? 1.f : 0.f;
+  for (int i = 0; i < LB; ++i) {
+    float s0 = (i == lane) ? 1.f : 0.f, s1 = 0.f;
 #pragma unroll
-  for (int t = 0; t < LB; ++t) {
-    const float lit = (lane > t) ? BJJ[lane * LBP + t] : 0.f;
-#pragma unroll
-    for (int c = 0; c <= t; ++c) {
-      const float wtc = __shfl_sync(0xffffffffu, w[c], t);
-      w[c] = fmaf(-lit, wtc, w[c]);
+    for (int j = 0; j < i; ++j) {
+      const float lij = BJJ[i * LBP + j];
+      if (j & 1) s1 = fmaf(-lij, w[j], s1);
+      else s0 = fmaf(-lij, w[j], s0);
     }
+    w[i] = s0 + s1;
   }
 #pragma unroll
-  for (int c = 0; c < LB; ++c) W[lane * LBP + c] = (c <= lane) ? w[c] : 0.f;
+  for (int i = 0; i < LB; ++i) W[i * LBP + lane] = w[i];
   __syncwarp();
   return bad;
 }
@@ -398,25 +417,22 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
   __shared__ int s_bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_bad = 0;
-  // batches of 8 independent loads per thread, so that their latencies overlap
-  for (int e0 = tid; e0 < nblk * LB * LB; e0 += NT * 8) {
+  // block (I, J) row r: warp-wide rows, 8 of them in flight per warp
+  for (int q0 = warp; q0 < nblk * LB; q0 += (NT / 32) * 8) {
     float v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * NT;
-      const int b = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
+      const int q = q0 + u * (NT / 32);  // block row: block q / LB, row q % LB
+      const int b = q / LB, r = q % LB;
       int I = 0;
       while (tri_blk(I + 1, 0) <= b) ++I;
-      const int J = b - tri_blk(I, 0);
-      const int i = I * LB + r, j = J * LB + c;
-      if (e < nblk * LB * LB && i < k && j < k) v[u] = (float)M[(int64_t)i * k + j];
-      else v[u] = (i == j) ? 1.f : 0.f;
+      const int i = I * LB + r, j = (b - tri_blk(I, 0)) * LB + lane;
+      v[u] = (q < nblk * LB && i < k && j < k) ? (float)M[(int64_t)i * k + j] : (i == j ? 1.f : 0.f);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * NT;
-      const int b = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
-      if (e < nblk * LB * LB) Bk[(size_t)b * LB * LBP + r * LBP + c] = v[u];
+      const int q = q0 + u * (NT / 32);
+      if (q < nblk * LB) Bk[(size_t)(q / LB) * LB * LBP + (q % LB) * LBP + lane] = v[u];
     }
   }
   __syncthreads();
@@ -459,24 +475,23 @@ __device__ __forceinline__ void ldl32_body(const double* __restrict__ M, int k,
   // L (unit lower, zero above, identity past k) in both layouts, the diagonal-block
   // inverses and their transposes, 1/D
   const int kp = o.kp;
-  for (int e = tid; e < kp * kp; e += NT) {
-    const int c = e / kp, i = e % kp;
-    float v = 0.f;
-    if (i > c) v = Bk[(size_t)tri_blk(i / LB, c / LB) * LB * LBP + (i % LB) * LBP + c % LB];
-    else if (i == c) v = 1.f;
-    o.LT[e] = v;
+  for (int x = warp; x < kp; x += NT / 32) {  // LT row x = column x of L; LR row x
+    for (int y = lane; y < kp; y += 32) {
+      const int X = x / LB, Y = y / LB;
+      float lt = 0.f, lr = 0.f;
+      if (y > x) lt = Bk[(size_t)tri_blk(Y, X) * LB * LBP + (y % LB) * LBP + x % LB];
+      else if (y == x) lt = 1.f;
+      if (x > y) lr = Bk[(size_t)tri_blk(X, Y) * LB * LBP + (x % LB) * LBP + y % LB];
+      else if (x == y) lr = 1.f;
+      o.LT[(size_t)x * kp + y] = lt;
+      o.LR[(size_t)x * kp + y] = lr;
+    }
   }
-  for (int e = tid; e < kp * kp; e += NT) {
-    const int i = e / kp, c = e % kp;
-    float v = 0.f;
-    if (i > c) v = Bk[(size_t)tri_blk(i / LB, c / LB) * LB * LBP + (i % LB) * LBP + c % LB];
-    else if (i == c) v = 1.f;
-    o.LR[e] = v;
-  }
-  for (int e = tid; e < nb * LB * LB; e += NT) {
-    const int b = e / (LB * LB), r = (e / LB) % LB, c = e % LB;
-    o.W[e] = Wb[(size_t)b * LB * LBP + r * LBP + c];
-    o.WT[e] = Wb[(size_t)b * LB * LBP + c * LBP + r];
+  for (int q = warp; q < nb * LB; q += NT / 32) {  // row q % LB of block q / LB
+    const float* Wq = Wb + (size_t)(q / LB) * LB * LBP;
+    const int r = q % LB;
+    o.W[(size_t)q * LB + lane] = Wq[r * LBP + lane];
+    o.WT[(size_t)q * LB + lane] = Wq[lane * LBP + r];
   }
   for (int i = tid; i < k; i += NT) o.dinv[i] = 1.0 / (double)dd[i];
   if (tid == 0 && s_bad && status) *status = RLU_EINVAL;
