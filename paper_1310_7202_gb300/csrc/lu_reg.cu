@@ -21,6 +21,10 @@
 // rest of the update runs while the records are in flight (receivers apply the winner's
 // pending update themselves).
 //
+// A problem whose rows fit one CTA (SOLO) skips the exchange: the owner warp writes its
+// record straight into the receive slot, a CTA barrier after the deferred update publishes
+// it, and that record is the winner.
+//
 // Waits on an mbarrier give up after about one second (globaltimer); the kernel then
 // records RLU_ETIMEOUT in the status word and keeps going without waiting, so every CTA
 // still reaches the same cluster barriers and exits.
@@ -168,7 +172,7 @@ struct LrShared {
   alignas(16) T prow[NW][2][Pad4<NB>::value + 4];
 };
 
-template <typename T, bool CROUT, int RT, int NB, int NT>
+template <typename T, bool CROUT, int RT, int NB, int NT, bool SOLO>
 __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
   constexpr int NW = NT / 32;
   cg::cluster_group cl = cg::this_cluster();
@@ -239,7 +243,7 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
     // mbarriers start at phase 0 in every launch, so step jj waits on phase (jj / 2) & 1
     const int par = jj & 1;
     const int live = w - jj;  // columns j .. p0 + w - 1
-    if (tid == 0) mbar_arm(mbar_a + 8 * par, (uint32_t)(ncta * RB));
+    if (!SOLO && tid == 0) mbar_arm(mbar_a + 8 * par, (uint32_t)(ncta * RB));
     // ---- candidates: thread, warp ----------------------------------------------------------
     uint64_t key = 0;
     int kpos = 0x7fffffff, krow = -1;
@@ -273,7 +277,7 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
       const int ow = warp_winner(k2, p2);  // owner warp
       if (warp == ow) {
         const int cta_row = sh.wrow[par][ow];
-        LrRec<T, NB>* rec = reinterpret_cast<LrRec<T, NB>*>(sh.stage);
+        LrRec<T, NB>* rec = reinterpret_cast<LrRec<T, NB>*>(SOLO ? &sh.recv[par][0][0] : sh.stage);
         if (cta_row < 0) {
           if (lane == 0) {  // no live row in this CTA
             rec->khi = 0;
@@ -302,7 +306,7 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
           }
         }
         __syncwarp();
-        if (lane < NCHUNK) {
+        if (!SOLO && lane < NCHUNK) {
           const uint4 v = *reinterpret_cast<const uint4*>(sh.stage + 16 * lane);
           const uint32_t dst = recv_a + (uint32_t)((par * 16 + crank) * RB + 16 * lane);
           const uint32_t bar = mbar_a + 8 * par;
@@ -343,7 +347,9 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
       }
     }
     // ---- wait for the cluster's records -----------------------------------------------------
-    if (!timed_out) {
+    if (SOLO) {
+      __syncthreads();  // the owner warp's record in slot 0
+    } else if (!timed_out) {
       const uint32_t bar = mbar_a + 8 * par;
       const uint32_t ph = (uint32_t)((jj >> 1) & 1);
       if (!mbar_try(bar, ph)) {
@@ -358,8 +364,8 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
       }
     }
     // ---- winner among the cluster's records, in every warp ----------------------------------
-    int win;
-    {
+    int win = 0;
+    if (!SOLO) {
       const LrRec<T, NB>* rr = reinterpret_cast<const LrRec<T, NB>*>(&sh.recv[par][lane < ncta ? lane : 0][0]);
       const uint64_t k3 = lane < ncta ? (((uint64_t)rr->khi << 32) | rr->klo) : 0ull;
       const int p3 = lane < ncta ? rr->pos : 0x7fffffff;
@@ -485,16 +491,16 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
   cl.sync();
 }
 
-template <typename T, bool CROUT, int RT, int NB, int NT>
+template <typename T, bool CROUT, int RT, int NB, int NT, bool SOLO>
 __global__ void __launch_bounds__(NT, 1) k_lu_reg(LuArgs a) {
-  lu_reg_body<T, CROUT, RT, NB, NT>(a);
+  lu_reg_body<T, CROUT, RT, NB, NT, SOLO>(a);
 }
 
 // Batched form: cluster c of the launch factors problem table[c] (one panel: pw = C).
-template <typename T, bool CROUT, int RT, int NB, int NT>
+template <typename T, bool CROUT, int RT, int NB, int NT, bool SOLO>
 __global__ void __launch_bounds__(NT, 1) k_lu_reg_batched(const LuArgs* __restrict__ table) {
   const int csize = (int)cg::this_cluster().num_blocks();
-  lu_reg_body<T, CROUT, RT, NB, NT>(table[blockIdx.x / csize]);
+  lu_reg_body<T, CROUT, RT, NB, NT, SOLO>(table[blockIdx.x / csize]);
 }
 
 // Asynchronous global -> shared copies (cp.async): 16 bytes, or one element.
@@ -716,7 +722,10 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t bytes = lr_smem_bytes<T, NB, NT>(rpc, in.C);
   if (bytes > (size_t)optin) return RLU_OK;
-  auto kern = k_lu_reg<T, CROUT, RT, NB, NT>;
+  auto kern = k_lu_reg<T, CROUT, RT, NB, NT, false>;
+  if constexpr (RT == 1) {  // one CTA: no exchange (RT = 1 covers every problem that fits one)
+    if (ncta == 1) kern = k_lu_reg<T, CROUT, RT, NB, NT, true>;
+  }
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
@@ -815,7 +824,10 @@ static int32_t lu_batched_group(bool crout, const LuArgs* table_dev, int first, 
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t bytes = lr_smem_bytes<T, NB, NT>(NT, 0);
   if (bytes > (size_t)optin) return RLU_EUNSUPPORTED;
-  auto kern = crout ? k_lu_reg_batched<T, true, 1, NB, NT> : k_lu_reg_batched<T, false, 1, NB, NT>;
+  auto kern = g == 1 ? (crout ? k_lu_reg_batched<T, true, 1, NB, NT, true>
+                              : k_lu_reg_batched<T, false, 1, NB, NT, true>)
+                    : (crout ? k_lu_reg_batched<T, true, 1, NB, NT, false>
+                             : k_lu_reg_batched<T, false, 1, NB, NT, false>);
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
