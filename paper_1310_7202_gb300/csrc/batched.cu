@@ -180,6 +180,18 @@ struct rlu_batch {
   int u3y_stages = 0, u3y_stage_bytes = 0, u3c_stages = 0, u3c_stage_bytes = 0;
   int ts_first[4] = {}, ts_count[4] = {};  // small-k substitution tiles per bucket of k
   rlu_batch_options opt{};
+  rlu::LuFork lu_fork{};  // helper streams: the LU groups run side by side
+  bool have_fork = false;
+  rlu_batch() = default;
+  rlu_batch(const rlu_batch&) = delete;
+  rlu_batch& operator=(const rlu_batch&) = delete;
+  ~rlu_batch() {  // streams with work pending are released once it completes
+    if (lu_fork.fork) cudaEventDestroy(lu_fork.fork);
+    for (int i = 0; i < rlu::kLuSide; ++i) {
+      if (lu_fork.hs[i]) cudaStreamDestroy(lu_fork.hs[i]);
+      if (lu_fork.join[i]) cudaEventDestroy(lu_fork.join[i]);
+    }
+  }
 };
 
 extern "C" size_t rlu_batch_workspace_size(const rlu_problem* problems, int32_t count,
@@ -220,6 +232,18 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
   if (ws_bytes < need) return RLU_ENOMEM;
   char* ws = static_cast<char*>(workspace);
   rlu_batch* b = new rlu_batch();
+  {
+    bool ok = cudaEventCreateWithFlags(&b->lu_fork.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < kLuSide; ++i)
+      ok = cudaStreamCreateWithFlags(&b->lu_fork.hs[i], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&b->lu_fork.join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      delete b;  // the destructor releases what was created
+      return RLU_ECUDA;
+    }
+    b->have_fork = true;
+  }
   b->ws = ws;
   b->count = count;
   b->prec = prec;
@@ -460,7 +484,7 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
                                              b->opt.gemm_tile_y)));
   RLU_TRY(launch_lu_reg_batched(false, b->opt.lu_rows_per_cta,
                                 reinterpret_cast<const LuArgs*>(ws + t.lu_y), b->first_y,
-                                b->count_y, s));
+                                b->count_y, s, b->have_fork ? &b->lu_fork : nullptr));
   RLU_TRY(build_ly_batched(reinterpret_cast<const BuildJob*>(ws + t.build), c, b->max_m,
                            b->max_k, s));
   if (t.small_k)  // the Gram is k x k with k <= 64: one CTA per problem
@@ -488,7 +512,7 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
                          s));
   RLU_TRY(launch_lu_reg_batched(true, b->opt.lu_rows_per_cta,
                                 reinterpret_cast<const LuArgs*>(ws + t.lu_b), b->first_b,
-                                b->count_b, s));
+                                b->count_b, s, b->have_fork ? &b->lu_fork : nullptr));
   RLU_TRY(gather_batched(reinterpret_cast<const GatherJob*>(ws + t.gather), c, b->max_k,
                          b->max_n, s));
   if (t.small_k)

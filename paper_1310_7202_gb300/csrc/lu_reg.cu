@@ -847,18 +847,37 @@ static int32_t lu_batched_group(bool crout, const LuArgs* table_dev, int first, 
 }
 
 int32_t launch_lu_reg_batched(bool crout, int rows_per_cta, const LuArgs* table_dev,
-                              const int* first, const int* count, cudaStream_t s) {
+                              const int* first, const int* count, cudaStream_t s,
+                              const LuFork* fork) {
   if (rows_per_cta != 512 && rows_per_cta != 256) return RLU_EINVAL;
-  for (int g = 1; g <= 16; ++g) {
-    if (count[g] == 0) continue;
-    if (rows_per_cta == 512)
-      RLU_TRY(lu_batched_group<512>(crout, table_dev, first[g], count[g], g, s));
+  int groups[kLuGroups], ng = 0;
+  for (int g = 16; g >= 1; --g)  // widest clusters first
+    if (count[g] > 0) groups[ng++] = g;
+  for (int g : {17, 18})  // one narrow CTA for small problems, several per SM
+    if (count[g] > 0) groups[ng++] = g;
+  const bool par = fork != nullptr && ng > 1;
+  if (par) RLU_CUDA_TRY(cudaEventRecord(fork->fork, s));
+  for (int i = 0; i < ng; ++i) {
+    const int g = groups[i];
+    cudaStream_t gs = s;
+    if (par) {
+      gs = fork->hs[i % kLuSide];
+      if (i < kLuSide) RLU_CUDA_TRY(cudaStreamWaitEvent(gs, fork->fork, 0));
+    }
+    if (g == 17)
+      RLU_TRY(lu_batched_group<128>(crout, table_dev, first[g], count[g], 1, gs));
+    else if (g == 18)
+      RLU_TRY(lu_batched_group<256>(crout, table_dev, first[g], count[g], 1, gs));
+    else if (rows_per_cta == 512)
+      RLU_TRY(lu_batched_group<512>(crout, table_dev, first[g], count[g], g, gs));
     else
-      RLU_TRY(lu_batched_group<256>(crout, table_dev, first[g], count[g], g, s));
+      RLU_TRY(lu_batched_group<256>(crout, table_dev, first[g], count[g], g, gs));
   }
-  // one narrow CTA for small problems, several per SM
-  if (count[17] > 0) RLU_TRY(lu_batched_group<128>(crout, table_dev, first[17], count[17], 1, s));
-  if (count[18] > 0) RLU_TRY(lu_batched_group<256>(crout, table_dev, first[18], count[18], 1, s));
+  if (par)
+    for (int i = 0; i < ng && i < kLuSide; ++i) {
+      RLU_CUDA_TRY(cudaEventRecord(fork->join[i], fork->hs[i]));
+      RLU_CUDA_TRY(cudaStreamWaitEvent(s, fork->join[i], 0));
+    }
   return RLU_OK;
 }
 

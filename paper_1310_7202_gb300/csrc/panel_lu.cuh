@@ -38,7 +38,18 @@ int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s
 // one 256-thread CTA (R <= 256). Each entry carries its rpc (rows per CTA), p0 = 0, pw = C
 // and its own position state (posg, psg).
 static constexpr int kLuGroups = 19;
+// Helper streams for the groups: with fork != nullptr every non-empty group is launched on
+// its own helper stream (fork / join events around them on s), so that the groups' CTAs
+// share the GPU instead of running one launch after another; works under stream capture
+// (parallel branches of the graph).
+static constexpr int kLuSide = 6;
+struct LuFork {
+  cudaStream_t hs[kLuSide];
+  cudaEvent_t fork;
+  cudaEvent_t join[kLuSide];
+};
 int32_t launch_lu_reg_batched(bool crout, int rows_per_cta, const LuArgs* table_dev,
-                              const int* first, const int* count, cudaStream_t s);
+                              const int* first, const int* count, cudaStream_t s,
+                              const LuFork* fork = nullptr);
 
 }  // namespace rlu
