@@ -960,6 +960,166 @@ __global__ void __launch_bounds__(TB / 2 * 64 / 4) k_trsm_batched(const TrsmJob*
   trsm_body<float, 64>(j.o, j.C, j.ldc, j.n, j.B, j.ldb, t.y);
 }
 
+// The same solve, right-looking: per block column J of L one pass X_J = W_J X_J, then one
+// pass X_I -= L_IJ X_J over every row block below J at once (forward), D^{-1}, then from the
+// last block Y_J = W_J^T Y_J and Y_I -= L_JI^T Y_J over every row block above J (backward).
+// 2 nb passes per direction instead of nb (nb + 1) / 2 block steps, each with all its rows'
+// work in flight. A pass needs 32 contiguous rows of L^T (forward: L^T row 32 J + t, columns
+// past the block) or of L (backward: L row 32 J + t, columns before the block) and the
+// diagonal block's inverse (W_J, or W_J^T backward): they stream into the other slot of a
+// two-slot cp.async ring while the current pass computes. 256 threads; in the update passes
+// each thread owns a TR x 4 tile (a warp: 32 / (TC / 4) row groups x TC / 4 column groups),
+// so every k-step is TR / 4 + 1 16-byte shared loads for 4 TR multiply-adds. D^{-1} is
+// applied in the storage precision (its reciprocals rounded once).
+static constexpr int RL_NT = 256;
+
+template <typename T>
+__host__ __device__ constexpr int rl_lpad(int kp) { return kp + 16 / (int)sizeof(T); }
+
+template <typename T, int TC, int TR>
+__global__ void __launch_bounds__(RL_NT) k_trsm_rl(LdlOut<T> o, const T* __restrict__ C,
+                                                   int64_t ldc, int64_t n, T* __restrict__ B,
+                                                   int64_t ldb) {
+  constexpr int CH = 16 / sizeof(T);  // elements per 16-byte copy
+  constexpr int CG = TC / 4;          // column groups of a warp in the update passes
+  constexpr int RG = 32 / CG;         // row groups (8 rows each) of a warp
+  constexpr int CPT = TC / 32;        // columns per thread in the diagonal passes
+  static_assert(TC == 32 || TC == 64, "TC");
+  extern __shared__ __align__(16) unsigned char rl_smem[];
+  const int k = o.k, kp = o.kp, nb = kp / TB, LP = rl_lpad<T>(kp);
+  T* Xs = reinterpret_cast<T*>(rl_smem);        // [kp][TC]
+  T* Ls = Xs + (size_t)kp * TC;                 // [2][TB][LP] rows of L^T / L
+  T* Wsm = Ls + (size_t)2 * TB * LP;            // [2][TB][LSP] W_J / W_J^T
+  T* Dsm = Wsm + (size_t)2 * TB * LSP;          // [kp] 1 / D
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c0 = (int64_t)blockIdx.x * TC;
+  const int npass = 2 * nb;  // pass q: forward block q (q < nb), backward block 2 nb - 1 - q
+  // stage pass q's operands into slot q & 1
+  auto stage = [&](int q) {
+    if (q < npass) {
+      const bool fwd = q < nb;
+      const int J = fwd ? q : npass - 1 - q;
+      const int i0 = fwd ? (J + 1) * TB : 0, i1 = fwd ? kp : J * TB;  // rows updated
+      const T* Lsrc = fwd ? o.LT : o.LR;
+      T* Ld = Ls + (size_t)(q & 1) * TB * LP;
+      const int per = (i1 - i0) / CH;  // 16-byte pieces per row
+      for (int e = tid; e < TB * per; e += RL_NT) {
+        const int t = e / per, i = i0 + (e % per) * CH;
+        cp_async16(Ld + t * LP + (i - i0), Lsrc + (int64_t)(J * TB + t) * kp + i);
+      }
+      const T* Wsrc = (fwd ? o.W : o.WT) + (size_t)J * TB * TB;
+      T* Wd = Wsm + (size_t)(q & 1) * TB * LSP;
+      for (int e = tid; e < TB * TB / CH; e += RL_NT) {
+        const int r = e / (TB / CH), c = (e % (TB / CH)) * CH;
+        cp_async16(Wd + r * LSP + c, Wsrc + r * TB + c);
+      }
+    }
+    cp_async_commit();
+  };
+  stage(0);
+  for (int i = tid; i < kp; i += RL_NT) Dsm[i] = i < k ? (T)o.dinv[i] : T(0);
+  constexpr int LDU = 8;  // batches of independent loads
+  for (int e0 = tid; e0 < kp * TC; e0 += RL_NT * LDU) {
+    T v[LDU];
+#pragma unroll
+    for (int u = 0; u < LDU; ++u) {
+      const int e = e0 + u * RL_NT, i = e / TC, c = e % TC;
+      v[u] = (i < k && c0 + c < n) ? C[(int64_t)i * ldc + c0 + c] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < LDU; ++u)
+      if (e0 + u * RL_NT < kp * TC) Xs[e0 + u * RL_NT] = v[u];
+  }
+  const int dr = warp * 4;          // diagonal pass: rows dr .. dr + 3 of the block
+  const int dc = lane * CPT;        //   and columns dc .. dc + CPT - 1
+  const int ug = lane / CG;         // update pass: row group of this thread in the warp strip
+  const int uc = (lane % CG) * 4;   //   and its 4 columns
+  for (int q = 0; q < npass; ++q) {
+    const bool fwd = q < nb;
+    const int J = fwd ? q : npass - 1 - q;
+    if (q == nb) {  // between the directions: X = D^{-1} X
+      __syncthreads();
+      for (int e = tid; e < k * TC; e += RL_NT) Xs[e] *= Dsm[e / TC];
+    }
+    cp_async_wait<0>();
+    __syncthreads();  // pass q's operands and the previous pass's rows of X are in place
+    stage(q + 1);     // the other slot was last read by pass q - 1
+    const T* Lq = Ls + (size_t)(q & 1) * TB * LP;
+    const T* Wq = Wsm + (size_t)(q & 1) * TB * LSP;
+    // diagonal pass: X_J = W X_J (W = W_J forward, W_J^T backward), 4 x CPT per thread
+    T* XJ = Xs + (size_t)J * TB * TC;
+    T d[4][CPT] = {};
+#pragma unroll 8
+    for (int t = 0; t < TB; ++t) {
+      T xv[CPT];
+#pragma unroll
+      for (int b = 0; b < CPT; ++b) xv[b] = XJ[t * TC + dc + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const T w = Wq[(dr + a) * LSP + t];
+#pragma unroll
+        for (int b = 0; b < CPT; ++b) d[a][b] = fma(w, xv[b], d[a][b]);
+      }
+    }
+    __syncthreads();  // every thread has read X_J
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < CPT; ++b) XJ[(dr + a) * TC + dc + b] = d[a][b];
+    __syncthreads();
+    // update pass: rows i0 .. i1 - 1 of X minus (staged rows t of L^T / L) x X_J
+    const int i0 = fwd ? (J + 1) * TB : 0, i1 = fwd ? kp : J * TB;
+    const int strips = (i1 - i0) / (RG * TR);
+    for (int st = warp; st < strips; st += RL_NT / 32) {
+      const int r0 = st * RG * TR + ug * TR;  // row offset within the updated range
+      T acc[TR][4] = {};
+#pragma unroll 4
+      for (int t = 0; t < TB; ++t) {
+        const Vec4<T> x = lds4(XJ + t * TC + uc);
+#pragma unroll
+        for (int h = 0; h < TR / 4; ++h) {
+          const Vec4<T> l = lds4(Lq + t * LP + r0 + 4 * h);
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[4 * h + a][b] = fma(l.v[a], x.v[b], acc[4 * h + a][b]);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < TR; ++a) {
+        T* xr = Xs + (size_t)(i0 + r0 + a) * TC + uc;
+        const Vec4<T> cur = lds4(xr);
+        xr[0] = cur.v[0] - acc[a][0];
+        xr[1] = cur.v[1] - acc[a][1];
+        xr[2] = cur.v[2] - acc[a][2];
+        xr[3] = cur.v[3] - acc[a][3];
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int e = tid; e < k * TC; e += RL_NT) {
+    const int i = e / TC, c = e % TC;
+    if (c0 + c < n) B[(int64_t)i * ldb + c0 + c] = Xs[e];
+  }
+}
+
+template <typename T>
+static size_t trsm_rl_smem_bytes(int kp, int tc) {
+  return sizeof(T) * ((size_t)kp * tc + 2 * (size_t)TB * rl_lpad<T>(kp) + 2 * (size_t)TB * LSP +
+                      (size_t)kp);
+}
+
+template <typename T, int TC, int TR = 8>
+static int32_t trsm_rl_launch(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t n, T* B,
+                              int64_t ldb, cudaStream_t s) {
+  const size_t bytes = trsm_rl_smem_bytes<T>(o.kp, TC);
+  RLU_CUDA_TRY(cudaFuncSetAttribute(k_trsm_rl<T, TC, TR>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  k_trsm_rl<T, TC, TR><<<(unsigned)ceil_div(n, TC), RL_NT, bytes, s>>>(o, C, ldc, n, B, ldb);
+  return last_launch_status();
+}
+
 template <typename T>
 static size_t trsm_smem_bytes(int kp, int tc) {
   return sizeof(T) * ((size_t)kp * tc + (size_t)TSTAGES * TB * LSP + 2 * (size_t)TB * tc);
@@ -982,6 +1142,10 @@ int32_t trsm_ldl(const LdlOut<T>& o, const T* C, int64_t ldc, int64_t n, T* B, i
   RLU_CUDA_TRY(cudaGetDevice(&dev));
   int optin = 0;
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (!narrow && trsm_rl_smem_bytes<T>(o.kp, 64) <= (size_t)optin)
+    return trsm_rl_launch<T, 64>(o, C, ldc, n, B, ldb, s);
+  if (trsm_rl_smem_bytes<T>(o.kp, 32) <= (size_t)optin)
+    return trsm_rl_launch<T, 32>(o, C, ldc, n, B, ldb, s);
   if (narrow && trsm_smem_bytes<T>(o.kp, 32) <= (size_t)optin)
     return trsm_launch<T, 32>(o, C, ldc, n, B, ldb, trsm_smem_bytes<T>(o.kp, 32), s);
   if (trsm_smem_bytes<T>(o.kp, 64) <= (size_t)optin)
