@@ -827,8 +827,11 @@ def batch_inputs(w: dict):
         sigma = synth.spectrum("exp_k", min(m, n), k)
         A = synth.prescribed_matrix_torch(m, n, sigma, w["seed_u"] + 2 * i, w["seed_u"] + 2 * i + 1,
                                           torch.float32)
-        # rows padded to 16 bytes: the tensor-core products read them with TMA
-        buf = torch.zeros(m, (n + 3) // 4 * 4, device="cuda")
+        # rows padded to 128 bytes: the tensor-core products read them with TMA in 128-byte
+        # (Y = A G) and 512-byte (C = L~^T A) pieces of rows, which then start on a 32-byte
+        # DRAM sector (with the 16 bytes TMA requires at least, a 128-byte piece can touch
+        # five sectors instead of four)
+        buf = torch.zeros(m, (n + 31) // 32 * 32, device="cuda")
         buf[:, :n] = A
         probs.append({"A": buf[:, :n], "k": k, "l": l, "seed": w["seed_g"] + i})
     return shapes, probs
@@ -996,14 +999,25 @@ def run_batched(args):
                                      oracle_sample=8)))
 
 
+def rotating_inputs(A: torch.Tensor, S: int = 2) -> list:
+    """A and copies of it, 256 MB (twice the L2) in all when A is smaller than L2, so that a
+    loop that takes them round robin reads every A from DRAM; the count is a multiple of S."""
+    nbytes = A.numel() * A.element_size()
+    if nbytes >= (128 << 20):
+        return [A] + [A.clone() for _ in range(S - 1)]
+    cnt = -(-(256 << 20) // nbytes)
+    cnt = -(-cnt // S) * S
+    return [A] + [A.clone() for _ in range(cnt - 1)]
+
+
 def in_flight_rate(make, A: torch.Tensor, seed: int, reps: int, S: int = 2) -> float:
     """Milliseconds per factorization with S in flight: factorization i on stream i % S with
-    its own factorizer (from make()) and its own copy of A."""
+    its own factorizer (from make()), input i of rotating_inputs(A)."""
     fzs = [make() for _ in range(S)]
-    As = [A] + [A.clone() for _ in range(S - 1)]
+    As = rotating_inputs(A, S)
     streams = [torch.cuda.current_stream()] + [torch.cuda.Stream() for _ in range(S - 1)]
     for i in range(2 * S):
-        fzs[i % S](As[i % S], seed, stream=streams[i % S])
+        fzs[i % S](As[i % len(As)], seed, stream=streams[i % S])
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = [torch.cuda.Event(enable_timing=True) for _ in range(S)]
@@ -1011,13 +1025,58 @@ def in_flight_rate(make, A: torch.Tensor, seed: int, reps: int, S: int = 2) -> f
     for st_ in streams[1:]:
         st_.wait_event(t0)
     for i in range(reps):
-        fzs[i % S](As[i % S], seed, stream=streams[i % S])
+        fzs[i % S](As[i % len(As)], seed, stream=streams[i % S])
     for j in range(S):
         t1[j].record(streams[j])
     torch.cuda.synchronize()
     ms = max(t0.elapsed_time(e) for e in t1) / reps
     del fzs, As
     return ms
+
+
+def graph_rate(make, A: torch.Tensor, seed: int, reps: int, S: int = 2):
+    """Milliseconds per factorization when each factorization is a CUDA graph replay: one
+    graph per input of rotating_inputs(A) (input j captured on stream j % S with that
+    stream's factorizer), replayed round robin with S in flight. A small problem's
+    factorization is some 17 short kernels, so the host's launch calls, not the GPU, bound
+    the API-call rate; a replay issues them in one call. Returns (ms, None) or (None, why)."""
+    fzs = [make() for _ in range(S)]
+    As = rotating_inputs(A, S)
+    streams = [torch.cuda.Stream() for _ in range(S)]
+    try:
+        for i in range(S):  # warm-up: the library's helper streams and kernel attributes
+            for _ in range(2):
+                fzs[i](As[i], seed, stream=streams[i])
+        torch.cuda.synchronize()
+        graphs = []
+        for j in range(len(As)):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=streams[j % S]):
+                fzs[j % S](As[j], seed, stream=streams[j % S])
+            graphs.append(g)
+        torch.cuda.synchronize()
+    except Exception as e:  # capture refused: report it instead of a number
+        torch.cuda.synchronize()
+        return None, f"{type(e).__name__}: {str(e)[:160]}"
+    for j in range(len(graphs)):
+        with torch.cuda.stream(streams[j % S]):
+            graphs[j].replay()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = [torch.cuda.Event(enable_timing=True) for _ in range(S)]
+    t0.record(streams[0])
+    for st_ in streams[1:]:
+        st_.wait_event(t0)
+    for i in range(reps):
+        j = i % len(graphs)
+        with torch.cuda.stream(streams[j % S]):
+            graphs[j].replay()
+    for j in range(S):
+        t1[j].record(streams[j])
+    torch.cuda.synchronize()
+    ms = max(t0.elapsed_time(e) for e in t1) / reps
+    del graphs, fzs, As
+    return ms, None
 
 
 def single_config(wname: str, K: int, W: int, peaks: dict, peak_kind: str) -> dict:
@@ -1081,6 +1140,13 @@ def single_config(wname: str, K: int, W: int, peaks: dict, peak_kind: str) -> di
         gemms[g_] = e
     ms2 = in_flight_rate(lambda: rlu.Factorizer(m, n, k, l, prec), A, w["seed_g"],
                          max(4, K))
+    graph = None
+    if small:  # launch-bound: the same factorizations as CUDA graph replays
+        gms, why = graph_rate(lambda: rlu.Factorizer(m, n, k, l, prec), A, w["seed_g"],
+                              max(64, 4 * K))
+        graph = ({"value": 1e3 / gms, "unit": "LU/s", "ms_per_step": gms, "in_flight": 2,
+                  "mode": "one captured CUDA graph per input, replayed round robin on 2 streams"}
+                 if gms else {"unavailable": why})
     P, Q, L, U, info = fz(A, w["seed_g"])
     fro_d, spec_d = rlu.reconstruct_error(A, P, Q, L, U, power_iters=100)
     torch.cuda.synchronize()
@@ -1171,9 +1237,11 @@ def single_config(wname: str, K: int, W: int, peaks: dict, peak_kind: str) -> di
     res = {"workload": f"{wname}: m={m} n={n} k={k} l={l}, sigma_i={w['spectrum']}, "
                        f"{w['dtype']} storage, {prec} path",
            "value": 1e3 / ms2, "unit": "LU/s", "ms_per_step": ms2, "in_flight": 2,
+           "graph_replay": graph,
            "single_stream": {"value": 1e3 / ms, "ms_per_step": ms}, "steps": K, "warmup": W,
            "dtype": prec, "gpu_launches": launches, "clocks": csum,
-           "l2": ("L2 flushed before every step" if small else
+           "l2": ("single stream: L2 flushed before every step; in flight and graph replays: "
+                  "256 MB of copies of A taken round robin" if small else
                   f"inputs larger than L2 (A = {A.numel() * A.element_size() / 1e6:.0f} MB)"),
            "setup_s": round(setup_s, 1), "stages_ms": {x: round(v, 4) for x, v in stage_ms.items()},
            "roofline": roof, "gemms": gemms,
