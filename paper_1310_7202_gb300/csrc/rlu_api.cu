@@ -89,11 +89,11 @@ static int32_t side_stream(cudaStream_t main, SideStream** out) {
   return RLU_OK;
 }
 
-static int split_for(int64_t M, int64_t N, int64_t K, int bm, int bn) {
+static int split_for(int64_t M, int64_t N, int64_t K, int bm, int bn, int kmin = 64) {
   const int64_t tiles = ceil_div(M, bm) * ceil_div(N, bn);
   const int64_t target = 2 * (int64_t)sm_count();
   int64_t s = ceil_div(target, tiles);
-  const int64_t kmax = K / 64 > 1 ? K / 64 : 1;  // at least 64 of K per split
+  const int64_t kmax = K / kmin > 1 ? K / kmin : 1;  // at least kmin of K per split
   if (s > kmax) s = kmax;
   if (s < 1) s = 1;
   return (int)s;
@@ -154,16 +154,19 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p,
   p.ldl = round_up(m, 8);
   p.ldb = round_up(n, 8);
   const int bm = gemm_tile_m(p.dt), bn = gemm_tile_n(p.dt);
-  p.split_y = split_for(m, l, n, bm, bn);
+  // FP64: a few tiles of FP64 multiply-adds (1/64 of the FP32 rate) would leave most SMs'
+  // FP64 units idle, so split K down to one 16-deep k-step per split
+  const int kmin = p.dt == RLU_F64 ? 16 : 64;
+  p.split_y = split_for(m, l, n, bm, bn, kmin);
   if (prec == RLU_PREC_MIXED) {  // tensor-core products: 128-row tiles, split-K fills the SMs
     p.split_y = umma3_splits(m, n, l);
   }
   if (prec == RLU_PREC_BF16) p.split_y = umma_bf16_splits(m, n, l, 256);
   if (prec == RLU_PREC_FP8) p.split_y = umma_fp8_splits(m, n, l);
   const bool bf16_like = prec == RLU_PREC_BF16 || prec == RLU_PREC_FP8;
-  p.split_g = split_for(k, k, m, bm, bn);
+  p.split_g = split_for(k, k, m, bm, bn, kmin);
   if (p.dt == RLU_F32 && p.split_g < 2) p.split_g = 2;  // FP32 partials, FP64 reduction
-  p.split_c = split_for(k, n, m, bm, bn);
+  p.split_c = split_for(k, n, m, bm, bn, kmin);
   if (prec == RLU_PREC_MIXED || bf16_like) {
     p.split_g = umma3_splits(k, m, k);
     p.split_c = umma3_splits(n, m, k);
