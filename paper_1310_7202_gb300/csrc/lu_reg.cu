@@ -795,7 +795,12 @@ static int32_t launch_reg_t(const LuArgs& a, cudaStream_t s, bool* launched) {
   // 4 rows per thread: 18 FP32 columns per panel spill ~48 bytes but halve the panel
   // launches against 10 columns (LU of Y at 32768 x 532: 2.16 -> 2.06 ms)
   constexpr int W4 = sizeof(T) == 4 ? 19 : 7;
-  if (a.R <= 16 * 512) RLU_TRY((try_launch<T, CROUT, 1, W1, 512>(a, s, launched)));
+  // FP64 multiply-adds run at 1/64 of the FP32 rate: up to 2048 rows take 128-thread CTAs,
+  // so that a step's rank-1 update spreads over four times as many SMs' FP64 units
+  if constexpr (sizeof(T) == 8) {
+    if (a.R <= 16 * 128) RLU_TRY((try_launch<T, CROUT, 1, W1, 128>(a, s, launched)));
+  }
+  if (!*launched && a.R <= 16 * 512) RLU_TRY((try_launch<T, CROUT, 1, W1, 512>(a, s, launched)));
   if (!*launched && a.R <= 16 * 1024) RLU_TRY((try_launch<T, CROUT, 2, W2, 512>(a, s, launched)));
   if (!*launched && a.R <= 16 * 2048) RLU_TRY((try_launch<T, CROUT, 4, W4, 512>(a, s, launched)));
   return RLU_OK;
