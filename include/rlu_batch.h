@@ -51,9 +51,11 @@ typedef struct {
  *   lu_rows_per_cta: rows of an LU held by one CTA of a problem's cluster: 0 or 512 (512
  *     threads), 256 (256 threads, twice the CTAs per problem; m and n <= 4096).
  *   umma_ctas_y, umma_ctas_c: under RLU_PREC_MIXED, CTAs of the tensor-core product Y = A G
- *     (resp. C = L~^T A) meant to share an SM: 0 or 1 (the deepest staging ring one CTA can
- *     hold), 2 (a shallower ring, so that two CTAs share the SM; a product whose two-slot
- *     ring does not fit that way keeps one CTA per SM). Ignored under RLU_PREC_F32. */
+ *     (resp. C = L~^T A) meant to share an SM: 0 or 1 (one CTA per SM, which keeps A's TF32
+ *     parts in tensor memory, with the deepest staging ring it can hold), 2 (A's parts
+ *     through shared memory and a shallower ring, so that two CTAs share the SM; a product
+ *     whose two-slot ring does not fit that way keeps one CTA per SM). Ignored under
+ *     RLU_PREC_F32. */
 typedef struct {
   int32_t gemm_tile_y;
   int32_t gemm_tile_c;

@@ -334,7 +334,7 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
       op.out_colmajor = true;
       op.status = p.info ? &p.info->status : nullptr;
       int sb = 0;
-      int32_t st = umma3_make_job(U3_MODE_Y2, op, &u3y[(size_t)i], &sb);
+      int32_t st = umma3_make_job(U3_MODE_Y2, op, &u3y[(size_t)i], &sb, opt.umma_ctas_y != 2);
       max_stage_y = std::max(max_stage_y, sb);
       op = Umma3Op{};
       op.A0 = static_cast<const float*>(p.A);
@@ -349,7 +349,8 @@ extern "C" int32_t rlu_batch_create(const rlu_problem* problems, int32_t count, 
       op.ldo = L.ldb;
       op.out_colmajor = true;
       op.status = p.info ? &p.info->status : nullptr;
-      if (st == RLU_OK) st = umma3_make_job(U3_MODE_C3, op, &u3c[(size_t)i], &sb);
+      if (st == RLU_OK)
+        st = umma3_make_job(U3_MODE_C3, op, &u3c[(size_t)i], &sb, opt.umma_ctas_c != 2);
       max_stage_c = std::max(max_stage_c, sb);
       if (st != RLU_OK) {
         delete b;
@@ -477,7 +478,8 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
     RLU_TRY(umma3_batched(U3_MODE_Y2, reinterpret_cast<const U3Job*>(ws + t.u3y),
                           reinterpret_cast<const int2*>(ws + t.u3y_tiles), t.n_tiles_y,
                           b->u3y_stages, b->u3y_stage_bytes,
-                          reinterpret_cast<unsigned*>(ws + t.u3_counter), s));
+                          reinterpret_cast<unsigned*>(ws + t.u3_counter), s,
+                          b->opt.umma_ctas_y != 2));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_y),
                                              c, b->max_m, b->max_l, true, true, false, s,
@@ -497,7 +499,8 @@ extern "C" int32_t rlu_factor_batched(rlu_batch* b, void* stream) {
     RLU_TRY(umma3_batched(U3_MODE_C3, reinterpret_cast<const U3Job*>(ws + t.u3c),
                           reinterpret_cast<const int2*>(ws + t.u3c_tiles), t.n_tiles_c,
                           b->u3c_stages, b->u3c_stage_bytes,
-                          reinterpret_cast<unsigned*>(ws + t.u3_counter), s));
+                          reinterpret_cast<unsigned*>(ws + t.u3_counter), s,
+                          b->opt.umma_ctas_c != 2));
   else
     RLU_TRY((gemm_simt_batched<float, float>(reinterpret_cast<const GemmArgs*>(ws + t.gemm_c),
                                              c, b->max_k, b->max_n, true, false, true, s,

@@ -50,17 +50,22 @@ struct U3Job {
   CUtensorMap map[4];
   Umma3Args a;
 };
-// Fills job (host memory) for op; *stage_bytes = its shared-memory slot size.
-int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes);
+// Fills job (host memory) for op; *stage_bytes = its shared-memory slot size. ta: the slot
+// of the kernel that keeps A's TF32 parts in tensor memory (umma3_batched with ta).
+int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes,
+                       bool ta = false);
 // Ring slots (at most 4) of this slot size that fit one CTA, or that still let ctas_per_sm
 // CTAs share an SM's shared memory (each CTA holds 256 of an SM's 512 TMEM columns).
 int32_t umma3_stages_for(int stage_bytes, int ctas_per_sm = 1);
 // One launch over a tile list (device, ntiles entries of (record, 128-row tile)), modes Y2
 // and C3, every record's BN <= 128: persistent CTAs (as many as stay resident) take tiles
 // from the list through counter (device, zeroed on s before the launch) and run one ring of
-// k-steps across their tiles with a double-buffered TMEM accumulator.
+// k-steps across their tiles with a double-buffered TMEM accumulator. ta: one CTA per SM,
+// A's TF32 parts in tensor memory (the MMAs read A from TMEM); else the parts go through
+// shared memory and two CTAs may share an SM.
 int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, int ntiles,
-                      int stages, int max_stage_bytes, unsigned* counter, cudaStream_t s);
+                      int stages, int max_stage_bytes, unsigned* counter, cudaStream_t s,
+                      bool ta = false);
 
 // BF16 products (see umma_bf16.cu), same output conventions as Umma3Op.
 // Y : A (M x K row-major BF16, lda), B0 = G^T (N x K row-major BF16, ldb), one product.

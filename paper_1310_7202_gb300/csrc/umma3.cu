@@ -452,9 +452,12 @@ k_umma3(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtenso
 // MMA issuer run one ring of k-steps across the CTA's tiles, so a tile's first loads are in
 // flight while the previous tile drains; the accumulator is double buffered in TMEM
 // (columns 0 and 128), so the epilogue of one tile overlaps the MMAs of the next. Ring slots
-// are slot bytes apart (the largest slot of the batch). Every wait is bounded: a wait that
-// gives up sets RLU_ETIMEOUT in the tile's status (or its CTA's first tile's) and ends the
-// role.
+// are slot bytes apart (the largest slot of the batch). With TA (one CTA per SM) the
+// converter stores A's hi / lo parts into tensor memory (U3_NA buffers of 64 columns after
+// the two accumulators) and the MMAs read A from there, as in the one-tile kernel; without
+// it (two CTAs per SM, 256 TMEM columns each) they go through the ring slot in shared memory.
+// Every wait is bounded: a wait that gives up sets RLU_ETIMEOUT in the tile's status (or its
+// CTA's first tile's) and ends the role.
 static constexpr int U3_QN = 4;  // tile queue depth
 struct U3PSmem {
   uint64_t full[U3_MAXST];
@@ -465,12 +468,18 @@ struct U3PSmem {
   uint64_t qfull[U3_QN];  // queue entry written (producer)
   uint64_t qempty[U3_QN]; // queue entry read (MMA 1 + converter 4 warps + epilogue 4 warps)
   uint64_t drain;         // final commit of the MMA issuer when a wait gave up
+  uint64_t afree[U3_NA];  // TA: TMEM A buffer b no longer read by the MMAs
   int queue[U3_QN];       // tile indices, -1 = no more tiles
   uint32_t tmem_base;
   int32_t err;
 };
 
-template <int MODE>
+// Ring slot of the persistent kernel: the one-tile layout when A's parts live in TMEM.
+__host__ __device__ inline U3Layout u3_persist_layout(int mode, int BN, bool ta) {
+  return ta ? u3_tile_layout(mode, BN) : u3_layout(mode, BN);
+}
+
+template <int MODE, bool TA>
 __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __restrict__ jobs,
                                                                  const int2* __restrict__ tiles,
                                                                  int ntiles, int S,
@@ -496,12 +505,14 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
       mb_init(su32(&sh.qempty[q]), 9);
     }
     mb_init(su32(&sh.drain), 1);
+    for (int b = 0; b < U3_NA; ++b) mb_init(su32(&sh.afree[b]), 1);
     sh.err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  constexpr uint32_t TCOLS = TA ? 512u : 256u;
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n"
-                 ::"r"(su32(&sh.tmem_base)) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 ::"r"(su32(&sh.tmem_base)), "r"(TCOLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -545,7 +556,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
       const int2 t = tiles[ti];
       const U3Job& j = jobs[t.x];
       const Umma3Args& a = j.a;
-      const U3Layout lay = u3_layout(MODE, a.BN);
+      const U3Layout lay = u3_persist_layout(MODE, a.BN, TA);
       const uint32_t tx = MODE == U3_MODE_Y2 ? U3_BM * 128 + (uint32_t)a.BN * 128
                                              : U3_BM * 128 + 2 * (uint32_t)a.BN * 128;
       const int m0 = t.y * U3_BM;
@@ -581,7 +592,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
       if (ti < 0) break;
       const int2 t = tiles[ti];
       const Umma3Args& a = jobs[t.x].a;
-      const U3Layout lay = u3_layout(MODE, a.BN);
+      const U3Layout lay = u3_persist_layout(MODE, a.BN, TA);
       const int buf = it & 1;
       if (it >= 2 && !mb_wait(su32(&sh.acce[buf]), (uint32_t)(((it / 2) - 1) & 1))) {
         fail(a);
@@ -601,16 +612,31 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t base = ring + st * slot;
+        if (TA) {  // A's parts of ring step g in TMEM buffer g % U3_NA
+          const uint32_t abuf = tmem + U3_ACOL + (g % (uint32_t)U3_NA) * 64u;
 #pragma unroll
-        for (int kk = 0; kk < U3_BK / 8; ++kk) {
-          const uint32_t off = kk * 32;
-          const uint64_t ah = desc_sw128(base + lay.a0 + off), al = desc_sw128(base + lay.a1 + off);
-          const uint64_t bh = desc_sw128(base + lay.b0 + off), bl = desc_sw128(base + lay.b1 + off);
-          mma_tf32(acc, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-          mma_tf32(acc, al, bh, idesc, 1u);
-          if (MODE != U3_MODE_Y2) mma_tf32(acc, ah, bl, idesc, 1u);
+          for (int kk = 0; kk < U3_BK / 8; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint64_t bh = desc_sw128(base + lay.b0 + off), bl = desc_sw128(base + lay.b1 + off);
+            const uint32_t ah = abuf + (uint32_t)kk * 8u, al = ah + 32u;
+            mma_tf32_ts(acc, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32_ts(acc, al, bh, idesc, 1u);
+            if (MODE != U3_MODE_Y2) mma_tf32_ts(acc, ah, bl, idesc, 1u);
+          }
+          commit(su32(&sh.empty[st]));
+          commit(su32(&sh.afree[g % (uint32_t)U3_NA]));
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < U3_BK / 8; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint64_t ah = desc_sw128(base + lay.a0 + off), al = desc_sw128(base + lay.a1 + off);
+            const uint64_t bh = desc_sw128(base + lay.b0 + off), bl = desc_sw128(base + lay.b1 + off);
+            mma_tf32(acc, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(acc, al, bh, idesc, 1u);
+            if (MODE != U3_MODE_Y2) mma_tf32(acc, ah, bl, idesc, 1u);
+          }
+          commit(su32(&sh.empty[st]));
         }
-        commit(su32(&sh.empty[st]));
       }
       if (!ok) break;
       commit(su32(&sh.accf[buf]));
@@ -670,7 +696,8 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
     }
   } else if (warp >= 6) {
     // ---- converter: one thread per tile row (128 rows) ------------------------------------
-    const int r = threadIdx.x - 192;  // 0..127
+    // TA: row r = TMEM lane r, so warp w serves the rows of its lane quarter w % 4
+    const int r = TA ? (warp & 3) * 32 + lane : threadIdx.x - 192;  // 0..127
     uint32_t g = 0;
     for (int it = 0; !__shfl_sync(0xffffffffu, *err, 0); ++it) {  // warp-uniform test
       const int ti = __shfl_sync(0xffffffffu, take(it, 0), 0);  // lane 0's outcome
@@ -678,7 +705,7 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
       if (ti < 0) break;
       const int2 t = tiles[ti];
       const Umma3Args& a = jobs[t.x].a;
-      const U3Layout lay = u3_layout(MODE, a.BN);
+      const U3Layout lay = u3_persist_layout(MODE, a.BN, TA);
       const int nk = (a.K + U3_BK - 1) / U3_BK;
       bool ok = true;
       for (int kt = 0; kt < nk; ++kt, ++g) {
@@ -690,6 +717,50 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
           break;
         }
         const uint32_t base = ring + st * slot;
+        if (TA) {
+          // TMEM buffer g % U3_NA is free once the MMAs of ring step g - U3_NA completed
+          const bool fr = g < (uint32_t)U3_NA ||
+                          mb_wait(su32(&sh.afree[g % (uint32_t)U3_NA]), ((g / U3_NA) - 1) & 1);
+          if (!__shfl_sync(0xffffffffu, fr ? 1 : 0, 0)) {
+            fail(a);
+            ok = false;
+            break;
+          }
+          uint32_t h[32], l[32];
+          if (MODE == U3_MODE_Y2) {  // swizzled row r: logical chunk c at chunk c ^ (r & 7)
+            const float4* row =
+                reinterpret_cast<const float4*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 8;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const float4 v = row[c ^ (r & 7)];
+              const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                float hx, lx;
+                split_tf32(vv[e], hx, lx);
+                h[4 * c + e] = __float_as_uint(hx);
+                l[4 * c + e] = __float_as_uint(lx);
+              }
+            }
+          } else {  // raw tile: 32 rows (K) x 128 floats (M); tile row r is its column r
+            const float* raw = reinterpret_cast<const float*>(u3_smem + (base + lay.a2 - su32(u3_smem)));
+#pragma unroll
+            for (int jx = 0; jx < 32; ++jx) {
+              float hx, lx;
+              split_tf32(raw[jx * U3_BM + r], hx, lx);
+              h[jx] = __float_as_uint(hx);
+              l[jx] = __float_as_uint(lx);
+            }
+          }
+          const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + U3_ACOL +
+                                 (g % (uint32_t)U3_NA) * 64u;
+          tmem_st32(taddr, h);
+          tmem_st32(taddr + 32u, l);
+          asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+          mb_arrive(su32(&sh.conv[st]));
+          continue;
+        }
         if (MODE == U3_MODE_Y2) {
           float* hi = reinterpret_cast<float*>(u3_smem + (base + lay.a0 - su32(u3_smem))) + r * 32;
           float* lo = reinterpret_cast<float*>(u3_smem + (base + lay.a1 - su32(u3_smem))) + r * 32;
@@ -745,7 +816,8 @@ __global__ void __launch_bounds__(U3_THREADS, 1) k_umma3_persist(const U3Job* __
   }
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n"
+                 ::"r"(tmem), "r"(TCOLS) : "memory");
   }
 }
 
@@ -861,10 +933,11 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
 
 // Fills one problem's record of the batched form (whole K, one N tile: N <= 256).
 template <int MODE>
-static int32_t make_job(const Umma3Op& op, U3Job* job, int* stage_bytes) {
+static int32_t make_job(const Umma3Op& op, U3Job* job, int* stage_bytes, bool ta) {
   if (op.M <= 0 || op.N <= 0 || op.N > 256 || op.K <= 0 || !op.out) return RLU_EINVAL;
+  if (ta && op.N > 128) return RLU_EINVAL;  // two accumulators of up to 128 columns
   const int BN = (int)round_up(op.N, 16);
-  const U3Layout lay = u3_layout(MODE, BN);
+  const U3Layout lay = u3_persist_layout(MODE, BN, ta);
   if (MODE == U3_MODE_Y2) {
     RLU_TRY(map2d(&job->map[0], op.A0, op.M, op.K, op.lda, U3_BK, U3_BM, true));
     RLU_TRY(map2d(&job->map[2], op.B0, op.N, op.K, op.ldb, U3_BK, BN, true));
@@ -894,9 +967,9 @@ static int32_t make_job(const Umma3Op& op, U3Job* job, int* stage_bytes) {
   return RLU_OK;
 }
 
-int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes) {
-  if (mode == U3_MODE_Y2) return make_job<U3_MODE_Y2>(op, job, stage_bytes);
-  if (mode == U3_MODE_C3) return make_job<U3_MODE_C3>(op, job, stage_bytes);
+int32_t umma3_make_job(int mode, const Umma3Op& op, U3Job* job, int* stage_bytes, bool ta) {
+  if (mode == U3_MODE_Y2) return make_job<U3_MODE_Y2>(op, job, stage_bytes, ta);
+  if (mode == U3_MODE_C3) return make_job<U3_MODE_C3>(op, job, stage_bytes, ta);
   return RLU_EINVAL;
 }
 
@@ -914,10 +987,18 @@ int32_t umma3_stages_for(int stage_bytes, int ctas_per_sm) {
 }
 
 int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, int ntiles,
-                      int stages, int max_stage_bytes, unsigned* counter, cudaStream_t s) {
+                      int stages, int max_stage_bytes, unsigned* counter, cudaStream_t s,
+                      bool ta) {
   if (ntiles <= 0) return RLU_OK;
   if (stages < 2) return RLU_EINVAL;
-  const size_t smem = 2048 + (size_t)stages * max_stage_bytes;
+  size_t smem = 2048 + (size_t)stages * max_stage_bytes;
+  if (ta) {  // 512 TMEM columns per CTA: ask for more than half the SM's shared memory
+    int dev = 0, per_sm = 0, reserved = 0;
+    RLU_CUDA_TRY(cudaGetDevice(&dev));
+    RLU_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    RLU_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    smem = std::max(smem, (size_t)(per_sm / 2 - reserved + 1024));
+  }
   // persistent: as many CTAs as stay resident (one or two per SM), each walking the list
   auto go = [&](auto kern) -> int32_t {
     RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -930,8 +1011,10 @@ int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, in
                                                   (uint32_t)max_stage_bytes, counter);
     return last_launch_status();
   };
-  if (mode == U3_MODE_Y2) return go(k_umma3_persist<U3_MODE_Y2>);
-  if (mode == U3_MODE_C3) return go(k_umma3_persist<U3_MODE_C3>);
+  if (mode == U3_MODE_Y2) return ta ? go(k_umma3_persist<U3_MODE_Y2, true>)
+                                    : go(k_umma3_persist<U3_MODE_Y2, false>);
+  if (mode == U3_MODE_C3) return ta ? go(k_umma3_persist<U3_MODE_C3, true>)
+                                    : go(k_umma3_persist<U3_MODE_C3, false>);
   return RLU_EINVAL;
 }
 
