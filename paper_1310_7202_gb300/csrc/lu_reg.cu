@@ -32,6 +32,7 @@
 
 #include "common.cuh"
 #include "panel_lu.cuh"
+#include "umma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -710,6 +711,22 @@ static size_t lr_smem_bytes(int rpc, int C) {
   return b;
 }
 
+// A rank-w trailing update: large ones (rank >= 64 over >= 128 columns) on the tensor cores
+// (FP32 with scratch for U^T's TF32 parts), the others (and where that form does not apply)
+// on the SIMT kernel, whose launch costs less than the tensor-core form's set-up.
+template <typename T>
+static int32_t trail(const LuArgs& in, T* X, int c_begin, int c_end, int p0, int w, T* U12,
+                     cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (in.u12t && w >= 64 && c_end - c_begin >= 128) {
+      const int32_t st = umma3_trail(X, in.ldx, in.R, c_begin, c_end, p0, w, in.posg, U12,
+                                     in.ldu, static_cast<float*>(in.u12t), in.status, s);
+      if (st != RLU_EUNSUPPORTED) return st;
+    }
+  }
+  return launch_trail<T>(X, in.ldx, in.R, c_begin, c_end, p0, w, in.posg, U12, in.ldu, s);
+}
+
 template <typename T, bool CROUT, int RT, int NB, int NT>
 static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
   *launched = false;
@@ -772,7 +789,7 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
       RLU_TRY(last_launch_status());
       *launched = true;
       if (p0 + a.pw < o1)
-        RLU_TRY(launch_trail<T>(X, in.ldx, in.R, p0 + a.pw, o1, p0, a.pw, in.posg, U12, in.ldu, s));
+        RLU_TRY(trail<T>(in, X, p0 + a.pw, o1, p0, a.pw, U12, s));
     }
     if (o1 < in.C) {
       const int W = o1 - o0;  // <= 96
@@ -781,7 +798,7 @@ static int32_t try_launch(const LuArgs& in, cudaStream_t s, bool* launched) {
                                                                           in.C, in.psg, U12,
                                                                           in.ldu);
       RLU_TRY(last_launch_status());
-      RLU_TRY(launch_trail<T>(X, in.ldx, in.R, o1, in.C, o0, W, in.posg, U12, in.ldu, s));
+      RLU_TRY(trail<T>(in, X, o1, in.C, o0, W, U12, s));
     }
   }
   return RLU_OK;

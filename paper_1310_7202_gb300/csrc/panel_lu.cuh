@@ -23,6 +23,8 @@ struct LuArgs {
   int cu;              // the launch solves the pivot rows of columns [p0 + pw, cu) (0: C)
   void* u12;           // [96][ldu] the solved pivot rows of the current panel or block,
   int64_t ldu;         //   dense (row s = pivot p0 + s), read by the trailing update
+  void* u12t;          // FP32 only, may be NULL: [2][96][ldu] floats of scratch; when set,
+                       //   the trailing updates run on the tensor cores (three TF32 products)
 };
 
 // crout = false: Doolittle (step 3, LU of Y); crout = true: pivot row scaled (step 6 on B^T).

@@ -121,7 +121,7 @@ struct Plan {
   size_t off_G = 0, off_Y = 0, off_Lt = 0, off_Lp = 0, off_M = 0, off_dinv = 0, off_LT = 0,
          off_LR = 0, off_W = 0, off_WT = 0,
          off_C = 0, off_T = 0, off_B = 0, off_Lb = 0, off_part = 0, off_Lhi = 0, off_Llo = 0,
-         off_pos = 0, off_ps = 0, off_u12 = 0, off_Bh = 0, off_Bm = 0, off_Bl = 0, total = 0;
+         off_pos = 0, off_ps = 0, off_u12 = 0, off_u12t = 0, off_Bh = 0, off_Bm = 0, off_Bl = 0, total = 0;
 };
 
 static size_t carve(size_t& cur, size_t bytes) {
@@ -210,6 +210,8 @@ static bool make_plan(int64_t m, int64_t n, int k, int l, int32_t prec, Plan& p,
   p.off_ps = carve(cur, (size_t)l * sizeof(int32_t));
   p.ldu12 = round_up(l, 4);  // the LUs' solved pivot rows, dense (<= 96 rows of <= l columns)
   p.off_u12 = carve(cur, (size_t)96 * p.ldu12 * e);
+  if (prec == RLU_PREC_MIXED || bf16_like)  // the LUs' trailing updates on the tensor cores
+    p.off_u12t = carve(cur, (size_t)2 * 96 * p.ldu12 * sizeof(float));
   if (prec == RLU_PREC_MIXED || bf16_like) {
     p.off_Lhi = carve(cur, (size_t)p.ldl * k * e);
     p.off_Llo = carve(cur, (size_t)p.ldl * k * e);
@@ -376,6 +378,7 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
     a.psg = reinterpret_cast<int32_t*>(ws + p.off_ps);
     a.u12 = ws + p.off_u12;
     a.ldu = p.ldu12;
+    a.u12t = p.off_u12t ? ws + p.off_u12t : nullptr;
     RLU_TRY(launch_cluster_lu(p.dt, false, a, s));
     return build_ly<T>(X, ld, rows, l, perm, Ln, nullptr, ld, s, hi, lo, parts);
   };
@@ -510,6 +513,7 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
     a.psg = reinterpret_cast<int32_t*>(ws + p.off_ps);
     a.u12 = ws + p.off_u12;
     a.ldu = p.ldu12;
+    a.u12t = p.off_u12t ? ws + p.off_u12t : nullptr;
     RLU_TRY(launch_cluster_lu(p.dt, false, a, s));
   }
   RLU_TRY(tm.rec(2, true, s));
@@ -623,6 +627,7 @@ static int32_t factor_t(const Plan& p, const void* Av, int64_t lda, uint64_t see
     a.psg = reinterpret_cast<int32_t*>(ws + p.off_ps);
     a.u12 = ws + p.off_u12;
     a.ldu = p.ldu12;
+    a.u12t = p.off_u12t ? ws + p.off_u12t : nullptr;
     RLU_TRY(launch_cluster_lu(p.dt, true, a, s));
   }
   RLU_TRY(tm.rec(8, true, s));

@@ -19,6 +19,10 @@ struct Umma3Args {
   int bn_last;  // MMA width of the last N tile (BF16 kernels)
   bool out_colmajor;
   int32_t* status;
+  // sub_pos != nullptr: out -= D instead of out = D, only in the rows r whose
+  // sub_pos[r] >= sub_min (one-tile kernel, column-major out, no split-K)
+  const int32_t* sub_pos;
+  int sub_min;
 };
 
 // Y2: A0 = A (M x K row-major, lda), B0 = G^T (N x K row-major, ldb).
@@ -40,9 +44,21 @@ struct Umma3Op {
   int splits;
   float* partial;
   int32_t* status;
+  const int32_t* sub_pos;  // see Umma3Args
+  int sub_min;
 };
 
 int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s);
+
+// Rank-w (w <= 96) trailing update of a pivoted LU on the tensor cores, FP32-accurate (three
+// TF32 products): X[r][c] -= sum_s X[r][p0 + s] U[s][c] for the columns c_begin <= c < c_end
+// of every row r whose position posg[r] >= p0 + w. X column-major (R x C, ldx, ldx % 4 == 0,
+// 16-byte aligned), U = the solved pivot rows (u12 + s * ldu, absolute column index), bt
+// scratch of 2 x 96 x (c_end - c_begin) floats (U^T's TF32 parts). RLU_EUNSUPPORTED when
+// the shapes or alignments do not suit it (the caller then runs the SIMT update).
+int32_t umma3_trail(float* X, int64_t ldx, int R, int c_begin, int c_end, int p0, int w,
+                    const int32_t* posg, const float* u12, int64_t ldu, float* bt,
+                    int32_t* status, cudaStream_t s);
 
 // Batched form (Y2 and C3 only, N <= 256, whole K per CTA): one record per problem with its
 // tensor maps (A0, A1, B0, B1) and arguments, in device memory, 64-byte aligned.

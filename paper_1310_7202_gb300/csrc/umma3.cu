@@ -320,6 +320,8 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
     const int quarter = warp & 3;
     const int row = m0 + quarter * 32 + lane;
     float* __restrict__ out = a.out + (size_t)kz * a.split_stride;
+    const bool sub = a.sub_pos != nullptr;  // out -= D in the rows still to be eliminated
+    const bool live = row < a.M && (!sub || a.sub_pos[row] >= a.sub_min);
     for (int c0 = 0; c0 < a.BN; c0 += 32) {
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
@@ -335,7 +337,20 @@ __device__ __forceinline__ void umma3_tile(const CUtensorMap& mA0, const CUtenso
             "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (ok && row < a.M) {
+      if (ok && live && sub) {
+        // all 32 loads first: stores between them would serialise their latencies
+        float cur[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = nb0 + c0 + j;
+          cur[j] = col < a.N ? out[(size_t)col * a.ldo + row] : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = nb0 + c0 + j;
+          if (col < a.N) out[(size_t)col * a.ldo + row] = cur[j] - __uint_as_float(v[j]);
+        }
+      } else if (ok && live) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = nb0 + c0 + j;
@@ -902,6 +917,9 @@ static int32_t launch_u3(const Umma3Op& op, cudaStream_t s) {
   a.stages = stages;
   a.ntiles = ntiles;
   a.status = op.status;
+  a.sub_pos = op.sub_pos;
+  a.sub_min = op.sub_min;
+  if (op.sub_pos && (splits != 1 || !op.out || !op.out_colmajor)) return RLU_EINVAL;
   if (splits == 1 && op.out) {
     a.out = op.out;
     a.ldo = op.ldo;
@@ -1016,6 +1034,51 @@ int32_t umma3_batched(int mode, const U3Job* jobs_dev, const int2* tiles_dev, in
   if (mode == U3_MODE_C3) return ta ? go(k_umma3_persist<U3_MODE_C3, true>)
                                     : go(k_umma3_persist<U3_MODE_C3, false>);
   return RLU_EINVAL;
+}
+
+// U^T's TF32 parts for the trailing update: bt_hi / bt_lo [c - c_begin][s] (row stride 96)
+// from u12[s][c]; rows s >= w are zero.
+__global__ void k_trail_bsplit(const float* __restrict__ u12, int64_t ldu, int c_begin, int nc,
+                               int w, float* __restrict__ bhi, float* __restrict__ blo) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nc * 96) return;
+  const int c = e / 96, t = e % 96;
+  const float x = t < w ? u12[(int64_t)t * ldu + c_begin + c] : 0.f;
+  float h, l;
+  u3::split_tf32(x, h, l);
+  bhi[e] = h;
+  blo[e] = l;
+}
+
+int32_t umma3_trail(float* X, int64_t ldx, int R, int c_begin, int c_end, int p0, int w,
+                    const int32_t* posg, const float* u12, int64_t ldu, float* bt,
+                    int32_t* status, cudaStream_t s) {
+  const int nc = c_end - c_begin;
+  if (nc <= 0) return RLU_OK;
+  if (w < 1 || w > 96 || R < 1 || !bt || (ldx & 3) != 0 || ((uintptr_t)X & 15) != 0)
+    return RLU_EUNSUPPORTED;
+  float* bhi = bt;
+  float* blo = bt + (size_t)96 * nc;
+  k_trail_bsplit<<<(unsigned)ceil_div((int64_t)nc * 96, 256), 256, 0, s>>>(u12, ldu, c_begin, nc,
+                                                                         w, bhi, blo);
+  RLU_TRY(last_launch_status());
+  Umma3Op op{};
+  op.A0 = X + (int64_t)p0 * ldx;  // the multipliers: K = w columns of R contiguous rows
+  op.lda = ldx;
+  op.B0 = bhi;
+  op.B1 = blo;
+  op.ldb = 96;
+  op.M = R;
+  op.N = nc;
+  op.K = w;
+  op.out = X + (int64_t)c_begin * ldx;
+  op.ldo = ldx;
+  op.out_colmajor = true;
+  op.splits = 1;
+  op.status = status;
+  op.sub_pos = posg;
+  op.sub_min = p0 + w;
+  return launch_u3<U3_MODE_C3>(op, s);
 }
 
 int32_t umma3_gemm(int mode, const Umma3Op& op, cudaStream_t s) {
