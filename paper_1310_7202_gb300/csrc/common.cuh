@@ -72,4 +72,25 @@ __device__ __forceinline__ void warp_argmax(T& mag, int& pos, int& row) {
 __device__ __forceinline__ bool is_finite_val(double x) { return isfinite(x); }
 __device__ __forceinline__ bool is_finite_val(float x) { return isfinite(x); }
 
+// Complex FP32 element of the register LU (same memory layout as float2): arithmetic with
+// fused multiply-adds, so that the LU's templates run on it as on float and double.
+struct __align__(8) cf32 {
+  float x, y;
+  cf32() = default;
+  __host__ __device__ constexpr cf32(float r) : x(r), y(0.f) {}
+  __host__ __device__ constexpr cf32(float r, float i) : x(r), y(i) {}
+};
+__device__ __forceinline__ cf32 operator-(cf32 a) { return cf32(-a.x, -a.y); }
+__device__ __forceinline__ cf32 operator*(cf32 a, cf32 b) {
+  return cf32(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ bool operator!=(cf32 a, cf32 b) { return a.x != b.x || a.y != b.y; }
+__device__ __forceinline__ bool operator==(cf32 a, cf32 b) { return a.x == b.x && a.y == b.y; }
+// a b + c (the float and double overloads stay visible beside it)
+using ::fma;
+__device__ __forceinline__ cf32 fma(cf32 a, cf32 b, cf32 c) {
+  return cf32(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ bool is_finite_val(cf32 v) { return isfinite(v.x) && isfinite(v.y); }
+
 }  // namespace rlu

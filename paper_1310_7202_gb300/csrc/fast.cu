@@ -23,6 +23,7 @@
 
 #include "common.cuh"
 #include "gemm_simt.cuh"
+#include "panel_lu.cuh"
 #include "small.cuh"
 #include "../../include/rlu_fast.h"
 
@@ -772,6 +773,43 @@ __global__ void k_frlu_pack_l(const float* __restrict__ Lo, int m, int k, float2
     L[(int64_t)j * ldl + i] = make_float2(Lo[(int64_t)j * m + i], Lo[(int64_t)(k + j) * m + i]);
 }
 
+// Row-major R x C complex (ld ldr) -> column-major (ld ldc), through a 32 x 32 shared tile.
+__global__ void k_c_rm_to_cm(const float2* __restrict__ Yr, int64_t ldr, int R, int C,
+                             float2* __restrict__ X, int64_t ldc) {
+  __shared__ float2 t[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < C) t[i][threadIdx.x] = Yr[(int64_t)r * ldr + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int c = c0 + j, r = r0 + threadIdx.x;
+    if (r < R && c < C) X[(int64_t)c * ldc + r] = t[threadIdx.x][j];
+  }
+}
+
+// The register LU's swap-free result back to the positional row-major layout of the rest of
+// the pipeline: row p of Yr = row perm[p] of X (column-major, ld ldc).
+__global__ void k_c_cm_to_rm_perm(const float2* __restrict__ X, int64_t ldc, int R, int C,
+                                  const int32_t* __restrict__ perm, float2* __restrict__ Yr,
+                                  int64_t ldr) {
+  __shared__ float2 t[32][33];
+  __shared__ int src[32];
+  const int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  if (threadIdx.y == 0) src[threadIdx.x] = p0 + threadIdx.x < R ? perm[p0 + threadIdx.x] : 0;
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {  // column c0 + j, rows src[x]
+    const int c = c0 + j, p = p0 + threadIdx.x;
+    if (p < R && c < C) t[threadIdx.x][j] = X[(int64_t)c * ldc + src[threadIdx.x]];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int p = p0 + i, c = c0 + threadIdx.x;
+    if (p < R && c < C) Yr[(int64_t)p * ldr + c] = t[i][threadIdx.x];
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Workspace plan and the entry points.
 // ---------------------------------------------------------------------------------------
@@ -783,6 +821,9 @@ struct FastPlan {
   size_t off_d = 0, off_Y = 0, off_pub = 0, off_S = 0, off_V = 0, off_part = 0, off_M = 0,
          off_LT = 0, off_LR = 0, off_W = 0, off_WT = 0, off_dinv = 0, off_Wst = 0, off_AJ = 0,
          off_C = 0, off_B = 0, off_Bt = 0, off_Lbe = 0, off_Lo = 0, total = 0;
+  // the register LU's column-major copy of Y (then of B^T), position state, pivot rows
+  size_t off_X = 0, off_posg = 0, off_psg = 0, off_u12 = 0;
+  int64_t ldxy = 0, ldxb = 0, ldu12 = 0;
 };
 
 static size_t fp_carve(size_t& cur, size_t bytes) {
@@ -828,8 +869,48 @@ static int32_t fast_plan(int64_t m, int64_t n, int k, int l, FastPlan& p) {
   p.off_Bt = fp_carve(cur, (size_t)n * k * sizeof(float2));
   p.off_Lbe = fp_carve(cur, (size_t)k2 * k2 * sizeof(float));
   p.off_Lo = fp_carve(cur, (size_t)m * k2 * sizeof(float));
+  p.ldxy = round_up(m, 4);
+  p.ldxb = round_up(n, 4);
+  p.ldu12 = round_up(l, 4);
+  p.off_X = fp_carve(cur, (size_t)std::max(p.ldxy * l, p.ldxb * k) * sizeof(float2));
+  p.off_posg = fp_carve(cur, (size_t)std::max(m, n) * sizeof(int32_t));
+  p.off_psg = fp_carve(cur, (size_t)l * sizeof(int32_t));
+  p.off_u12 = fp_carve(cur, (size_t)96 * p.ldu12 * sizeof(float2));
   p.total = cur;
   return RLU_OK;
+}
+
+// Steps 3 and 7: the pivoted LU (|Re| + |Im| pivots) of a tall complex matrix, row-major
+// R x C (ld ldy), in place: on return row p holds the factors of position p and perm[p] the
+// original row there. The cluster register LU (lu_reg.cu, complex FP32) factors a
+// column-major copy, swap-free, and the result is gathered back; where it does not launch
+// (shape), the cooperative kernel factors Y directly.
+static int32_t clu_factor(const FastPlan& p, char* ws, bool crout, float2* Y, int64_t ldy, int R,
+                          int C, int32_t* perm, void* pub, int32_t* status, int32_t* nonfinite,
+                          int32_t* first_zero, cudaStream_t s) {
+  const int64_t ldx = round_up(R, 4);
+  float2* X = reinterpret_cast<float2*>(ws + p.off_X);
+  const dim3 tb(32, 8), tg((unsigned)ceil_div(R, 32), (unsigned)ceil_div(C, 32));
+  k_c_rm_to_cm<<<tg, tb, 0, s>>>(Y, ldy, R, C, X, ldx);
+  RLU_TRY(last_launch_status());
+  LuArgs a{};
+  a.X = X;
+  a.ldx = ldx;
+  a.R = R;
+  a.C = C;
+  a.perm = perm;
+  a.zero_step = first_zero;
+  a.nonfinite = nonfinite;
+  a.status = status;
+  a.posg = reinterpret_cast<int32_t*>(ws + p.off_posg);
+  a.psg = reinterpret_cast<int32_t*>(ws + p.off_psg);
+  a.u12 = ws + p.off_u12;
+  a.ldu = p.ldu12;
+  bool launched = false;
+  RLU_TRY(launch_lu_reg(kLuC64, crout, a, s, &launched));
+  if (!launched) return clu_coop(crout, Y, ldy, R, C, perm, pub, sm_count(), status, first_zero, s);
+  k_c_cm_to_rm_perm<<<tg, tb, 0, s>>>(X, ldx, R, C, perm, Y, ldy);
+  return last_launch_status();
 }
 
 // Steps 1-2: d = exp(2 pi i theta) into d (n values), then Y = A D F S.
@@ -874,8 +955,9 @@ static int32_t fast_factor(const FastPlan& p, const float* A, int64_t m, int64_t
   // steps 1-2: Y = A D F S
   RLU_TRY(srft_apply(A, m, n, lda, theta, sel, l, d, p.fft, Y, l, status, s));
   // step 3: P Y = L_y U_y
-  RLU_TRY(clu_coop(false, Y, l, (int)m, l, P, pub, sm_count(), status,
-                   info ? &info->first_zero_pivot_y : nullptr, s));
+  RLU_TRY(clu_factor(p, ws, false, Y, l, (int)m, l, P, pub, status,
+                     info ? &info->nonfinite : nullptr,
+                     info ? &info->first_zero_pivot_y : nullptr, s));
   // steps 4-6: V = L_y^H L_f (planes), M's real form, W = V L_1^{-1}, C = W A(J,:), B = M^{-1} C
   k_frlu_planes<<<dim3((unsigned)ceil_div(m, 32), (unsigned)ceil_div(l, 32)), dim3(32, 8), 0, s>>>(
       Y, l, (int)m, l, S);
@@ -921,8 +1003,9 @@ static int32_t fast_factor(const FastPlan& p, const float* A, int64_t m, int64_t
   k_frlu_pack_bt<<<dim3((unsigned)ceil_div(n, 32), (unsigned)ceil_div(k, 32)), dim3(32, 8), 0, s>>>(
       Bst, p.ldn, k, (int)n, Bt, k);
   RLU_TRY(last_launch_status());
-  RLU_TRY(clu_coop(true, Bt, k, (int)n, k, Q, pub, sm_count(), status,
-                   info ? &info->first_zero_pivot_b : nullptr, s));
+  RLU_TRY(clu_factor(p, ws, true, Bt, k, (int)n, k, Q, pub, status,
+                     info ? &info->nonfinite : nullptr,
+                     info ? &info->first_zero_pivot_b : nullptr, s));
   // steps 8-9: U = U_b, L = L_y L_b
   k_frlu_unpack_u<<<dim3((unsigned)ceil_div(n, 32), (unsigned)ceil_div(k, 32)), dim3(32, 8), 0, s>>>(
       Bt, k, k, (int)n, U, ldu);

@@ -29,6 +29,7 @@
 // records RLU_ETIMEOUT in the status word and keeps going without waiting, so every CTA
 // still reaches the same cluster barriers and exits.
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "common.cuh"
 #include "panel_lu.cuh"
@@ -84,6 +85,11 @@ __device__ __forceinline__ uint64_t mag_key(double v) {
   const double a = fabs(v);
   return (a == a) ? (uint64_t)__double_as_longlong(a) : 0ull;
 }
+// Complex FP32 (the fast randomized LU of Algorithm 4): pivots by |Re| + |Im|.
+__device__ __forceinline__ uint64_t mag_key(cf32 v) {
+  const float a = fabsf(v.x) + fabsf(v.y);
+  return (a == a) ? ((uint64_t)__float_as_uint(a) << 32) : 0ull;
+}
 
 // Reciprocal of a pivot: the hardware approximation refined by Newton-Raphson steps
 // (y' = y + y (1 - p y)): one step in FP32 (within an ulp or so), two from the FP32 seed in
@@ -97,6 +103,13 @@ __device__ __forceinline__ float rcp_piv(float p) {
   const float y = rcp_approx(p);
   if (!isfinite(y)) return y;
   return fmaf(y, fmaf(-p, y, 1.0f), y);
+}
+// 1 / p with the larger of |Re p|, |Im p| scaled out first (no overflow of |p|^2)
+__device__ __forceinline__ cf32 rcp_piv(cf32 p) {
+  const float sc = fmaxf(fabsf(p.x), fabsf(p.y));
+  const float qx = p.x / sc, qy = p.y / sc;
+  const float den = (qx * qx + qy * qy) * sc;
+  return cf32(qx / den, -qy / den);
 }
 __device__ __forceinline__ double rcp_piv(double p) {
   const double a = fabs(p);
@@ -139,6 +152,21 @@ __device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
 }
 __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
   *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void ld4(const cf32* p, cf32 (&o)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 2);
+  o[0] = cf32(a.x, a.y); o[1] = cf32(a.z, a.w); o[2] = cf32(b.x, b.y); o[3] = cf32(b.z, b.w);
+}
+__device__ __forceinline__ void st4(cf32* p, cf32 a, cf32 b, cf32 c, cf32 d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  *reinterpret_cast<float4*>(p + 2) = make_float4(c.x, c.y, d.x, d.y);
+}
+// warp shuffle of one element
+__device__ __forceinline__ float shfl_t(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl_t(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ cf32 shfl_t(cf32 v, int src) {
+  return cf32(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 __device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
   *reinterpret_cast<double2*>(p) = make_double2(a, b);
@@ -450,7 +478,7 @@ __device__ __forceinline__ void lu_reg_body(const LuArgs& a) {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
         for (int s = 32 * q; s < min(w, 32 * q + 32); ++s) {
-          T us = __shfl_sync(0xffffffffu, u[q], s - 32 * q);
+          T us = shfl_t(u[q], s - 32 * q);
           if (CROUT) {
             const T pv = L11[s * NB + s];
             if (pv != T(0)) us = us * rcp_piv(pv);
@@ -680,7 +708,7 @@ __global__ void __launch_bounds__(256) k_lu_u12(T* __restrict__ X, int64_t ldx, 
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     for (int s = 32 * q; s < min(W, 32 * q + 32); ++s) {
-      T us = __shfl_sync(0xffffffffu, u[q], s - 32 * q);
+      T us = shfl_t(u[q], s - 32 * q);
       if (CROUT) {
         const T pv = L11[s * WP + s];
         if (pv != T(0)) us = us * rcp_piv(pv);
@@ -814,7 +842,7 @@ static int32_t launch_reg_t(const LuArgs& a, cudaStream_t s, bool* launched) {
   constexpr int W4 = sizeof(T) == 4 ? 19 : 7;
   // FP64 multiply-adds run at 1/64 of the FP32 rate: up to 2048 rows take 128-thread CTAs,
   // so that a step's rank-1 update spreads over four times as many SMs' FP64 units
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (std::is_same<T, double>::value) {
     if (a.R <= 16 * 128) RLU_TRY((try_launch<T, CROUT, 1, W1, 128>(a, s, launched)));
   }
   if (!*launched && a.R <= 16 * 512) RLU_TRY((try_launch<T, CROUT, 1, W1, 512>(a, s, launched)));
@@ -827,6 +855,7 @@ int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s
   *launched = false;
   if (dtype == RLU_F64) return crout ? launch_reg_t<double, true>(a, s, launched) : launch_reg_t<double, false>(a, s, launched);
   if (dtype == RLU_F32) return crout ? launch_reg_t<float, true>(a, s, launched) : launch_reg_t<float, false>(a, s, launched);
+  if (dtype == kLuC64) return crout ? launch_reg_t<cf32, true>(a, s, launched) : launch_reg_t<cf32, false>(a, s, launched);
   return RLU_OK;
 }
 

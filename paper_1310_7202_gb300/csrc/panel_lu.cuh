@@ -31,6 +31,9 @@ struct LuArgs {
 int32_t launch_cluster_lu(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s);
 
 // Register-resident variant (lu_reg.cu); *launched is false when the shape does not fit it.
+// dtype RLU_F64, RLU_F32 or kLuC64 (complex FP32, interleaved (Re, Im) pairs; pivots by
+// |Re| + |Im|; the fast randomized LU of Algorithm 4).
+static constexpr int32_t kLuC64 = 64;
 int32_t launch_lu_reg(int32_t dtype, bool crout, const LuArgs& a, cudaStream_t s, bool* launched);
 
 // Batched FP32 LUs of single-panel problems (C <= 76, R <= 16 x rows_per_cta), one cluster
