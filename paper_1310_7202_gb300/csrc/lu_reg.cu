@@ -845,6 +845,11 @@ static int32_t launch_reg_t(const LuArgs& a, cudaStream_t s, bool* launched) {
   if constexpr (std::is_same<T, double>::value) {
     if (a.R <= 16 * 128) RLU_TRY((try_launch<T, CROUT, 1, W1, 128>(a, s, launched)));
   }
+  // complex: four real multiply-adds per element; up to 4096 rows take 256-thread CTAs, twice
+  // the SMs of 512-thread ones for the rank-1 updates
+  if constexpr (std::is_same<T, cf32>::value) {
+    if (a.R <= 16 * 256) RLU_TRY((try_launch<T, CROUT, 1, W1, 256>(a, s, launched)));
+  }
   if (!*launched && a.R <= 16 * 512) RLU_TRY((try_launch<T, CROUT, 1, W1, 512>(a, s, launched)));
   if (!*launched && a.R <= 16 * 1024) RLU_TRY((try_launch<T, CROUT, 2, W2, 512>(a, s, launched)));
   if (!*launched && a.R <= 16 * 2048) RLU_TRY((try_launch<T, CROUT, 4, W4, 512>(a, s, launched)));
