@@ -25,6 +25,7 @@
 #include "gemm_simt.cuh"
 #include "panel_lu.cuh"
 #include "small.cuh"
+#include "umma.cuh"
 #include "../../include/rlu_fast.h"
 
 namespace rlu {
@@ -810,6 +811,28 @@ __global__ void k_c_cm_to_rm_perm(const float2* __restrict__ X, int64_t ldc, int
   }
 }
 
+// Exact TF32 parts (hi = x with its 13 low mantissa bits cleared, lo = x - hi) of the
+// transpose of a row-major R x C matrix: hi / lo[c * ldo + r] from X[r * ldx + c].
+__global__ void k_split_t(const float* __restrict__ X, int64_t ldx, int R, int C,
+                          float* __restrict__ hi, float* __restrict__ lo, int64_t ldo) {
+  __shared__ float t[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    t[i][threadIdx.x] = (r < R && c < C) ? X[(int64_t)r * ldx + c] : 0.f;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int c = c0 + j, r = r0 + threadIdx.x;
+    if (r < R && c < C) {
+      const float v = t[threadIdx.x][j];
+      const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+      hi[(int64_t)c * ldo + r] = h;
+      lo[(int64_t)c * ldo + r] = v - h;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Workspace plan and the entry points.
 // ---------------------------------------------------------------------------------------
@@ -824,6 +847,11 @@ struct FastPlan {
   // the register LU's column-major copy of Y (then of B^T), position state, pivot rows
   size_t off_X = 0, off_posg = 0, off_psg = 0, off_u12 = 0;
   int64_t ldxy = 0, ldxb = 0, ldu12 = 0;
+  // the three plane products on the tensor cores (TF32 splits of their second operands,
+  // FP32 partial slices) when every leading dimension suits TMA
+  bool tc = false;
+  int split_vt = 1;
+  size_t off_Sh = 0, off_Sl = 0, off_Wh = 0, off_Wl = 0, off_Lbh = 0, off_Lbl = 0, off_part2 = 0;
 };
 
 static size_t fp_carve(size_t& cur, size_t bytes) {
@@ -876,6 +904,21 @@ static int32_t fast_plan(int64_t m, int64_t n, int k, int l, FastPlan& p) {
   p.off_posg = fp_carve(cur, (size_t)std::max(m, n) * sizeof(int32_t));
   p.off_psg = fp_carve(cur, (size_t)l * sizeof(int32_t));
   p.off_u12 = fp_carve(cur, (size_t)96 * p.ldu12 * sizeof(float2));
+  p.tc = m % 4 == 0 && l % 4 == 0 && k % 2 == 0 && p.ldn % 4 == 0;
+  if (p.tc) {
+    p.split_vt = umma3_splits(k, 2 * m, 2 * (int64_t)l);
+    const int64_t kc = round_up(ceil_div(2 * m, p.split_vt), 32);
+    const int64_t sv = ceil_div(2 * m, kc);
+    p.off_Sh = fp_carve(cur, (size_t)(2 * m) * (2 * l) * sizeof(float));
+    p.off_Sl = fp_carve(cur, (size_t)(2 * m) * (2 * l) * sizeof(float));
+    p.off_Wh = fp_carve(cur, (size_t)k2 * l * sizeof(float));
+    p.off_Wl = fp_carve(cur, (size_t)k2 * l * sizeof(float));
+    p.off_Lbh = fp_carve(cur, (size_t)k2 * k2 * sizeof(float));
+    p.off_Lbl = fp_carve(cur, (size_t)k2 * k2 * sizeof(float));
+    p.off_part2 = fp_carve(cur, std::max<size_t>((size_t)sv * k * (2 * l),
+                                                 (size_t)2 * std::max(m, n) * k2) *
+                                    sizeof(float));
+  }
   p.total = cur;
   return RLU_OK;
 }
@@ -962,7 +1005,29 @@ static int32_t fast_factor(const FastPlan& p, const float* A, int64_t m, int64_t
   k_frlu_planes<<<dim3((unsigned)ceil_div(m, 32), (unsigned)ceil_div(l, 32)), dim3(32, 8), 0, s>>>(
       Y, l, (int)m, l, S);
   RLU_TRY(last_launch_status());
-  {
+  if (p.tc) {  // V = S[:, :k]^T S: three TF32 products (A split on chip, S's parts), FP64 sum
+    float* Sh = reinterpret_cast<float*>(ws + p.off_Sh);
+    float* Sl = reinterpret_cast<float*>(ws + p.off_Sl);
+    float* part2 = reinterpret_cast<float*>(ws + p.off_part2);
+    RLU_TRY(split_parts(S, 2 * m, 2 * m, 2 * l, Sh, Sl, Bf16Parts{}, s));
+    Umma3Op op{};
+    op.A0 = S;
+    op.lda = 2 * m;
+    op.B0 = Sh;
+    op.B1 = Sl;
+    op.ldb = 2 * m;
+    op.M = k;
+    op.N = 2 * (int64_t)l;
+    op.K = 2 * m;
+    op.out = nullptr;
+    op.splits = p.split_vt;
+    op.partial = part2;
+    op.status = status;
+    RLU_TRY(umma3_gemm(U3_MODE_Y3, op, s));
+    const int64_t kc = round_up(ceil_div(2 * m, p.split_vt), 32);
+    RLU_TRY(splitk_reduce_f64(part2, (int)ceil_div(2 * m, kc), k, 2 * (int64_t)l, V,
+                              2 * (int64_t)l, s));
+  } else {
     GemmOp op{S, 2 * m, true, S, 2 * m, true, V, 2 * (int64_t)l, true, k, 2 * (int64_t)l, 2 * m,
               p.split_v, ws + p.off_part, false};
     RLU_TRY((gemm_simt<float, double>(op, s)));
@@ -994,7 +1059,27 @@ static int32_t fast_factor(const FastPlan& p, const float* A, int64_t m, int64_t
   k_frlu_gather_aj<<<dim3((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)l), 256, 0, s>>>(
       A, lda, (int)n, P, AJ, p.ldn);
   RLU_TRY(last_launch_status());
-  {
+  if (p.tc) {  // C^T = A(J,:)^T W^T: A(J,:) as the raw n-contiguous operand, W's TF32 parts
+    float* Wh = reinterpret_cast<float*>(ws + p.off_Wh);
+    float* Wl = reinterpret_cast<float*>(ws + p.off_Wl);
+    RLU_TRY(split_parts(Wst, l, l, k2, Wh, Wl, Bf16Parts{}, s));
+    Umma3Op op{};
+    op.A0 = AJ;
+    op.lda = p.ldn;
+    op.B0 = Wh;
+    op.B1 = Wl;
+    op.ldb = l;
+    op.M = n;
+    op.N = k2;
+    op.K = l;
+    op.out = Cst;
+    op.ldo = p.ldn;
+    op.out_colmajor = true;
+    op.splits = umma3_splits(n, l, k2);
+    op.partial = reinterpret_cast<float*>(ws + p.off_part2);
+    op.status = status;
+    RLU_TRY(umma3_gemm(U3_MODE_C3, op, s));
+  } else {
     GemmOp op{Wst, l, true, AJ, p.ldn, false, Cst, p.ldn, true, k2, n, l, 1, nullptr, false};
     RLU_TRY((gemm_simt<float, float>(op, s)));
   }
@@ -1013,7 +1098,30 @@ static int32_t fast_factor(const FastPlan& p, const float* A, int64_t m, int64_t
   k_frlu_lb_embed<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)k * k, 256), 4096), 256, 0, s>>>(
       Bt, k, k, Lbe);
   RLU_TRY(last_launch_status());
-  {
+  if (p.tc) {  // L's planes = S (read with ld m) Lbe: S as the raw m-contiguous operand
+    float* Lbh = reinterpret_cast<float*>(ws + p.off_Lbh);
+    float* Lbl = reinterpret_cast<float*>(ws + p.off_Lbl);
+    // Lbe is row-major (row = K index); the operand wants its columns contiguous
+    k_split_t<<<dim3((unsigned)ceil_div(k2, 32), (unsigned)ceil_div(k2, 32)), dim3(32, 8), 0, s>>>(
+        Lbe, k2, k2, k2, Lbh, Lbl, k2);
+    RLU_TRY(last_launch_status());
+    Umma3Op op{};
+    op.A0 = S;
+    op.lda = m;
+    op.B0 = Lbh;
+    op.B1 = Lbl;
+    op.ldb = k2;
+    op.M = m;
+    op.N = k2;
+    op.K = k2;
+    op.out = Lo;
+    op.ldo = m;
+    op.out_colmajor = true;
+    op.splits = umma3_splits(m, k2, k2);
+    op.partial = reinterpret_cast<float*>(ws + p.off_part2);
+    op.status = status;
+    RLU_TRY(umma3_gemm(U3_MODE_C3, op, s));
+  } else {
     GemmOp op{S, m, false, Lbe, k2, false, Lo, m, false, m, k2, k2, 1, nullptr, false};
     RLU_TRY((gemm_simt<float, float>(op, s)));
   }
