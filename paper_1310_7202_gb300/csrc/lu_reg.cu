@@ -1,7 +1,9 @@
 // Register-resident pivoted LU of a tall-skinny column-major X (R x C) on one thread-block
 // cluster: the fast form of steps 3 (Doolittle, X = Y) and 6 (Crout, X = B^T) of
 // Algorithm 1, with the same swap-free position bookkeeping and tie rule as panel_lu.cu
-// (largest |value|, then smallest current position, which is getf2's choice).
+// (largest |value|, then smallest current position, which is getf2's choice). The element
+// type is float, double or cf32 (complex FP32, for the fast randomized LU of Algorithm 4,
+// whose pivots go by |Re| + |Im|).
 //
 // One launch factors one panel of up to NB-1 columns; the positions of the rows persist in
 // global memory between launches, and k_lu_trail (all SMs) applies each panel's rank-w

@@ -6,21 +6,24 @@
 //   MODE_Y2  Y = A G (step 2): A row-major (K-major), split on chip; G not split (rounding
 //            G only changes the Gaussian test matrix). Products hi(A) G + lo(A) G.
 //   MODE_C3  C^T = A^T L~ (step 5): the A tile arrives n-contiguous (MN-major) and is
-//            transposed and split on chip into K-major tiles; L~ comes pre-split (hi, lo).
-//            Products Ahi Lhi + Alo Lhi + Ahi Llo.
+//            transposed and split on chip; L~ comes pre-split (hi, lo). Products
+//            Ahi Lhi + Alo Lhi + Ahi Llo. Also the LUs' large trailing updates
+//            (umma3_trail: X's multiplier columns as A, with an epilogue that subtracts the
+//            product from the rows still to be eliminated) and two plane products of the
+//            fast randomized LU.
 //   MODE_G3  Gram L~^T L~ (step 5): both operands pre-split, three products.
 //   MODE_Y3  Y = A Z (the power iterations of Section 5): A split on chip as in MODE_Y2, Z
 //            pre-split (hi, lo); products hi(A) Zhi + lo(A) Zhi + hi(A) Zlo.
 //
 // Warp roles: warp 0 TMA producer (ring of STAGES slots, full/empty mbarriers), warp 1
 // TMEM allocation and MMA issue, warps 2..5 epilogue (tcgen05.ld), warps 6..9 converter
-// (MODE_Y2 / MODE_Y3 / MODE_C3): one thread per tile row. In the one-tile kernel the
-// converter stores the row's hi and lo parts into tensor memory (tcgen05.st, the thread's
-// own TMEM lane) and the MMAs take A from there, so shared memory carries only what TMA
-// brings and what the MMAs read of B; in the persistent batched kernel it writes
-// 128-byte-swizzled K-major hi/lo tiles to shared memory and fences them to the async
-// proxy. Either way it arrives on a per-slot mbarrier. Every wait is bounded (~1 s) and
-// records an error instead of hanging.
+// (MODE_Y2 / MODE_Y3 / MODE_C3): one thread per tile row. In the one-tile kernel, and in
+// the persistent batched kernel with one CTA per SM, the converter stores the row's hi and
+// lo parts into tensor memory (tcgen05.st, the thread's own TMEM lane) and the MMAs take A
+// from there, so shared memory carries only what TMA brings and what the MMAs read of B;
+// in the persistent kernel with two CTAs per SM it writes 128-byte-swizzled K-major hi/lo
+// tiles to shared memory and fences them to the async proxy. Either way it arrives on a
+// per-slot mbarrier. Every wait is bounded (~1 s) and records an error instead of hanging.
 #include <algorithm>
 
 #include <cuda.h>
